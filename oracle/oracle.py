@@ -1,0 +1,396 @@
+"""Plain FP64 CPU oracle for linear-time Sinkhorn with positive features.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check of the build
+entry point and the CPU-baseline leg of the benchmark may import this module.
+The product path (the CUDA library and its Python binding) never imports it and
+shares no code with it.
+
+What it computes, in the paper's order and notation (Scetbon & Cuturi,
+"Linear Time Sinkhorn Divergences using Positive Features", arXiv 2006.07057):
+
+* Lemma 1 (Sec. 3.2): the Gaussian kernel k(x,y) = exp(-||x-y||^2/eps) has the
+  positive feature map
+      phi(x,u) = (2q)^{d/4} exp(-2||x-u||^2/eps) exp(||u||^2/(eps q)),
+  u ~ rho = N(0, sigma^2 I), sigma^2 = q eps / 4,
+  q = R^2 / (2 eps d W0(R^2/(eps d))), W0 the principal Lambert branch.
+  The Lemma statement prints the last exponent as ||u||^2/(eps(1/2 + R^2/eps));
+  its proof derives ||u||^2/(eps q), the only form for which the integral
+  identity holds (pinned by the Monte Carlo unbiasedness test).
+* Sec. 3.2: phi_theta(x) = r^{-1/2} (phi(x,u_1), ..., phi(x,u_r)), u_k iid rho.
+* Sec. 3.1: K_theta = xi^T zeta (here xi is stored point-major, n x r).
+* Alg. 1 (Sec. 2): Sinkhorn scaling updates, run here as u <- a/(K v),
+  v <- b/(K^T u) from v = 1 (one iteration = one u-half then one v-half); the
+  reported residual is ||u o (K v) - a||_1 after the last v-half.
+* Eq. (6): W_hat = eps (a^T log u + b^T log v).
+* Eq. (2): debiased W_bar = W(a,b) - (W(a,a) + W(b,b))/2 with one shared theta.
+* Prop. 3.3 and the formula after it (Sec. 3.3): dW/dK = -eps u v^T at the
+  optimum, chained through xi(X) with theta held fixed.
+
+The primary solver works in the log domain (always representable in FP64).
+``sinkhorn_scaled`` runs the same iterates in the scaling domain with per-row
+log shifts; it is faster and is checked against the log-domain solver.
+``sinkhorn_dense`` is textbook Alg. 1 on an explicit matrix, for tiny inputs.
+
+Every function here is pinned by tests against values fixed by the paper or the
+mathematics (closed forms, invariants, library routines, brute force).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "lambert_w0",
+    "gaussian_params",
+    "radius",
+    "anchors",
+    "log_features",
+    "features",
+    "gaussian_kernel",
+    "lse",
+    "sinkhorn_log",
+    "sinkhorn_scaled",
+    "sinkhorn_dense",
+    "dual_estimate",
+    "dual_objective",
+    "primal_objective",
+    "Theta",
+    "make_theta",
+    "solve",
+    "divergence",
+    "gradient",
+    "deviation",
+]
+
+
+# --------------------------------------------------------------------------
+# Lemma 1 parameters
+# --------------------------------------------------------------------------
+
+def lambert_w0(z):
+    """Principal branch W0 of the Lambert function for real z >= 0.
+
+    W0(z) is the solution w >= 0 of w e^w = z (used by Lemma 1 to set q).
+    Halley's iteration on f(w) = w e^w - z from the start w = log(1 + z), which
+    lies above the root for z > 0; the iteration is run to FP64 convergence.
+    """
+    z = np.asarray(z, dtype=np.float64)
+    if np.any(z < 0):
+        raise ValueError("lambert_w0: this oracle only needs z >= 0")
+    w = np.log1p(z)
+    for _ in range(100):
+        ew = np.exp(w)
+        f = w * ew - z
+        denom = ew * (w + 1.0) - (w + 2.0) * f / (2.0 * w + 2.0)
+        step = np.where(denom != 0, f / np.where(denom != 0, denom, 1.0), 0.0)
+        w_new = w - step
+        done = np.all(np.abs(w_new - w) <= 4e-16 * np.maximum(np.abs(w_new), 1e-300))
+        w = w_new
+        if done:
+            break
+    return w if w.ndim else float(w)
+
+
+def gaussian_params(R: float, eps: float, d: int) -> tuple[float, float]:
+    """(q, sigma) of Lemma 1: q = R^2/(2 eps d W0(R^2/(eps d))), sigma^2 = q eps/4.
+
+    As R -> 0, z/W0(z) -> 1 so q -> 1/2; that limit is returned for R = 0.
+    """
+    z = R * R / (eps * d)
+    if z == 0.0:
+        q = 0.5
+    else:
+        q = R * R / (2.0 * eps * d * lambert_w0(z))
+    sigma = math.sqrt(q * eps / 4.0)
+    return float(q), float(sigma)
+
+
+def radius(X: np.ndarray, Y: np.ndarray) -> float:
+    """R = largest Euclidean norm over both clouds, so that both lie in B(0, R).
+
+    Lemma 1 asks for x, y in B(0, R) without saying how R is picked; this is the
+    smallest such R centred at the origin.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    rx = np.sqrt((X * X).sum(axis=1)).max() if X.shape[0] else 0.0
+    ry = np.sqrt((Y * Y).sum(axis=1)).max() if Y.shape[0] else 0.0
+    return float(max(rx, ry))
+
+
+def anchors(Z: np.ndarray, sigma: float) -> np.ndarray:
+    """Anchors u_k ~ N(0, sigma^2 I) from standard normal draws Z (r x d)."""
+    return sigma * np.asarray(Z, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Feature map
+# --------------------------------------------------------------------------
+
+def log_features(P: np.ndarray, U: np.ndarray, eps: float, q: float) -> np.ndarray:
+    """log phi_theta(p)_k for every point p (rows of P) and anchor u_k (rows of U).
+
+    log phi_theta(p)_k = (d/4) log(2q) - (1/2) log r - (2/eps)||p - u_k||^2
+                         + ||u_k||^2/(eps q)
+    (Lemma 1 feature with the proof's constant, scaled by r^{-1/2} as in the
+    definition of phi_theta).  Returns an n x r FP64 array.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    r, d = U.shape
+    diff = P[:, None, :] - U[None, :, :]
+    sq = (diff * diff).sum(axis=2)
+    unorm2 = (U * U).sum(axis=1)
+    return (d / 4.0) * math.log(2.0 * q) - 0.5 * math.log(r) - (2.0 / eps) * sq \
+        + unorm2[None, :] / (eps * q)
+
+
+def features(P, U, eps, q):
+    """phi_theta(p) for every row p of P, as an n x r array (may underflow)."""
+    return np.exp(log_features(P, U, eps, q))
+
+
+def gaussian_kernel(X, Y, eps):
+    """k(x, y) = exp(-||x - y||^2 / eps), the kernel Lemma 1 decomposes."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    diff = X[:, None, :] - Y[None, :, :]
+    return np.exp(-(diff * diff).sum(axis=2) / eps)
+
+
+def lse(A: np.ndarray, axis: int) -> np.ndarray:
+    """log sum exp along an axis, shifted by the maximum so nothing overflows."""
+    mx = A.max(axis=axis, keepdims=True)
+    mx = np.where(np.isfinite(mx), mx, 0.0)
+    out = np.log(np.exp(A - mx).sum(axis=axis, keepdims=True)) + mx
+    return np.squeeze(out, axis=axis)
+
+
+# --------------------------------------------------------------------------
+# Alg. 1 on the factored kernel K = xi zeta^T
+# --------------------------------------------------------------------------
+
+def _log_Kv(Lx, Ly, logv):
+    """log (K v) with K_ij = sum_k exp(Lx_ik + Ly_jk): first zeta^T v, then xi (.)."""
+    lt = lse(Ly + logv[:, None], axis=0)          # log (zeta^T v)_k
+    return lse(Lx + lt[None, :], axis=1), lt      # log (xi (zeta^T v))_i
+
+
+def sinkhorn_log(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray, iters: int,
+                 track_mass: bool = False) -> dict:
+    """Alg. 1 on K = exp(Lx) exp(Ly)^T in the log domain, FP64.
+
+    Starts from v = 1 (log v = 0); each iteration is u <- a/(K v) then
+    v <- b/(K^T u).  Returns log u, log v, the row residual ||u o (K v) - a||_1
+    after the last v-half, and the two r-vectors t_u = log(xi^T u),
+    t_v = log(zeta^T v) of the final state.  With ``track_mass`` the value
+    u^T K v after every half step is recorded (it equals 1 after any update).
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    loga, logb = np.log(a), np.log(b)
+    logu = np.zeros(Lx.shape[0])
+    logv = np.zeros(Ly.shape[0])
+    mass = []
+    for _ in range(iters):
+        logKv, _ = _log_Kv(Lx, Ly, logv)
+        logu = loga - logKv
+        if track_mass:
+            mass.append(float(np.exp(lse(logu + logKv, axis=0))))
+        logKtu, _ = _log_Kv(Ly, Lx, logu)
+        logv = logb - logKtu
+        if track_mass:
+            mass.append(float(np.exp(lse(logv + logKtu, axis=0))))
+    logKv, lt_v = _log_Kv(Lx, Ly, logv)
+    residual = float(np.abs(np.exp(logu + logKv) - a).sum())
+    lt_u = lse(Lx + logu[:, None], axis=0)
+    return {"logu": logu, "logv": logv, "residual": residual, "lt_u": lt_u, "lt_v": lt_v,
+            "mass": mass}
+
+
+def sinkhorn_scaled(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray,
+                    iters: int) -> dict:
+    """The same iterates as ``sinkhorn_log`` in the scaling domain, FP64.
+
+    Rows are shifted by their maxima, xi~ = exp(Lx - mx), zeta~ = exp(Ly - my),
+    so that K = diag(e^mx) xi~ zeta~^T diag(e^my); the shifted scalings
+    u~ = u e^mx, v~ = v e^my then follow u~ = a/(xi~ (zeta~^T v~)),
+    v~ = b/(zeta~ (xi~^T u~)).  v = 1 means v~ = e^my, stored as e^(my - M)
+    with M = max my: a global factor that passes through every update
+    (u~ carries e^M, v~ carries e^-M) and is removed when log u, log v are
+    formed.  Valid while the FP64 range holds (row spread below ~700).
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    mx = Lx.max(axis=1)
+    my = Ly.max(axis=1)
+    Fx = np.exp(Lx - mx[:, None])
+    Fy = np.exp(Ly - my[:, None])
+    M = my.max()
+    v = np.exp(my - M)
+    u = np.zeros(Lx.shape[0])
+    for _ in range(iters):
+        u = a / (Fx @ (Fy.T @ v))
+        v = b / (Fy @ (Fx.T @ u))
+    s = Fx @ (Fy.T @ v)
+    residual = float(np.abs(u * s - a).sum())
+    logu = np.log(u) - mx - M
+    logv = np.log(v) - my + M
+    return {"logu": logu, "logv": logv, "residual": residual}
+
+
+def sinkhorn_dense(K: np.ndarray, a: np.ndarray, b: np.ndarray, iters: int) -> dict:
+    """Textbook Alg. 1 on an explicit positive matrix K (tiny n only), FP64."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    v = np.ones(K.shape[1])
+    u = np.ones(K.shape[0])
+    for _ in range(iters):
+        u = a / (K @ v)
+        v = b / (K.T @ u)
+    residual = float(np.abs(u * (K @ v) - a).sum())
+    return {"u": u, "v": v, "logu": np.log(u), "logv": np.log(v), "residual": residual}
+
+
+def dual_estimate(a, b, logu, logv, eps: float) -> float:
+    """Eq. (6): W_hat = eps (a^T log u + b^T log v)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(eps * (a @ logu + b @ logv))
+
+
+def dual_objective(a, b, logu, logv, logK: np.ndarray, eps: float) -> float:
+    """Eq. (5) objective at alpha = eps log u, beta = eps log v (dense K, tiny n)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    mass = np.exp(logu[:, None] + logK + logv[None, :]).sum()
+    return float(eps * (a @ logu) + eps * (b @ logv) - eps * mass + eps)
+
+
+def primal_objective(logu, logv, logK: np.ndarray, eps: float) -> float:
+    """Eq. (3) objective <P, C> - eps H(P) + eps at P = diag(u) K diag(v).
+
+    C = -eps log K (Eq. 7 with K = K_theta) and H(P) = -sum P (log P - 1).
+    """
+    logP = logu[:, None] + logK + logv[None, :]
+    P = np.exp(logP)
+    C = -eps * logK
+    H = -(P * (logP - 1.0)).sum()
+    return float((P * C).sum() - eps * H + eps)
+
+
+# --------------------------------------------------------------------------
+# Full path: theta, W, debiased W_bar
+# --------------------------------------------------------------------------
+
+class Theta:
+    """Frozen feature parameters theta = (q, U) shared by all terms of Eq. (2)."""
+
+    def __init__(self, q: float, sigma: float, U: np.ndarray, eps: float, R: float):
+        self.q, self.sigma, self.U, self.eps, self.R = q, sigma, U, eps, R
+
+
+def make_theta(X, Y, Z, eps: float) -> Theta:
+    """R from both clouds, (q, sigma) from Lemma 1, anchors U = sigma Z."""
+    R = radius(X, Y)
+    d = np.asarray(X).shape[1]
+    q, sigma = gaussian_params(R, eps, d)
+    return Theta(q, sigma, anchors(Z, sigma), eps, R)
+
+
+def solve(Lx, Ly, a, b, iters, mode="log"):
+    if mode == "log":
+        return sinkhorn_log(Lx, Ly, a, b, iters)
+    if mode == "scaled":
+        return sinkhorn_scaled(Lx, Ly, a, b, iters)
+    raise ValueError(mode)
+
+
+def divergence(X, Y, a, b, Z=None, eps=None, iters=100, theta: Theta | None = None,
+               debiased: bool = True, mode: str = "log") -> dict:
+    """W(a,b) and, if asked, W(a,a), W(b,b) and W_bar (Eq. 2) with one theta.
+
+    theta is computed from (X, Y, Z, eps) unless given (it is given, frozen,
+    when differentiating).
+    """
+    if theta is None:
+        theta = make_theta(X, Y, Z, eps)
+    eps = theta.eps
+    Lx = log_features(X, theta.U, eps, theta.q)
+    Ly = log_features(Y, theta.U, eps, theta.q)
+    out = {"theta": theta}
+    sxy = solve(Lx, Ly, a, b, iters, mode)
+    out["xy"] = sxy
+    out["W_xy"] = dual_estimate(a, b, sxy["logu"], sxy["logv"], eps)
+    out["res_xy"] = sxy["residual"]
+    if debiased:
+        sxx = solve(Lx, Lx, a, a, iters, mode)
+        syy = solve(Ly, Ly, b, b, iters, mode)
+        out["xx"], out["yy"] = sxx, syy
+        out["W_xx"] = dual_estimate(a, a, sxx["logu"], sxx["logv"], eps)
+        out["W_yy"] = dual_estimate(b, b, syy["logu"], syy["logv"], eps)
+        out["res_xx"], out["res_yy"] = sxx["residual"], syy["residual"]
+        out["W_bar"] = out["W_xy"] - 0.5 * (out["W_xx"] + out["W_yy"])
+    return out
+
+
+# --------------------------------------------------------------------------
+# Envelope gradient (Prop. 3.3 and the chain rule of Sec. 3.3)
+# --------------------------------------------------------------------------
+
+def _grad_points(P, U, L, logu, lt):
+    """sum_k exp(log u_i + L_ik + lt_k) * 4 (p_i - u_k), for every row p_i.
+
+    This is -eps sum_k u_i (zeta^T v)_k d xi_ik / d p_i with
+    d xi_ik / d p_i = xi_ik * (-4/eps)(p_i - u_k).
+    """
+    Mass = np.exp(logu[:, None] + L + lt[None, :])
+    return 4.0 * (Mass.sum(axis=1)[:, None] * P - Mass @ U)
+
+
+def gradient(X, Y, a, b, theta: Theta, state: dict, debiased: bool = True) -> dict:
+    """Envelope gradient of W (or W_bar) w.r.t. X, Y, a, b, theta held fixed.
+
+    For W(a,b): dW/dK = -eps u v^T (Prop. 3.3), K = xi zeta^T, so
+      grad_X = -eps (d xi/dX)^T u (zeta^T v)^T  (formula after Prop. 3.3),
+      grad_Y = -eps (d zeta/dY)^T v (xi^T u)^T,
+      grad_a = eps log u, grad_b = eps log v  (alpha* = eps log u*, Eq. 5).
+    For W(a,a) the kernel is xi xi^T, so X enters both factors:
+      dW/dxi = -eps (u (xi^T v)^T + v (xi^T u)^T), grad_a = eps (log u + log v).
+    ``state`` is the output of ``divergence``; the potentials are those of its
+    final iterate.  Gradients w.r.t. weights are defined up to a constant.
+    """
+    eps = theta.eps
+    U = theta.U
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    Lx = log_features(X, U, eps, theta.q)
+    Ly = log_features(Y, U, eps, theta.q)
+    s = state["xy"]
+    lt_v = lse(Ly + s["logv"][:, None], axis=0)     # log zeta^T v
+    lt_u = lse(Lx + s["logu"][:, None], axis=0)     # log xi^T u
+    gX = _grad_points(X, U, Lx, s["logu"], lt_v)
+    gY = _grad_points(Y, U, Ly, s["logv"], lt_u)
+    ga = eps * s["logu"]
+    gb = eps * s["logv"]
+    out = {"W": {"X": gX, "Y": gY, "a": ga, "b": gb}}
+    if debiased:
+        gx_xx, ga_xx = _grad_self(X, U, Lx, state["xx"], eps)
+        gy_yy, gb_yy = _grad_self(Y, U, Ly, state["yy"], eps)
+        out["W_bar"] = {"X": gX - 0.5 * gx_xx, "Y": gY - 0.5 * gy_yy,
+                        "a": ga - 0.5 * ga_xx, "b": gb - 0.5 * gb_yy}
+    return out
+
+
+def _grad_self(P, U, L, s, eps):
+    """Gradient of W(w,w) on one cloud (kernel xi xi^T) w.r.t. its points and weights."""
+    lt_v = lse(L + s["logv"][:, None], axis=0)
+    lt_u = lse(L + s["logu"][:, None], axis=0)
+    g = _grad_points(P, U, L, s["logu"], lt_v) + _grad_points(P, U, L, s["logv"], lt_u)
+    return g, eps * (s["logu"] + s["logv"])
+
+
+def deviation(rot: float, rot_hat: float) -> float:
+    """Deviation from ground truth used in Sec. 4: D = 100 (ROT - ROT_hat)/|ROT| + 100."""
+    return 100.0 * (rot - rot_hat) / abs(rot) + 100.0

@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a library
+routine, a closed form, an identity from a proof, an invariant, an independent
+optimiser, or brute force.  Together they are meant to catch a dropped term, a
+wrong sign or index, or a transposed operand anywhere in the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize
+import scipy.special
+
+from oracle import oracle as o
+import synth
+
+
+def _tiny_factors(seed=0, n=7, m=5, r=3, d=2, eps=0.5):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)) * 0.5
+    Y = rng.standard_normal((m, d)) * 0.5 + 0.3
+    Z = rng.standard_normal((r, d))
+    a = rng.exponential(size=n); a /= a.sum()
+    b = rng.exponential(size=m); b /= b.sum()
+    th = o.make_theta(X, Y, Z, eps)
+    Lx = o.log_features(X, th.U, eps, th.q)
+    Ly = o.log_features(Y, th.U, eps, th.q)
+    return X, Y, Z, a, b, th, Lx, Ly
+
+
+# ---------------------------------------------------------------- Lambert W0
+
+def test_lambert_w0_matches_scipy():
+    z = np.concatenate([[0.0, 1e-300, 1e-12, math.e], np.logspace(-8, 12, 200)])
+    w = o.lambert_w0(z)
+    ref = scipy.special.lambertw(z, 0).real
+    np.testing.assert_allclose(w, ref, rtol=2e-15, atol=1e-300)
+
+
+def test_lambert_w0_special_values_and_identity():
+    assert o.lambert_w0(0.0) == 0.0
+    assert abs(o.lambert_w0(math.e) - 1.0) < 1e-15
+    z = np.logspace(-6, 8, 57)
+    w = o.lambert_w0(z)
+    np.testing.assert_allclose(w * np.exp(w), z, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- Lemma 1 q, sigma
+
+@pytest.mark.parametrize("R,eps,d", [(1.0, 0.5, 2), (1.73, 0.1, 3), (14.5, 1.0, 128), (3.0, 0.05, 16)])
+def test_q_satisfies_lambert_characterisation(R, eps, d):
+    # q = z/(2 W0(z)) with z = R^2/(eps d) means 2q = e^{W0(z)}, i.e. 2q log(2q) = z.
+    q, sigma = o.gaussian_params(R, eps, d)
+    z = R * R / (eps * d)
+    assert abs(2 * q * math.log(2 * q) - z) <= 1e-13 * max(1.0, z)
+    assert q > 0.5
+    assert abs(sigma * sigma - q * eps / 4) <= 1e-15 * q * eps
+
+
+def test_q_limit_small_radius():
+    q0, _ = o.gaussian_params(0.0, 0.5, 2)
+    q1, _ = o.gaussian_params(1e-6, 0.5, 2)
+    assert q0 == 0.5 and abs(q1 - 0.5) < 1e-10
+
+
+# ---------------------------------------------------------------- feature map
+
+@pytest.mark.parametrize("d,eps", [(2, 0.5), (3, 0.1), (16, 1.0)])
+def test_feature_product_identity_from_proof(d, eps):
+    # Proof of Lemma 1: phi(x,u) phi(y,u) = (2q)^{d/2} k(x,y)
+    #   exp(-4||u - (x+y)/2||^2/eps) exp(2||u||^2/(eps q)), pointwise in u.
+    rng = np.random.default_rng(d)
+    X = rng.standard_normal((9, d)) * 0.4
+    Y = rng.standard_normal((9, d)) * 0.4
+    q, sigma = o.gaussian_params(o.radius(X, Y), eps, d)
+    U = sigma * rng.standard_normal((1, d))          # r = 1: phi_theta = phi
+    lx = o.log_features(X, U, eps, q)[:, 0]
+    ly = o.log_features(Y, U, eps, q)[:, 0]
+    u = U[0]
+    mid = 0.5 * (X + Y)
+    rhs = (d / 2) * math.log(2 * q) - ((X - Y) ** 2).sum(1) / eps \
+        - 4.0 * ((u - mid) ** 2).sum(1) / eps + 2.0 * (u @ u) / (eps * q)
+    np.testing.assert_allclose(lx + ly, rhs, rtol=1e-13, atol=1e-12)
+
+
+def test_features_scale_with_r():
+    # phi_theta = r^{-1/2}(phi(x,u_1),...): duplicating every anchor halves each
+    # squared entry, so k_theta is unchanged.
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((4, 2)); Y = rng.standard_normal((5, 2))
+    U = rng.standard_normal((6, 2)) * 0.3
+    q = 0.9
+    k1 = o.features(X, U, 0.5, q) @ o.features(Y, U, 0.5, q).T
+    U2 = np.concatenate([U, U])
+    k2 = o.features(X, U2, 0.5, q) @ o.features(Y, U2, 0.5, q).T
+    np.testing.assert_allclose(k1, k2, rtol=1e-13)
+
+
+def test_monte_carlo_unbiased_gaussian_kernel():
+    # E_rho[phi(x,u) phi(y,u)] = k(x,y) for u ~ N(0, q eps/4 I) (Lemma 1).
+    rng = np.random.default_rng(11)
+    d, eps, r = 2, 0.5, 400_000
+    X = rng.standard_normal((6, d)) * 0.4
+    Y = rng.standard_normal((6, d)) * 0.4
+    q, sigma = o.gaussian_params(o.radius(X, Y), eps, d)
+    U = sigma * rng.standard_normal((r, d))
+    Lx = o.log_features(X, U, eps, q) + 0.5 * math.log(r)   # per-anchor phi(x,u_k)
+    Ly = o.log_features(Y, U, eps, q) + 0.5 * math.log(r)
+    k = o.gaussian_kernel(X, Y, eps)
+    for i in range(X.shape[0]):
+        samples = np.exp(Lx[i][None, :] + Ly) / k[i][:, None]     # ratio per anchor, mean 1
+        mean = samples.mean(axis=1)
+        se = samples.std(axis=1) / math.sqrt(r)
+        assert np.all(np.abs(mean - 1.0) < 6 * se + 1e-12), (mean, se)
+
+
+def test_monte_carlo_rate_is_inverse_sqrt_r():
+    # Prop. 3.2: the ratio error of k_theta vs k shrinks like r^{-1/2}.
+    d, eps = 2, 1.0
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((5, d)) * 0.3
+    Y = rng.standard_normal((5, d)) * 0.3
+    q, sigma = o.gaussian_params(o.radius(X, Y), eps, d)
+    k = o.gaussian_kernel(X, Y, eps)
+    rs = [100, 1000, 10000, 100000]
+    errs = []
+    for r in rs:
+        e = []
+        for s in range(12):
+            U = sigma * np.random.default_rng([r, s]).standard_normal((r, d))
+            kt = o.features(X, U, eps, q) @ o.features(Y, U, eps, q).T
+            e.append(np.sqrt(np.mean((kt / k - 1.0) ** 2)))
+        errs.append(np.mean(e))
+    slope = np.polyfit(np.log(rs), np.log(errs), 1)[0]
+    assert -0.62 < slope < -0.38, (slope, errs)
+
+
+# ---------------------------------------------------------------- Alg. 1
+
+def test_factored_log_matches_dense_textbook():
+    X, Y, Z, a, b, th, Lx, Ly = _tiny_factors()
+    K = np.exp(Lx) @ np.exp(Ly).T                       # K_theta = xi^T zeta (Sec. 3.1)
+    for iters in (1, 2, 7, 40):
+        sd = o.sinkhorn_dense(K, a, b, iters)
+        sl = o.sinkhorn_log(Lx, Ly, a, b, iters)
+        np.testing.assert_allclose(sl["logu"], sd["logu"], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(sl["logv"], sd["logv"], rtol=1e-12, atol=1e-12)
+        assert abs(sl["residual"] - sd["residual"]) < 1e-13
+
+
+def test_scaled_matches_log():
+    p = synth.tiny_problem(n=300, m=250, r=40, iters=30)
+    th = o.make_theta(p.X, p.Y, p.Z, p.eps)
+    Lx = o.log_features(p.X, th.U, p.eps, th.q)
+    Ly = o.log_features(p.Y, th.U, p.eps, th.q)
+    sl = o.sinkhorn_log(Lx, Ly, p.a, p.b, p.iters)
+    ss = o.sinkhorn_scaled(Lx, Ly, p.a, p.b, p.iters)
+    np.testing.assert_allclose(ss["logu"], sl["logu"], rtol=1e-11, atol=1e-10)
+    np.testing.assert_allclose(ss["logv"], sl["logv"], rtol=1e-11, atol=1e-10)
+    assert abs(ss["residual"] - sl["residual"]) < 1e-12
+
+
+def test_mass_is_one_after_every_half_step():
+    # Sec. 2: u^T K v = 1 whenever the loop has been applied once (weights sum to 1).
+    *_, a, b, th, Lx, Ly = _tiny_factors(seed=2)
+    s = o.sinkhorn_log(Lx, Ly, a, b, 15, track_mass=True)
+    np.testing.assert_allclose(s["mass"], 1.0, rtol=1e-13)
+
+
+def test_column_marginal_exact_after_v_half_and_rows_converge():
+    *_, a, b, th, Lx, Ly = _tiny_factors(seed=4)
+    K = np.exp(Lx) @ np.exp(Ly).T
+    for iters, tol in ((3, None), (4000, 1e-12)):
+        s = o.sinkhorn_log(Lx, Ly, a, b, iters)
+        P = np.exp(s["logu"][:, None] + np.log(K) + s["logv"][None, :])
+        np.testing.assert_allclose(P.sum(0), b, rtol=1e-12)          # v-half makes P^T 1 = b
+        assert abs(np.abs(P.sum(1) - a).sum() - s["residual"]) < 1e-13
+        if tol:
+            assert s["residual"] < tol
+
+
+def test_dual_estimate_equals_primal_and_dual_at_convergence():
+    # Eq. (3) primal, Eq. (5) dual objective and Eq. (6) estimate coincide at the optimum.
+    *_, a, b, th, Lx, Ly = _tiny_factors(seed=6)
+    eps = th.eps
+    logK = np.log(np.exp(Lx) @ np.exp(Ly).T)
+    s = o.sinkhorn_log(Lx, Ly, a, b, 5000)
+    w6 = o.dual_estimate(a, b, s["logu"], s["logv"], eps)
+    w5 = o.dual_objective(a, b, s["logu"], s["logv"], logK, eps)
+    w3 = o.primal_objective(s["logu"], s["logv"], logK, eps)
+    assert abs(w6 - w5) < 1e-12 and abs(w6 - w3) < 1e-10
+
+
+def test_dual_estimate_matches_independent_lbfgs_optimum():
+    # Maximise the Eq. (5) objective directly with a generic optimiser.
+    *_, a, b, th, Lx, Ly = _tiny_factors(seed=8)
+    eps = th.eps
+    K = np.exp(Lx) @ np.exp(Ly).T
+    n, m = K.shape
+
+    def negf(z):
+        al, be = z[:n], z[n:]
+        E = np.exp(al / eps)[:, None] * K * np.exp(be / eps)[None, :]
+        f = a @ al + b @ be - eps * E.sum() + eps
+        g = np.concatenate([a - E.sum(1), b - E.sum(0)])
+        return -f, -g
+
+    res = scipy.optimize.minimize(negf, np.zeros(n + m), jac=True, method="L-BFGS-B",
+                                  options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 20000})
+    s = o.sinkhorn_log(Lx, Ly, a, b, 5000)
+    w = o.dual_estimate(a, b, s["logu"], s["logv"], eps)
+    assert abs(-res.fun - w) < 1e-9 * max(1.0, abs(w))
+
+
+def test_rank_one_closed_form():
+    # r = 1: after one iteration P = a b^T and
+    # W = eps [sum a log a - sum a log xi + sum b log b - sum b log zeta].
+    rng = np.random.default_rng(9)
+    Lx = rng.standard_normal((6, 1)); Ly = rng.standard_normal((4, 1))
+    a = rng.exponential(size=6); a /= a.sum()
+    b = rng.exponential(size=4); b /= b.sum()
+    eps = 0.7
+    s = o.sinkhorn_log(Lx, Ly, a, b, 1)
+    w = o.dual_estimate(a, b, s["logu"], s["logv"], eps)
+    closed = eps * (a @ np.log(a) - a @ Lx[:, 0] + b @ np.log(b) - b @ Ly[:, 0])
+    assert abs(w - closed) < 1e-13
+    assert s["residual"] < 1e-15
+
+
+def test_single_point_gives_the_cost():
+    # n = m = 1: W = -eps log k_theta(x, y) = c_theta(x, y) (Eq. 7).
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((1, 3)); Y = rng.standard_normal((1, 3))
+    Z = rng.standard_normal((17, 3))
+    eps = 0.8
+    out = o.divergence(X, Y, np.ones(1), np.ones(1), Z, eps, iters=3, debiased=False)
+    th = out["theta"]
+    k = (o.features(X, th.U, eps, th.q) @ o.features(Y, th.U, eps, th.q).T)[0, 0]
+    assert abs(out["W_xy"] - (-eps * math.log(k))) < 1e-12
+
+
+def test_debiased_divergence_of_identical_measures_is_zero():
+    p = synth.small_problem(1, 200, 200, 2, 30, 0.3, 20, weights="dirichlet")
+    out = o.divergence(p.X, p.X.copy(), p.a, p.a.copy(), p.Z, p.eps, p.iters)
+    assert abs(out["W_bar"]) < 1e-12 * (abs(out["W_xy"]) + 1)
+
+
+def test_translation_moves_only_the_anchor_weights():
+    # Moving points and anchors together leaves every ||p - u_k|| unchanged, so the
+    # log-features change only through the per-anchor term ||u_k||^2/(eps q).
+    p = synth.small_problem(2, 60, 70, 3, 20, 0.4, 25)
+    th = o.make_theta(p.X, p.Y, p.Z, p.eps)
+    shift = np.array([0.3, -1.1, 2.0])
+    U2 = th.U + shift
+    corr = ((U2 ** 2).sum(1) - (th.U ** 2).sum(1)) / (p.eps * th.q)
+    for P in (p.X, p.Y):
+        L = o.log_features(P, th.U, p.eps, th.q)
+        L2 = o.log_features(P + shift, U2, p.eps, th.q)
+        np.testing.assert_allclose(L2 - corr[None, :], L, rtol=1e-12, atol=1e-10)
+    # the anchor weights do matter: moving the points alone (theta recomputed) changes W
+    base = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=False)
+    moved = o.divergence(p.X + 5.0, p.Y + 5.0, p.a, p.b, p.Z, p.eps, p.iters, debiased=False)
+    assert abs(moved["W_xy"] - base["W_xy"]) > 1e-6
+
+
+def test_permutation_invariance():
+    p = synth.small_problem(3, 50, 40, 2, 25, 0.5, 30, weights="dirichlet")
+    base = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters)
+    pi = np.random.default_rng(0).permutation(p.n)
+    pj = np.random.default_rng(1).permutation(p.m)
+    perm = o.divergence(p.X[pi], p.Y[pj], p.a[pi], p.b[pj], p.Z, p.eps, p.iters)
+    for key in ("W_xy", "W_xx", "W_yy", "W_bar"):
+        assert abs(perm[key] - base[key]) < 1e-12 * max(1, abs(base[key]))
+
+
+def test_kernel_approximation_improves_with_r():
+    # Sec. 4 deviation D against dense Sinkhorn with the true Gaussian kernel.
+    rng = np.random.default_rng(12)
+    n, d, eps = 40, 2, 1.0
+    X = rng.standard_normal((n, d)) * 0.5
+    Y = rng.standard_normal((n, d)) * 0.3 + 0.5
+    a = np.full(n, 1.0 / n); b = np.full(n, 1.0 / n)
+    Kt = o.gaussian_kernel(X, Y, eps)
+    sd = o.sinkhorn_dense(Kt, a, b, 500)
+    rot = o.dual_estimate(a, b, sd["logu"], sd["logv"], eps)
+    devs = {}
+    for r in (30, 3000, 100000):
+        ds = []
+        for s in range(4):
+            Z = np.random.default_rng([r, s]).standard_normal((r, d))
+            out = o.divergence(X, Y, a, b, Z, eps, iters=500, debiased=False, mode="scaled")
+            ds.append(abs(o.deviation(rot, out["W_xy"]) - 100.0))
+        devs[r] = np.mean(ds)
+    assert devs[100000] < devs[3000] < devs[30], devs
+    assert devs[100000] < 1.0
+
+
+# ---------------------------------------------------------------- gradient
+
+def _fd_problem():
+    rng = np.random.default_rng(13)
+    n, m, d, r, eps = 6, 5, 2, 7, 0.5
+    X = rng.standard_normal((n, d)) * 0.5
+    Y = rng.standard_normal((m, d)) * 0.5 + 0.2
+    Z = rng.standard_normal((r, d))
+    a = rng.exponential(size=n); a /= a.sum()
+    b = rng.exponential(size=m); b /= b.sum()
+    th = o.make_theta(X, Y, Z, eps)
+    return X, Y, a, b, th
+
+
+@pytest.mark.parametrize("debiased", [False, True])
+def test_envelope_gradient_matches_central_differences(debiased):
+    X, Y, a, b, th = _fd_problem()
+    iters = 1500
+    key = "W_bar" if debiased else "W_xy"
+    st = o.divergence(X, Y, a, b, theta=th, iters=iters, debiased=debiased)
+    g = o.gradient(X, Y, a, b, th, st, debiased=debiased)["W_bar" if debiased else "W"]
+
+    def W(X_, Y_, a_, b_):
+        return o.divergence(X_, Y_, a_, b_, theta=th, iters=iters, debiased=debiased)[key]
+
+    h = 1e-5
+    for (name, arr) in (("X", X), ("Y", Y)):
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            e = np.zeros_like(arr); e[idx] = h
+            args_p = [X, Y, a, b]; args_m = [X, Y, a, b]
+            k = 0 if name == "X" else 1
+            args_p[k] = arr + e; args_m[k] = arr - e
+            fd[idx] = (W(*args_p) - W(*args_m)) / (2 * h)
+        np.testing.assert_allclose(g[name], fd, rtol=1e-6, atol=1e-8)
+    # weights: only zero-sum (simplex tangent) directions are meaningful; the
+    # O(h^2) truncation error grows like 1/a_i^2, so use a smaller step here
+    h = 2e-6
+    for (name, w) in (("a", a), ("b", b)):
+        for (i, j) in ((0, 1), (2, 4), (3, 0)):
+            e = np.zeros_like(w); e[i] = h; e[j] = -h
+            if name == "a":
+                fd = (W(X, Y, a + e, b) - W(X, Y, a - e, b)) / (2 * h)
+            else:
+                fd = (W(X, Y, a, b + e) - W(X, Y, a, b - e)) / (2 * h)
+            assert abs((g[name][i] - g[name][j]) - fd) < 1e-8 * max(1.0, abs(fd))
