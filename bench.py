@@ -1,0 +1,325 @@
+"""Benchmark: Sinkhorn n*r entry-updates per second on the large two-cloud workload.
+
+Workload (one step = the whole hot path once): n = m = 2^20 points in R^3, X
+uniform on the unit cube, Y ~ N(0.5*1, 0.1^2 I), uniform weights, eps = 0.1,
+r = 1024 Gaussian positive features (Lemma 1), 200 iterations of Alg. 1 for
+each of the three solves of the debiased divergence (Eq. 2), stored features.
+A step runs: radius, Lemma 1 parameters, anchors, features of both clouds, the
+lock-step debiased solve, residuals and the Eq. (6)/(2) reductions.
+
+Updates per step = iters * 3 * (n + m) * r  (each feature entry used once per
+half-iteration of each of the three solves).
+
+Output: one JSON line. ``value`` is device-timed with inputs resident in HBM;
+``e2e`` times the same call from pinned host buffers, including the copies in
+and the read-back of the result. ``roofline`` reports the dominant kernel (the
+fused pass) against the measured HBM copy bandwidth. ``cpu_baseline`` times the
+FP64 oracle on a bounded sample of the same workload on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Sinkhorn n*r updates/s & %HBM roofline; batched/served solves/s, p99 vs plain"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="stored", choices=["stored", "recompute"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing
+
+def oracle_sample(n_sample: int, iters: int) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload (host cores)."""
+    from oracle import oracle as o
+    p = synth.large_problem(seed=0, n=n_sample, iters=iters)
+    t0 = time.perf_counter()
+    o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=True, mode="scaled")
+    dt = time.perf_counter() - t0
+    updates = iters * 3 * (p.n + p.m) * p.r
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        nt = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if nt:
+            cores = int(max(nt))
+    except Exception:
+        pass
+    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle (scaling-domain mode, numpy BLAS) on n=m={n_sample} points "
+                      f"of the same distributions, r={p.r}, eps={p.eps}, {iters} iterations, "
+                      f"debiased (3 solves): {dt:.2f} s"}
+
+
+# ---------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    iters = 20
+    n_sample = 1 << 13
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(n_sample, iters)
+    for _ in range(args.steps):
+        vals.append(oracle_sample(n_sample, iters))
+    value = statistics.median(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"large two-cloud: n=m={args.n}, d=3, X~U[0,1]^3 vs Y~N(0.5,0.1^2 I), "
+                        f"uniform weights, eps=0.1, r=1024 Gaussian features, {args.iters} "
+                        f"iterations, debiased (Eq. 2), {args.mode} features",
+            "n": args.n, "m": args.n, "d": 3, "r": 1024, "eps": 0.1, "iters": args.iters,
+            "debiased": True, "mode": args.mode,
+            "l2": "inputs larger than L2 (two 4 GiB feature matrices streamed every pass)",
+            "parallelism": f"replicas x{args.gpus} (independent problems, no collective)"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2006_07057_gb300 as lsf
+    lsf.lib()
+
+    p = synth.large_problem(seed=rank, n=args.n, iters=args.iters)
+    updates = args.iters * 3 * (p.n + p.m) * p.r
+    dev = torch.device("cuda", local)
+    host = {k: torch.from_numpy(getattr(p, k)).pin_memory() for k in ("X", "Y", "a", "b", "Z")}
+    devt = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+    stream = torch.cuda.current_stream()
+
+    def step_resident():
+        prob = lsf.SinkhornProblem(devt["X"], devt["Y"], devt["a"], devt["b"], devt["Z"], p.eps,
+                                   mode=args.mode)
+        prob.run(args.iters, debiased=True)
+        return prob
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        prob = step_resident()
+    torch.cuda.synchronize()
+    check = prob.values()
+    if check["status"] != 0 or not np.isfinite(check["W_bar"]):
+        raise SystemExit(f"solver reported status {check['status']}, W_bar {check['W_bar']}")
+
+    # ---- device-timed region, inputs resident
+    sampler = ClockSampler(local)
+    sampler.start()
+    lsf.lsf_profile_enable(True)
+    lsf.lsf_launch_count_reset()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        prob = step_resident()
+    e1.record(stream)
+    barrier()
+    launches = lsf.lsf_launch_count()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    pass_ms, pass_n, pass_bytes = lsf.lsf_profile_read(lsf.LSF_KERNEL_PASS)
+    feat_ms, feat_n, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
+    lsf.lsf_profile_enable(False)
+    vals = prob.values()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = updates * world / (ms / 1e3)
+
+    # ---- end to end from pinned host buffers through the public API
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+
+        def step_e2e():
+            d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            pr = lsf.SinkhornProblem(d["X"], d["Y"], d["a"], d["b"], d["Z"], p.eps, mode=args.mode)
+            pr.run(args.iters, debiased=True)
+            out_host.copy_(pr.wbar, non_blocking=True)
+            return pr
+
+        step_e2e()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        f1.record(stream)
+        barrier()
+        ms_e2e = f0.elapsed_time(f1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": updates * world / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+
+    peak, peak_kind = load_peaks()
+    achieved = (pass_bytes / 1e9) / (pass_ms / 1e3) if pass_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "pass_kernel (fused Sinkhorn half-iteration)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "traffic": None,
+                "launches": pass_n, "avg_launch_ms": pass_ms / max(pass_n, 1),
+                "bytes_per_launch": pass_bytes / max(pass_n, 1),
+                "share_of_step": pass_ms / (ms * args.steps) if ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(1 << 13, 20)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args), "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "result": {"W_bar": vals["W_bar"], "W_xy": vals["W_xy"], "res_xy": vals["res_xy"],
+                       "status": vals["status"]},
+            "features_ms_per_step": feat_ms / args.steps,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

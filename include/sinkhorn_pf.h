@@ -1,0 +1,240 @@
+/*
+ * sinkhorn_pf.h -- C ABI of libsinkhorn_pf.so, a GB300 (sm_103a) implementation of
+ * linear-time Sinkhorn divergences with positive features (Scetbon & Cuturi,
+ * arXiv 2006.07057).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All functions return an int status (lsf_status). They never abort or throw.
+ *    On failure lsf_last_error() returns a message for the calling thread.
+ *  - "device" pointers are CUDA global-memory pointers owned by the caller; the
+ *    library never allocates, frees or keeps them. "host" pointers are plain
+ *    host memory. Every device call is asynchronous on the given CUDA stream
+ *    (a cudaStream_t passed as void*; NULL is the legacy default stream).
+ *  - Floating point data is FP32, row-major, contiguous. Points are n x d.
+ *  - Features are stored point-major: F is n x ldr with F[i*ldr + k] the k-th
+ *    shifted feature of point i (the transpose of the paper's r x n xi).
+ *    ldr >= r, ldr % 4 == 0, ldr <= 1024; columns r..ldr-1 hold zeros.
+ *  - Row shifts: shift[i] = max_k log phi_theta(x_i)_k, and F holds
+ *    phi_theta(x_i)_k * exp(-shift[i]), so every stored row has maximum 1.
+ *  - Scalings are stored shifted: u~_i = u_i exp(shift_x[i]) * exp(M) and
+ *    v~_j = v_j exp(shift_y[j]) * exp(-M), where M = max_j shift_y[j] is the
+ *    global factor fixed at start (lsf_result.log_scale). Hence
+ *      log u_i = log u~_i - shift_x[i] - M,   log v_j = log v~_j - shift_y[j] + M.
+ *  - Device-side failures (a non-finite scaling, a bounded wait that ran out)
+ *    are reported in lsf_result.status on the device; host-side checks
+ *    (arguments, launch errors) in the return value.
+ *  - Sizes: a measure has at least one point (n >= 1); empty measures are an
+ *    argument error (LSF_ERR_ARG).
+ */
+#ifndef SINKHORN_PF_H
+#define SINKHORN_PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSF_OK = 0,
+  LSF_ERR_ARG = 1,         /* invalid argument: NULL pointer, bad size, misalignment  */
+  LSF_ERR_NONFINITE = 2,   /* a scaling became 0, inf or NaN (device status bit)       */
+  LSF_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out (device status bit)   */
+  LSF_ERR_WORKSPACE = 8,   /* workspace smaller than lsf_workspace_bytes() asks for    */
+  LSF_ERR_CUDA = 16,       /* a CUDA runtime call or launch failed                     */
+  LSF_ERR_UNSUPPORTED = 32 /* a size outside what the kernels handle                   */
+} lsf_status;
+
+/* Solver variants for the fused passes of Alg. 1 (Sec. 2) on K = xi zeta^T (Sec. 3.1). */
+typedef enum {
+  LSF_MODE_STORED = 0,     /* stream stored shifted features F (HBM-bound)            */
+  LSF_MODE_RECOMPUTE = 1   /* recompute features from X, U in registers (ALU-bound)   */
+} lsf_mode;
+
+/* Feature parameters theta = (U, c), shared by every term of Eq. (2). Device pointers. */
+typedef struct {
+  const float* U;   /* r x d anchors u_k (Lemma 1: u_k ~ N(0, sigma^2 I))                */
+  const float* c;   /* r per-anchor log-constants
+                       c_k = (d/4) log(2q) - (1/2) log r + ||u_k||^2 / (eps q)            */
+  int r;            /* number of features, 1 <= r <= ldr                                  */
+  int ldr;          /* row stride of stored features (multiple of 4, <= 1024)             */
+  int d;            /* dimension of the points, 1 <= d                                    */
+  double eps;       /* entropic regularisation eps > 0                                    */
+} lsf_theta;
+
+/* One weighted point cloud with its features. Device pointers. */
+typedef struct {
+  const float* X;      /* n x d points (needed by RECOMPUTE and by the gradient)         */
+  const float* F;      /* n x ldr shifted features (needed by STORED; may be NULL else)  */
+  const float* shift;  /* n row log-shifts                                               */
+  const float* w;      /* n positive weights (a or b)                                    */
+  int64_t n;           /* number of points, >= 1                                         */
+} lsf_cloud;
+
+/* Outputs of one solve: shifted scalings and the two r-vectors of the last state. */
+typedef struct {
+  float* u;     /* n   u~ (see conventions)                                               */
+  float* v;     /* m   v~                                                                 */
+  float* t_u;   /* ldr xi~^T u~   (zero beyond r)                                         */
+  float* t_v;   /* ldr zeta~^T v~ (zero beyond r)                                         */
+} lsf_scalings;
+
+/* Device-resident result record of one solve (caller allocates sizeof(lsf_result)). */
+typedef struct {
+  double W;          /* Eq. (6) estimate eps (a^T log u + b^T log v); set by lsf_divergence  */
+  double residual;   /* ||u o (K v) - a||_1 after the last v-half (Alg. 1 stopping quantity)  */
+  double log_scale;  /* M, the global factor of the scalings (see conventions)                */
+  int32_t status;    /* OR of device-side status bits (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT)    */
+  int32_t iters;     /* iterations run                                                         */
+} lsf_result;
+
+/* ---------------------------------------------------------------- library */
+
+/* ABI version of this header (increments on any incompatible change). */
+int lsf_version(void);
+
+/* Last error message of the calling host thread ("" if none). Never NULL. */
+const char* lsf_last_error(void);
+
+/* ---------------------------------------------------------------- host math */
+
+/*
+ * Lemma 1 (Sec. 3.2): q = R^2 / (2 eps d W0(R^2/(eps d))) with W0 the principal
+ * Lambert branch, sigma = sqrt(q eps / 4). R = 0 gives the limit q = 1/2.
+ * Host only. Errors: LSF_ERR_ARG if eps <= 0, d < 1, R < 0 or R not finite,
+ * or q/sigma NULL.
+ */
+int lsf_gaussian_params(double R, double eps, int d, double* q, double* sigma);
+
+/* ---------------------------------------------------------------- features */
+
+/*
+ * R for Lemma 1: the largest Euclidean norm over the rows of X (n x d) and
+ * Y (m x d), written as one float to device R_out. Lemma 1 needs x, y in
+ * B(0, R); this is the smallest such ball centred at 0.
+ */
+int lsf_radius(const float* X, int64_t n, const float* Y, int64_t m, int d,
+               float* R_out, void* stream);
+
+/*
+ * Anchors and their log-constants (Lemma 1 and the definition of phi_theta,
+ * Sec. 3.2): U = sigma * Z for standard normal draws Z (r x d, device), and
+ * c_k = (d/4) log(2q) - (1/2) log r + ||u_k||^2 / (eps q) (computed in FP64,
+ * stored FP32). Outputs U (r x d) and c (r), device.
+ */
+int lsf_anchors(const float* Z, int r, int d, double q, double sigma, double eps,
+                float* U, float* c, void* stream);
+
+/*
+ * Stored shifted features (Lemma 1 map, phi_theta of Sec. 3.2):
+ *   L_ik = c_k - (2/eps) ||x_i - u_k||^2,   shift[i] = max_{k<r} L_ik,
+ *   F[i*ldr + k] = exp(L_ik - shift[i]) for k < r, 0 for r <= k < ldr.
+ * X: n x d device; F: n x ldr device (16-byte aligned); shift: n device.
+ * spread (device float, may be NULL) receives max_i (max_k L_ik - min_k L_ik)
+ * via an atomic maximum; zero it before the first call.
+ */
+int lsf_features(const float* X, int64_t n, const lsf_theta* theta,
+                 float* F, float* shift, float* spread, void* stream);
+
+/* As lsf_features but writes only shift (and spread): the RECOMPUTE prologue. */
+int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta,
+                  float* shift, float* spread, void* stream);
+
+/* ---------------------------------------------------------------- solver */
+
+/*
+ * Bytes of scratch workspace one solve or one debiased solve needs for a given
+ * ldr on the current device. The same workspace must not be used by two calls
+ * that can overlap on the GPU.
+ */
+int lsf_workspace_bytes(int ldr, size_t* bytes);
+
+/*
+ * Alg. 1 (Sec. 2) on the factored kernel K_theta = xi^T zeta (Sec. 3.1),
+ * spec order: from v = 1, `iters` times u <- a/(K v), v <- b/(K^T u).
+ * Each half is one fused pass over a feature matrix that forms s = F t,
+ * divides the weights by s and accumulates the transposed product in the same
+ * read. After the loop one more read of F gives the residual
+ * ||u o (K v) - a||_1. x->w = a, y->w = b.
+ * Writes out (u~, v~, t_u, t_v) and result->{residual, log_scale, status, iters}.
+ * workspace: >= lsf_workspace_bytes(theta->ldr) bytes, device, 256-byte aligned.
+ */
+int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
+              int mode, const lsf_scalings* out, lsf_result* result,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Eq. (6) for up to three solved pairs and their weighted sum:
+ *   result[t].W = eps (sum_i a_i log u_i + sum_j b_j log v_j)   (FP64 compensated sum)
+ *   *combined   = sum_t coef[t] * result[t].W    (combined may be NULL)
+ * With coef = {1, -1/2, -1/2} over (xy, xx, yy) this is Eq. (2).
+ */
+int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* xs,
+                   const lsf_cloud* const* ys, const lsf_scalings* const* s,
+                   lsf_result* const* result, const double* coef, double* combined,
+                   void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Debiased Sinkhorn divergence, Eq. (2): W(a,b) - (W(a,a) + W(b,b))/2 with one
+ * shared theta. The three solves run in lock-step so that per iteration xi is
+ * read twice ({XY-u, XX-u}, {XX-v}) and zeta twice ({XY-v, YY-u}, {YY-v}).
+ * result: device array of 3 lsf_result (xy, xx, yy), each with W filled in.
+ * wbar: device double receiving W_bar (may be NULL).
+ */
+int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
+                 int mode, const lsf_scalings* s_xy, const lsf_scalings* s_xx,
+                 const lsf_scalings* s_yy, lsf_result* result, double* wbar,
+                 void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/*
+ * Envelope gradient (Prop. 3.3 and the formula after it, Sec. 3.3) with theta
+ * held fixed. For W(a,b): dW/dK = -eps u v^T, chained through the features:
+ *   grad x_i = 4 u~_i sum_k t_v[k] F_ik (x_i - u_k)   (t_v = zeta~^T v~)
+ *   grad y_j = 4 v~_j sum_k t_u[k] G_jk (y_j - u_k)   (t_u = xi~^T u~)
+ *   grad a_i = eps log u_i,  grad b_j = eps log v_j.
+ * With debiased != 0 the gradient is that of Eq. (2): the self terms W(a,a),
+ * W(b,b) (kernel xi xi^T, X on both sides) enter with weight -1/2, using
+ * s_xx, s_yy and result[1], result[2].
+ * gX (n x d), gY (m x d), ga (n), gb (m): device outputs (any may be NULL).
+ * result: device array of 1 (or 3 when debiased) lsf_result from the solve.
+ */
+int lsf_gradient(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
+                 const lsf_scalings* s_xy, const lsf_scalings* s_xx,
+                 const lsf_scalings* s_yy, const lsf_result* result, int debiased,
+                 float* gX, float* gY, float* ga, float* gb, void* stream);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Kernel classes timed by the optional event recorder. */
+typedef enum {
+  LSF_KERNEL_PASS = 0,       /* fused Sinkhorn passes (stored features)   */
+  LSF_KERNEL_PASS_RECOMPUTE, /* fused Sinkhorn passes (recompute)         */
+  LSF_KERNEL_FEATURES,       /* feature build and row shifts              */
+  LSF_KERNEL_OTHER,          /* small kernels: init, reductions, adjoint  */
+  LSF_KERNEL_NCLASSES
+} lsf_kernel_class;
+
+/*
+ * Optional CUDA-event timing of every launch the library makes, on the stream
+ * it is launched on. lsf_profile_enable(1) starts recording (and clears past
+ * records); lsf_profile_read synchronises the recorded events and returns, per
+ * class, the summed device time in milliseconds, the number of launches and the
+ * algorithmic bytes those launches move (as the library counts them).
+ * Not thread-safe; meant for a benchmark driving one stream.
+ */
+int lsf_profile_enable(int on);
+int lsf_profile_read(int kernel_class, double* total_ms, int64_t* launches, double* bytes);
+
+/* Number of kernel launches the library issued since the last lsf_launch_count_reset(). */
+int64_t lsf_launch_count(void);
+void lsf_launch_count_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SINKHORN_PF_H */

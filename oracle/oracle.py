@@ -139,11 +139,16 @@ def log_features(P: np.ndarray, U: np.ndarray, eps: float, q: float) -> np.ndarr
     P = np.asarray(P, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
     r, d = U.shape
-    diff = P[:, None, :] - U[None, :, :]
-    sq = (diff * diff).sum(axis=2)
     unorm2 = (U * U).sum(axis=1)
-    return (d / 4.0) * math.log(2.0 * q) - 0.5 * math.log(r) - (2.0 / eps) * sq \
-        + unorm2[None, :] / (eps * q)
+    const = (d / 4.0) * math.log(2.0 * q) - 0.5 * math.log(r)
+    out = np.empty((P.shape[0], r))
+    # rows are independent; they are processed in blocks only to bound memory
+    step = max(1, (1 << 23) // max(1, r * d))
+    for i0 in range(0, P.shape[0], step):
+        diff = P[i0:i0 + step, None, :] - U[None, :, :]
+        sq = (diff * diff).sum(axis=2)
+        out[i0:i0 + step] = const - (2.0 / eps) * sq + unorm2[None, :] / (eps * q)
+    return out
 
 
 def features(P, U, eps, q):

@@ -1,0 +1,45 @@
+// Fused Sinkhorn pass over a stored feature matrix (one half of Alg. 1).
+#pragma once
+
+#include "common.cuh"
+
+namespace lsf {
+
+enum PassMode : int {
+  kPassUpdate = 0,  // s = F t; res += |old s - w|; new = w / s; t' += new F
+  kPassAxpy = 1,    // t' += given F            (given scaling in `old`)
+  kPassDot = 2      // s = F t; res += |old s - w|  (no update)
+};
+
+// One right-hand side of a pass: the r-vector it multiplies and what it updates.
+struct PassRhs {
+  const float* t_in;  // ldr   (Update, Dot)
+  const float* w;     // n     weights (Update, Dot)
+  const float* old;   // n     previous scaling (residual) or the given scaling (Axpy); may be NULL in Update
+  float* out;         // n     new scaling (Update)
+  float* t_out;       // ldr   reduced F^T new (Update, Axpy)
+  double* res_out;    // 1     residual sum |old s - w| (Update with old, Dot)
+};
+
+struct PassArgs {
+  const float* F;   // n x ldr
+  int64_t n;
+  int ldr;
+  int tile_rows;
+  int64_t ntiles;
+  int nstages;
+  PassRhs rhs[2];
+  float* part;        // workspace partial r-vectors
+  double* rpart;      // workspace partial residuals
+  unsigned* counter;  // workspace arrival counter (zero between launches)
+  int* status;        // device status word (lsf_result.status)
+};
+
+// Launch one fused pass (nrhs = 1 or 2) with tiling chosen for F's shape.
+// bytes_moved is the algorithmic traffic of the launch, recorded for profiling.
+int launch_pass(int mode, int nrhs, PassArgs args, cudaStream_t st);
+
+// Algorithmic bytes of one pass launch.
+double pass_bytes(int mode, int nrhs, int64_t n, int ldr, bool with_old);
+
+}  // namespace lsf

@@ -1,0 +1,400 @@
+// Alg. 1 on the factored kernel (Sec. 3.1), Eq. (6) and Eq. (2): host orchestration
+// of the fused passes plus the small kernels around them (start vector, the
+// divergence reduction).
+#include <cuda_runtime.h>
+
+#include "pass.cuh"
+#include "recompute.cuh"
+
+namespace lsf {
+namespace {
+
+// Running maximum of a float array as an order-preserving key (key 0 = -inf).
+__global__ void max_key_kernel(const float* __restrict__ x, int64_t n, unsigned* __restrict__ key) {
+  float best = -INFINITY;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    best = fmaxf(best, x[i]);
+  best = warp_max(best);
+  if ((threadIdx.x & 31) == 0) atomicMax(key, float_key(best));
+}
+
+// v = 1 in shifted form: v~_j = exp(shift_j - M) with M = max shift (the global
+// factor exp(-M) cancels in P and W and is recorded in log_scale).
+__global__ void init_scaling_kernel(const float* __restrict__ shift, int64_t n,
+                                    const unsigned* __restrict__ key, float* __restrict__ v,
+                                    double* log_scale_a, double* log_scale_b) {
+  const float M = key_float(*key);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    v[i] = expf(shift[i] - M);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (log_scale_a) *log_scale_a = static_cast<double>(M);
+    if (log_scale_b) *log_scale_b = static_cast<double>(M);
+  }
+}
+
+__global__ void set_iters_kernel(lsf_result* r0, lsf_result* r1, lsf_result* r2, int iters) {
+  if (threadIdx.x == 0) {
+    if (r0) r0->iters = iters;
+    if (r1) r1->iters = iters;
+    if (r2) r2->iters = iters;
+  }
+}
+
+// ---------------------------------------------------------------- Eq. (6) reduction
+
+struct DivSeg {
+  const float* s;      // shifted scaling u~ or v~
+  const float* shift;  // row shifts
+  const float* w;      // weights
+  int64_t n;
+  int term;            // which result record
+  double sign;         // +1: log u = log u~ - shift - M ; -1: log v = log v~ - shift + M
+};
+
+struct DivArgs {
+  DivSeg seg[6];
+  int nseg;
+  int nterms;
+  double eps;
+  double coef[3];
+  lsf_result* res[3];
+  double* combined;
+  double* dpart;       // [gridDim][3]
+  unsigned* counter;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) divergence_kernel(const DivArgs a) {
+  __shared__ double s_w[8][3];
+  __shared__ int s_last;
+  KahanSum acc[3];
+  for (int sgi = 0; sgi < a.nseg; ++sgi) {
+    const DivSeg sg = a.seg[sgi];
+    const double M = a.res[sg.term]->log_scale;
+    const int64_t chunk = (sg.n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = chunk * blockIdx.x;
+    const int64_t hi = min(sg.n, lo + chunk);
+    KahanSum part;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double lg = static_cast<double>(logf(sg.s[i])) - static_cast<double>(sg.shift[i]) - sg.sign * M;
+      part.add(static_cast<double>(sg.w[i]) * lg);
+    }
+    // Fold this segment's thread sum into its term in a fixed order.
+    if (sg.term == 0) acc[0].add(part.value());
+    else if (sg.term == 1) acc[1].add(part.value());
+    else acc[2].add(part.value());
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const double v = warp_sum_d(acc[t].value());
+    if (lane == 0) s_w[warp][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < 3; ++t) {
+      KahanSum b;
+      for (int w = 0; w < 8; ++w) b.add(s_w[w][t]);
+      a.dpart[blockIdx.x * 3 + t] = b.value();
+    }
+    __threadfence();
+    s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double comb = 0.0;
+  for (int t = 0; t < a.nterms; ++t) {
+    KahanSum tot;
+    for (unsigned g = 0; g < gridDim.x; ++g) tot.add(__ldcg(a.dpart + g * 3 + t));
+    const double W = a.eps * tot.value();
+    a.res[t]->W = W;
+    comb += a.coef[t] * W;
+  }
+  if (a.combined) *a.combined = comb;
+  *a.counter = 0u;
+}
+
+// ---------------------------------------------------------------- validation
+
+int check_theta(const lsf_theta* th) {
+  if (!th) return fail(LSF_ERR_ARG, "theta is NULL");
+  if (th->r < 1 || th->d < 1 || th->r > th->ldr)
+    return fail(LSF_ERR_ARG, "theta: need r >= 1, d >= 1, r <= ldr");
+  if (th->ldr % 4 != 0 || th->ldr > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "theta: ldr must be a multiple of 4, <= 1024");
+  if (!(th->eps > 0.0)) return fail(LSF_ERR_ARG, "theta: eps must be > 0");
+  return LSF_OK;
+}
+
+int check_cloud(const lsf_cloud* c, int mode, const char* name) {
+  if (!c) return fail(LSF_ERR_ARG, "%s cloud is NULL", name);
+  if (c->n < 1) return fail(LSF_ERR_ARG, "%s: a measure needs n >= 1 points", name);
+  if (!c->shift || !c->w) return fail(LSF_ERR_ARG, "%s: shift and w are required", name);
+  if (mode == LSF_MODE_STORED) {
+    if (!c->F) return fail(LSF_ERR_ARG, "%s: stored mode needs F", name);
+    if (reinterpret_cast<uintptr_t>(c->F) % 16 != 0)
+      return fail(LSF_ERR_ARG, "%s: F must be 16-byte aligned", name);
+  } else if (mode == LSF_MODE_RECOMPUTE) {
+    if (!c->X) return fail(LSF_ERR_ARG, "%s: recompute mode needs X", name);
+  } else {
+    return fail(LSF_ERR_ARG, "unknown mode %d", mode);
+  }
+  return LSF_OK;
+}
+
+int check_scalings(const lsf_scalings* s, const char* name) {
+  if (!s || !s->u || !s->v || !s->t_u || !s->t_v)
+    return fail(LSF_ERR_ARG, "%s scalings: u, v, t_u, t_v are required", name);
+  if (reinterpret_cast<uintptr_t>(s->t_u) % 16 || reinterpret_cast<uintptr_t>(s->t_v) % 16)
+    return fail(LSF_ERR_ARG, "%s scalings: t_u, t_v must be 16-byte aligned", name);
+  return LSF_OK;
+}
+
+#define LSF_TRY(expr)          \
+  do {                         \
+    int _rc = (expr);          \
+    if (_rc != LSF_OK) return _rc; \
+  } while (0)
+
+// One fused pass on one cloud in the chosen mode.
+struct Side {
+  const lsf_cloud* cl;
+};
+
+int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int nrhs,
+             const PassRhs* rhs, const Workspace& ws, int* status, cudaStream_t st) {
+  if (mode == LSF_MODE_STORED) {
+    PassArgs a{};
+    a.F = cl->F;
+    a.n = cl->n;
+    a.ldr = th->ldr;
+    for (int k = 0; k < nrhs; ++k) a.rhs[k] = rhs[k];
+    a.part = ws.part;
+    a.rpart = ws.rpart;
+    a.counter = ws.counters;
+    a.status = status;
+    return launch_pass(pmode, nrhs, a, st);
+  }
+  RecomputeArgs a{};
+  a.X = cl->X;
+  a.shift = cl->shift;
+  a.n = cl->n;
+  a.U = th->U;
+  a.c = th->c;
+  a.r = th->r;
+  a.ldr = th->ldr;
+  a.d = th->d;
+  a.two_over_eps = static_cast<float>(2.0 / th->eps);
+  for (int k = 0; k < nrhs; ++k) a.rhs[k] = rhs[k];
+  a.part = ws.part;
+  a.rpart = ws.rpart;
+  a.counter = ws.counters;
+  a.status = status;
+  return launch_recompute_pass(pmode, nrhs, a, st);
+}
+
+int start_solve(void* workspace, size_t ws_bytes, int ldr, lsf_result* result, int nres,
+                Workspace* ws, cudaStream_t st) {
+  LSF_TRY(carve_workspace(workspace, ws_bytes, ldr, ws));
+  if (!result) return fail(LSF_ERR_ARG, "result is NULL");
+  if (cudaMemsetAsync(result, 0, sizeof(lsf_result) * nres, st) != cudaSuccess ||
+      cudaMemsetAsync(ws->counters, 0, sizeof(unsigned) * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(ws->keys, 0, sizeof(unsigned) * 8, st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "solve: memset failed");
+  return LSF_OK;
+}
+
+int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double* ls_b,
+              cudaStream_t st) {
+  const int grid = device_info().sms * 2;
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * cl->n);
+  max_key_kernel<<<grid, 256, 0, st>>>(cl->shift, cl->n, key);
+  init_scaling_kernel<<<grid, 256, 0, st>>>(cl->shift, cl->n, key, v, ls_a, ls_b);
+  return check_launch("init_scaling_kernel");
+}
+
+int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* xs,
+                      const lsf_cloud* const* ys, const lsf_scalings* const* s,
+                      lsf_result* const* res, const double* coef, double* combined,
+                      const Workspace& ws, cudaStream_t st) {
+  DivArgs a{};
+  a.nterms = nterms;
+  a.eps = th->eps;
+  a.combined = combined;
+  a.dpart = ws.dpart;
+  a.counter = ws.counters + 1;
+  double bytes = 0.0;
+  for (int t = 0; t < nterms; ++t) {
+    a.coef[t] = coef ? coef[t] : 1.0;
+    a.res[t] = res[t];
+    a.seg[a.nseg++] = DivSeg{s[t]->u, xs[t]->shift, xs[t]->w, xs[t]->n, t, +1.0};
+    a.seg[a.nseg++] = DivSeg{s[t]->v, ys[t]->shift, ys[t]->w, ys[t]->n, t, -1.0};
+    bytes += 12.0 * (xs[t]->n + ys[t]->n);
+  }
+  for (int t = nterms; t < 3; ++t) a.res[t] = res[0];
+  LaunchScope ls(st, LSF_KERNEL_OTHER, bytes);
+  divergence_kernel<<<kDivGrid, 256, 0, st>>>(a);
+  return check_launch("divergence_kernel");
+}
+
+}  // namespace
+}  // namespace lsf
+
+using namespace lsf;
+
+extern "C" {
+
+int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters, int mode,
+              const lsf_scalings* out, lsf_result* result, void* workspace, size_t ws_bytes,
+              void* stream) {
+  LSF_TRY(check_theta(theta));
+  LSF_TRY(check_cloud(x, mode, "x"));
+  LSF_TRY(check_cloud(y, mode, "y"));
+  LSF_TRY(check_scalings(out, "out"));
+  if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+  cudaStream_t st = as_stream(stream);
+  Workspace ws{};
+  LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 1, &ws, st));
+  int* status = &result->status;
+
+  LSF_TRY(init_side(y, ws.keys + 0, out->v, &result->log_scale, nullptr, st));
+  {
+    PassRhs r{};
+    r.old = out->v;
+    r.t_out = out->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassAxpy, 1, &r, ws, status, st));
+  }
+  for (int it = 0; it < iters; ++it) {
+    PassRhs ru{};
+    ru.t_in = out->t_v; ru.w = x->w; ru.out = out->u; ru.t_out = out->t_u;
+    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 1, &ru, ws, status, st));
+    PassRhs rv{};
+    rv.t_in = out->t_u; rv.w = y->w; rv.out = out->v; rv.t_out = out->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 1, &rv, ws, status, st));
+  }
+  {
+    PassRhs rd{};
+    rd.t_in = out->t_v; rd.w = x->w; rd.old = out->u; rd.res_out = &result->residual;
+    LSF_TRY(run_pass(mode, theta, x, kPassDot, 1, &rd, ws, status, st));
+  }
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    set_iters_kernel<<<1, 32, 0, st>>>(result, nullptr, nullptr, iters);
+  }
+  return check_launch("set_iters_kernel");
+}
+
+int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* xs,
+                   const lsf_cloud* const* ys, const lsf_scalings* const* s,
+                   lsf_result* const* result, const double* coef, double* combined,
+                   void* workspace, size_t ws_bytes, void* stream) {
+  LSF_TRY(check_theta(theta));
+  if (nterms < 1 || nterms > 3) return fail(LSF_ERR_ARG, "nterms must be 1..3");
+  if (!xs || !ys || !s || !result) return fail(LSF_ERR_ARG, "lsf_divergence: NULL array");
+  for (int t = 0; t < nterms; ++t) {
+    if (!xs[t] || !ys[t] || !s[t] || !result[t]) return fail(LSF_ERR_ARG, "NULL term %d", t);
+    if (!xs[t]->shift || !xs[t]->w || !ys[t]->shift || !ys[t]->w || !s[t]->u || !s[t]->v)
+      return fail(LSF_ERR_ARG, "term %d: missing arrays", t);
+    if (xs[t]->n < 1 || ys[t]->n < 1) return fail(LSF_ERR_ARG, "term %d: empty measure", t);
+  }
+  cudaStream_t st = as_stream(stream);
+  Workspace ws{};
+  LSF_TRY(carve_workspace(workspace, ws_bytes, theta->ldr, &ws));
+  if (cudaMemsetAsync(ws.counters + 1, 0, sizeof(unsigned), st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "lsf_divergence: memset failed");
+  return launch_divergence(theta, nterms, xs, ys, s, result, coef, combined, ws, st);
+}
+
+int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
+                 int mode, const lsf_scalings* s_xy, const lsf_scalings* s_xx,
+                 const lsf_scalings* s_yy, lsf_result* result, double* wbar, void* workspace,
+                 size_t ws_bytes, void* stream) {
+  LSF_TRY(check_theta(theta));
+  LSF_TRY(check_cloud(x, mode, "x"));
+  LSF_TRY(check_cloud(y, mode, "y"));
+  LSF_TRY(check_scalings(s_xy, "xy"));
+  LSF_TRY(check_scalings(s_xx, "xx"));
+  LSF_TRY(check_scalings(s_yy, "yy"));
+  if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+  cudaStream_t st = as_stream(stream);
+  Workspace ws{};
+  LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 3, &ws, st));
+  lsf_result* rxy = result + 0;
+  lsf_result* rxx = result + 1;
+  lsf_result* ryy = result + 2;
+  int* status = &rxy->status;
+
+  // v = 1 for all three solves: v~ = exp(shift - max shift) on the side each v lives on.
+  LSF_TRY(init_side(y, ws.keys + 0, s_xy->v, &rxy->log_scale, &ryy->log_scale, st));
+  if (cudaMemcpyAsync(s_yy->v, s_xy->v, sizeof(float) * y->n, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return fail(LSF_ERR_CUDA, "debiased: copy of the start vector failed");
+  LSF_TRY(init_side(x, ws.keys + 1, s_xx->v, &rxx->log_scale, nullptr, st));
+  {
+    PassRhs r[2] = {};
+    r[0].old = s_xy->v; r[0].t_out = s_xy->t_v;
+    r[1].old = s_yy->v; r[1].t_out = s_yy->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassAxpy, 2, r, ws, status, st));
+    PassRhs q{};
+    q.old = s_xx->v; q.t_out = s_xx->t_v;
+    LSF_TRY(run_pass(mode, theta, x, kPassAxpy, 1, &q, ws, status, st));
+  }
+  for (int it = 0; it < iters; ++it) {
+    // xi pass: {XY u-half, XX u-half}
+    PassRhs p1[2] = {};
+    p1[0].t_in = s_xy->t_v; p1[0].w = x->w; p1[0].out = s_xy->u; p1[0].t_out = s_xy->t_u;
+    p1[1].t_in = s_xx->t_v; p1[1].w = x->w; p1[1].out = s_xx->u; p1[1].t_out = s_xx->t_u;
+    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 2, p1, ws, status, st));
+    // zeta pass: {XY v-half, YY u-half}
+    PassRhs p2[2] = {};
+    p2[0].t_in = s_xy->t_u; p2[0].w = y->w; p2[0].out = s_xy->v; p2[0].t_out = s_xy->t_v;
+    p2[1].t_in = s_yy->t_v; p2[1].w = y->w; p2[1].out = s_yy->u; p2[1].t_out = s_yy->t_u;
+    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 2, p2, ws, status, st));
+    // xi pass: {XX v-half}
+    PassRhs p3{};
+    p3.t_in = s_xx->t_u; p3.w = x->w; p3.out = s_xx->v; p3.t_out = s_xx->t_v;
+    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 1, &p3, ws, status, st));
+    // zeta pass: {YY v-half}
+    PassRhs p4{};
+    p4.t_in = s_yy->t_u; p4.w = y->w; p4.out = s_yy->v; p4.t_out = s_yy->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 1, &p4, ws, status, st));
+  }
+  {
+    PassRhs d1[2] = {};
+    d1[0].t_in = s_xy->t_v; d1[0].w = x->w; d1[0].old = s_xy->u; d1[0].res_out = &rxy->residual;
+    d1[1].t_in = s_xx->t_v; d1[1].w = x->w; d1[1].old = s_xx->u; d1[1].res_out = &rxx->residual;
+    LSF_TRY(run_pass(mode, theta, x, kPassDot, 2, d1, ws, status, st));
+    PassRhs d2{};
+    d2.t_in = s_yy->t_v; d2.w = y->w; d2.old = s_yy->u; d2.res_out = &ryy->residual;
+    LSF_TRY(run_pass(mode, theta, y, kPassDot, 1, &d2, ws, status, st));
+  }
+  {
+    const lsf_cloud* xs[3] = {x, x, y};
+    const lsf_cloud* ys[3] = {y, x, y};
+    const lsf_scalings* ss[3] = {s_xy, s_xx, s_yy};
+    lsf_result* rs[3] = {rxy, rxx, ryy};
+    const double coef[3] = {1.0, -0.5, -0.5};
+    LSF_TRY(launch_divergence(theta, 3, xs, ys, ss, rs, coef, wbar, ws, st));
+  }
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    set_iters_kernel<<<1, 32, 0, st>>>(rxy, rxx, ryy, iters);
+  }
+  // Status bits of all passes were collected in the first record; mirror them.
+  if (cudaMemcpyAsync(&rxx->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&ryy->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess)
+    return fail(LSF_ERR_CUDA, "debiased: status copy failed");
+  return check_launch("set_iters_kernel");
+}
+
+}  // extern "C"
