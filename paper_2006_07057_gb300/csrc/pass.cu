@@ -17,7 +17,7 @@
 
 #include <algorithm>
 
-#include "pass.cuh"
+#include "reduce.cuh"
 
 namespace lsf {
 namespace {
@@ -209,63 +209,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
   if (flag) atomicOr(&s_flag, flag);
   __syncthreads();
 
-  // ------------------------------------------------------------ CTA partials
-  const unsigned G = gridDim.x;
-  const int nv = NRHS * ldr;
-  if (kAcc) {
-    const float* red = sF;
-    for (int idx = threadIdx.x; idx < nv; idx += blockDim.x) {
-      float sum = 0.f;
-#pragma unroll
-      for (int w = 0; w < kConsumerWarps; ++w) sum += red[static_cast<size_t>(w) * nv + idx];
-      a.part[static_cast<size_t>(blockIdx.x) * nv + idx] = sum;
-    }
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) {
-      double r = 0.0;
-      for (int w = 0; w < kConsumerWarps; ++w) r += s_res[w][k];
-      a.rpart[static_cast<size_t>(blockIdx.x) * NRHS + k] = r;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    s_last = (atomicAdd(a.counter, 1u) == G - 1u) ? 1 : 0;
-    if (s_flag) atomicOr(a.status, s_flag);
-  }
-  __syncthreads();
-  if (!s_last) return;
-
-  // ------------------------------------------------------------ last CTA: fixed-order sum
-  __threadfence();
-  if (kAcc) {
-    for (int idx = threadIdx.x; idx < nv; idx += blockDim.x) {
-      double s0 = 0.0, s1 = 0.0;
-      unsigned g = 0;
-      for (; g + 1 < G; g += 2) {
-        s0 += __ldcg(a.part + static_cast<size_t>(g) * nv + idx);
-        s1 += __ldcg(a.part + static_cast<size_t>(g + 1) * nv + idx);
-      }
-      if (g < G) s0 += __ldcg(a.part + static_cast<size_t>(g) * nv + idx);
-      const int k = idx / ldr;
-      const int col = idx - k * ldr;
-      float* to = a.rhs[k].t_out;
-      if (to) to[col] = static_cast<float>(s0 + s1);
-    }
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) {
-      if (!a.rhs[k].res_out) continue;
-      double r = 0.0;
-      for (unsigned g = 0; g < G; ++g) r += __ldcg(a.rpart + static_cast<size_t>(g) * NRHS + k);
-      *a.rhs[k].res_out = r;
-    }
-    *a.counter = 0u;
-  }
+  finish_pass<NRHS, kAcc>(sF, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.rpart, a.counter,
+                         a.status, s_flag, &s_last);
 }
+
+}  // namespace
+
+namespace {
 
 template <int C, int NRHS>
 int launch_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {

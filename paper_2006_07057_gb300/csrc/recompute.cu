@@ -1,9 +1,309 @@
+// Fused Sinkhorn pass that recomputes the shifted features in registers.
+//
+// Instead of streaming a stored n x r feature matrix, each entry is rebuilt
+// from the points and the anchors in the log2 domain:
+//   log2 F_ik = A_k + B_i + sum_d x_id W_kd,
+//   A_k = log2(e) (c_k - (2/eps)||u_k||^2),  W_kd = log2(e) (4/eps) u_kd,
+//   B_i = -log2(e) ((2/eps)||x_i||^2 + shift_i),
+// (the expansion of c_k - (2/eps)||x_i - u_k||^2 - shift_i, Lemma 1), then one
+// hardware ex2 per entry, shared by the row product and the transposed
+// accumulation of the same pass. HBM traffic drops to the points and vectors;
+// the bound becomes the FMA and MUFU pipes.
+//
+// Layout: 256 threads; a row group of GW warps owns one row at a time with each
+// thread holding four consecutive feature columns (their A_k and W_kd stay in
+// registers for the whole launch). A batch gives every group 8 rows; row data
+// (x, B, weights, previous scalings) for the next batch is loaded into registers
+// while the current batch computes, then parked in the other shared buffer.
+// Cross-warp row sums go through shared memory in a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
 #include "recompute.cuh"
+#include "reduce.cuh"
 
 namespace lsf {
+namespace {
 
-int launch_recompute_pass(int, int, RecomputeArgs, cudaStream_t) {
-  return fail(LSF_ERR_UNSUPPORTED, "recompute mode is not built yet");
+constexpr int kRcThreads = 256;
+constexpr int kRcWarps = kRcThreads / 32;
+constexpr int kRcRB = 8;  // rows per group per batch
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Row data slots per row in shared memory: x[D], B, then per rhs (w, old).
+template <int D, int NRHS>
+struct RowSlots {
+  static constexpr int kStride = D + 1 + 2 * NRHS;
+};
+
+template <int GW, int D, int NRHS>
+__global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeArgs a, const int mode) {
+  constexpr int NG = kRcWarps / GW;         // row groups per CTA
+  constexpr int RPB = NG * kRcRB;           // rows per batch
+  constexpr int TPG = GW * 32;              // threads per group
+  constexpr int SR = RowSlots<D, NRHS>::kStride;
+  __shared__ float s_rows[2][RPB * SR];
+  __shared__ float s_red[NRHS * kRcRB * kRcWarps];  // per-warp partial row products
+  __shared__ double s_res[kRcWarps][2];
+  __shared__ int s_flag, s_last;
+  extern __shared__ __align__(16) float s_part[];  // [NG][NRHS * ldr] at the end
+
+  const bool kUpd = mode == kPassUpdate, kAx = mode == kPassAxpy, kDt = mode == kPassDot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp / GW;                  // my group
+  const int tg = tid - g * TPG;             // my thread index inside the group
+  const int wg = warp - g * GW;             // my warp index inside the group
+  const int ldr = a.ldr, d = a.d;
+  const int col0 = 4 * tg;                  // my four columns
+
+  if (tid == 0) s_flag = 0;
+  // per-column constants
+  float Ap[4], Wp[4][D];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int k = col0 + e;
+    if (k < a.r) {
+      float nrm = 0.f;
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) {
+        const float u = (dd < d) ? a.U[static_cast<int64_t>(k) * d + dd] : 0.f;
+        nrm = fmaf(u, u, nrm);
+        Wp[e][dd] = kLog2e * (2.f * a.two_over_eps) * u;
+      }
+      Ap[e] = kLog2e * (a.c[k] - a.two_over_eps * nrm);
+    } else {
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) Wp[e][dd] = 0.f;
+      Ap[e] = -INFINITY;  // ex2(-inf) = 0: padded columns carry no mass
+    }
+  }
+  float t[NRHS][4], acc[NRHS][4];
+  double res[NRHS];
+  bool has_old[NRHS];
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) {
+    res[k] = 0.0;
+    has_old[k] = a.rhs[k].old != nullptr;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int col = col0 + e;
+      t[k][e] = (!kAx && col < ldr) ? a.rhs[k].t_in[col] : 0.f;
+      acc[k][e] = 0.f;
+    }
+  }
+  int flag = 0;
+
+  const int64_t nbatch = (a.n + RPB - 1) / RPB;
+  // register prefetch of one row's data by threads tid < RPB
+  float pre[SR];
+  auto load_rows = [&](int64_t b) {
+    if (tid >= RPB) return;
+    const int64_t i = b * RPB + tid;
+    if (b >= nbatch || i >= a.n) {
+#pragma unroll
+      for (int q = 0; q < SR; ++q) pre[q] = 0.f;
+      pre[D] = -INFINITY;
+      return;
+    }
+    float nrm = 0.f;
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+      const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
+      pre[dd] = x;
+      nrm = fmaf(x, x, nrm);
+    }
+    pre[D] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) {
+      pre[D + 1 + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
+      pre[D + 2 + 2 * k] = has_old[k] ? a.rhs[k].old[i] : 0.f;
+    }
+  };
+  auto park_rows = [&](int buf) {
+    if (tid >= RPB) return;
+#pragma unroll
+    for (int q = 0; q < SR; ++q) s_rows[buf][tid * SR + q] = pre[q];
+  };
+
+  int buf = 0;
+  load_rows(blockIdx.x);
+  park_rows(0);
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
+    load_rows(b + gridDim.x);  // in flight while this batch computes
+    const float* rows = s_rows[buf];
+    float F[kRcRB][4];
+    float dots[NRHS][kRcRB];
+#pragma unroll
+    for (int q = 0; q < kRcRB; ++q) {
+      const float* rw = rows + (g * kRcRB + q) * SR;
+      const float B = rw[D];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float E = Ap[e] + B;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) E = fmaf(rw[dd], Wp[e][dd], E);
+        F[q][e] = ex2_approx(E);
+      }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+        dots[k][q] = fmaf(F[q][0], t[k][0], fmaf(F[q][1], t[k][1], fmaf(F[q][2], t[k][2], F[q][3] * t[k][3])));
+    }
+    if (!kAx) {
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+        for (int q = 0; q < kRcRB; ++q) dots[k][q] = warp_sum(dots[k][q]);
+      if (GW > 1) {
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+            for (int q = 0; q < kRcRB; ++q) s_red[(k * kRcRB + q) * kRcWarps + warp] = dots[k][q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+          for (int q = 0; q < kRcRB; ++q) {
+            const float* pr = s_red + (k * kRcRB + q) * kRcWarps + g * GW;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < GW; ++w) s += pr[w];
+            dots[k][q] = s;
+          }
+      }
+    }
+    const int64_t row0 = b * RPB + g * kRcRB;
+#pragma unroll
+    for (int q = 0; q < kRcRB; ++q) {
+      const int64_t i = row0 + q;
+      if (i >= a.n) break;
+      const float* rw = rows + (g * kRcRB + q) * SR;
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        const float wi = rw[D + 1 + 2 * k];
+        const float oi = rw[D + 2 + 2 * k];
+        float scale;
+        if (kAx) {
+          scale = oi;
+        } else {
+          const float s = dots[k][q];
+          if (has_old[k] && tg == 0)
+            res[k] += fabs(static_cast<double>(oi) * static_cast<double>(s) - static_cast<double>(wi));
+          scale = kUpd ? wi / s : 0.f;
+          if (kUpd && tg == 0) {
+            a.rhs[k].out[i] = scale;
+            if (!(s > 0.f) || !isfinite(scale)) flag |= LSF_ERR_NONFINITE;
+          }
+        }
+        if (!kDt) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(scale, F[q][e], acc[k][e]);
+        }
+      }
+    }
+    park_rows(buf ^ 1);
+    __syncthreads();
+  }
+
+  // partials: group g writes its columns into s_part[g][k][col]
+  if (!kDt) {
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = col0 + e;
+        if (col < ldr) s_part[static_cast<size_t>(g) * NRHS * ldr + k * ldr + col] = acc[k][e];
+      }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) s_res[warp][k] = (wg == 0) ? res[k] : 0.0;
+  if (flag) atomicOr(&s_flag, flag);
+  __syncthreads();
+  // residual sums are per warp; fold each group's warps into slot g (in order)
+  if (tid == 0) {
+    for (int gg = 0; gg < NG; ++gg)
+      for (int k = 0; k < NRHS; ++k) {
+        double r = 0.0;
+        for (int w = 0; w < GW; ++w) r += s_res[gg * GW + w][k];
+        s_res[gg][k] = r;
+      }
+  }
+  __syncthreads();
+  if (kDt)
+    finish_pass<NRHS, false>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.rpart, a.counter,
+                             a.status, s_flag, &s_last);
+  else
+    finish_pass<NRHS, true>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.rpart, a.counter,
+                            a.status, s_flag, &s_last);
+}
+
+template <int GW, int D, int NRHS>
+int launch_gdn(int mode, const RecomputeArgs& a, cudaStream_t st) {
+  constexpr int NG = kRcWarps / GW;
+  const size_t smem = sizeof(float) * static_cast<size_t>(NG) * NRHS * a.ldr;
+  auto kern = recompute_kernel<GW, D, NRHS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "recompute: smem attribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRcThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t rpb = NG * kRcRB;
+  const int64_t nbatch = (a.n + rpb - 1) / rpb;
+  const int64_t grid = std::min<int64_t>(static_cast<int64_t>(device_info().sms) * per_sm, nbatch);
+  kern<<<static_cast<unsigned>(grid), kRcThreads, smem, st>>>(a, mode);
+  return check_launch("recompute_kernel");
+}
+
+template <int GW, int NRHS>
+int launch_gn(int mode, const RecomputeArgs& a, int Dp, cudaStream_t st) {
+  switch (Dp) {
+    case 2: return launch_gdn<GW, 2, NRHS>(mode, a, st);
+    case 3: return launch_gdn<GW, 3, NRHS>(mode, a, st);
+    case 4: return launch_gdn<GW, 4, NRHS>(mode, a, st);
+    case 8: return launch_gdn<GW, 8, NRHS>(mode, a, st);
+    default: return launch_gdn<GW, 16, NRHS>(mode, a, st);
+  }
+}
+
+template <int NRHS>
+int launch_n(int mode, const RecomputeArgs& a, int GW, int Dp, cudaStream_t st) {
+  switch (GW) {
+    case 1: return launch_gn<1, NRHS>(mode, a, Dp, st);
+    case 2: return launch_gn<2, NRHS>(mode, a, Dp, st);
+    case 4: return launch_gn<4, NRHS>(mode, a, Dp, st);
+    default: return launch_gn<8, NRHS>(mode, a, Dp, st);
+  }
+}
+
+}  // namespace
+
+int launch_recompute_pass(int mode, int nrhs, RecomputeArgs a, cudaStream_t st) {
+  if (a.n < 1) return fail(LSF_ERR_ARG, "recompute: n must be >= 1");
+  if (a.d < 1 || a.d > 16)
+    return fail(LSF_ERR_UNSUPPORTED, "recompute mode handles 1 <= d <= 16 (stored mode otherwise)");
+  if (a.ldr < 4 || a.ldr % 4 != 0 || a.ldr > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "recompute: ldr must be a multiple of 4 in [4, 1024]");
+  if (!a.X || !a.U || !a.c || !a.shift) return fail(LSF_ERR_ARG, "recompute: NULL argument");
+  int quads = (a.ldr + 3) / 4;
+  int qpr = 32;
+  while (qpr < quads) qpr *= 2;
+  const int GW = qpr / 32;  // 1, 2, 4 or 8 warps per row
+  const int Dp = a.d <= 2 ? 2 : a.d <= 3 ? 3 : a.d <= 4 ? 4 : a.d <= 8 ? 8 : 16;
+  double bytes = 4.0 * a.n * (a.d + 1) + 4.0 * a.n * nrhs * 3.0;
+  LaunchScope ls(st, LSF_KERNEL_PASS_RECOMPUTE, bytes);
+  if (nrhs == 1) return launch_n<1>(mode, a, GW, Dp, st);
+  return launch_n<2>(mode, a, GW, Dp, st);
 }
 
 }  // namespace lsf

@@ -4,9 +4,10 @@ Tolerances (FP32 device arithmetic against an FP64 oracle):
   * divergences: |W_gpu - W_orc| <= 1e-4 |W_orc|; for the debiased W_bar, whose
     value can sit near 0, the scale is |W_xy| + |W_xx|/2 + |W_yy|/2;
   * residual ||P1 - a||_1: absolute 1e-5 (it is normalised by sum a = 1);
-  * stored features: each entry is exp(L - shift) with L = c - (2/eps)||x-u||^2
-    formed in FP32, so its relative error is about |L| * 2^-23 plus the
-    exponential's own rounding; the test allows 4 |L| 2^-23 + 1e-6 relative;
+  * stored features: L = c - (2/eps)||x-u||^2 is formed in FP32 as a sum of d
+    rounded squares, so its absolute error grows like sqrt(d) ulps of the
+    terms; the test allows (2 sqrt(d) + 4)(|L| + |c|) 2^-24 on L and the shift,
+    twice that (relative) on F = exp(L - shift), plus 1e-6;
   * potentials log u, log v: 2e-4 (1 + |log u|), from the same feature error
     carried through the fixed point.
 """
@@ -109,14 +110,16 @@ def test_features_match_oracle(lsf, n, d, r, eps):
     th = o.make_theta(p.X, p.Y, p.Z, eps)
     L = o.log_features(p.X, th.U, eps, th.q)
     shift = L.max(axis=1)
+    c = (d / 4) * math.log(2 * th.q) - 0.5 * math.log(r) + (th.U ** 2).sum(1) / (eps * th.q)
+    tolL = (2 * math.sqrt(d) + 4) * (np.abs(L) + np.abs(c)[None, :]) * 2.0 ** -24
     gshift = prob.x.shift.double().cpu().numpy()
-    assert np.all(np.abs(gshift - shift) <= 4 * np.abs(shift) * 2.0 ** -23 + 1e-5)
+    assert np.all(np.abs(gshift - shift) <= tolL.max(axis=1) + 1e-6)
     F = prob.x.F.double().cpu().numpy()
     ldr = prob.theta.ldr
     assert F.shape == (n, ldr)
     assert np.all(F[:, r:] == 0.0)
     ref = np.exp(L - shift[:, None])
-    tol = 4 * (np.abs(L) + np.abs(shift)[:, None]) * 2.0 ** -23 + 1e-6
+    tol = 2 * (tolL + tolL.max(axis=1)[:, None]) + 1e-6
     rel = np.abs(F[:, :r] - ref) / np.maximum(ref, 1e-30)
     ok = (rel <= tol) | (np.abs(F[:, :r] - ref) <= 1e-37)
     assert ok.all(), (rel[~ok][:5], ref[~ok][:5])
@@ -202,7 +205,9 @@ def test_large_workload_full_size(lsf):
     sh = L.max(1)
     F = prob.x.F[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     ref = np.exp(L - sh[:, None])
-    tol = 4 * (np.abs(L) + np.abs(sh)[:, None]) * 2.0 ** -23 + 1e-6
+    c = 0.75 * math.log(2 * th.q) - 0.5 * math.log(p.r) + (th.U ** 2).sum(1) / (p.eps * th.q)
+    tolL = (2 * math.sqrt(3) + 4) * (np.abs(L) + np.abs(c)[None, :]) * 2.0 ** -24
+    tol = 2 * (tolL + tolL.max(axis=1)[:, None]) + 1e-6
     assert np.all((np.abs(F - ref) <= tol * ref) | (np.abs(F - ref) <= 1e-37))
     # column marginals after the v-half: v~_j (zeta~_j . xi~^T u~) = b_j
     for s, Fa, Fb, wb in ((prob.s_xy, prob.x.F, prob.y.F, b), (prob.s_yy, prob.y.F, prob.y.F, b),
