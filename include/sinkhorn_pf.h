@@ -207,6 +207,19 @@ int lsf_gradient(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  const lsf_scalings* s_yy, const lsf_result* result, int debiased,
                  float* gX, float* gY, float* ga, float* gb, void* stream);
 
+/* ---------------------------------------------------------------- tuning */
+
+/*
+ * Tiling of the stored-feature pass: target bytes per shared-memory tile
+ * (rounded to whole rows for every consumer warp, and shrunk for small inputs so
+ * that every SM gets work) and the maximum depth of the copy ring (limited by
+ * shared memory). Not a paper quantity: a launch parameter picked by the
+ * autotuner. Process-wide; set it before launching. Errors: LSF_ERR_ARG if
+ * tile_bytes is outside [512, 131072] or max_stages outside [2, 16].
+ */
+int lsf_set_pass_tiling(int tile_bytes, int max_stages);
+int lsf_get_pass_tiling(int* tile_bytes, int* max_stages);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Kernel classes timed by the optional event recorder. */

@@ -232,6 +232,17 @@ def lsf_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: Scaling
                              _p(gX), _p(gY), _p(ga), _p(gb), _stream(stream)), "lsf_gradient")
 
 
+def lsf_set_pass_tiling(tile_bytes: int, max_stages: int) -> None:
+    check(lib().lsf_set_pass_tiling(int(tile_bytes), int(max_stages)), "lsf_set_pass_tiling")
+
+
+def lsf_get_pass_tiling() -> tuple[int, int]:
+    tb = ctypes.c_int()
+    st = ctypes.c_int()
+    check(lib().lsf_get_pass_tiling(ctypes.byref(tb), ctypes.byref(st)), "lsf_get_pass_tiling")
+    return tb.value, st.value
+
+
 def lsf_profile_enable(on: bool) -> None:
     check(lib().lsf_profile_enable(int(bool(on))), "lsf_profile_enable")
 

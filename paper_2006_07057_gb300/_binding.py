@@ -80,6 +80,8 @@ _SIGNATURES = {
     "lsf_gradient": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), _P(LsfScalings),
                              _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lsf_set_pass_tiling": (c_int, [c_int, c_int]),
+    "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),
     "lsf_profile_enable": (c_int, [c_int]),
     "lsf_profile_read": (c_int, [c_int, _P(c_double), _P(c_int64), _P(c_double)]),
     "lsf_launch_count": (c_int64, []),

@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
       }
     }
 
+    // Each warp takes RW rows of a tile at once (rows rr and rr + kConsumerWarps):
+    // their chains of shared loads, FMAs and shuffles are independent, which hides
+    // latency with only two warps per SMSP. With two right-hand sides the two dot
+    // products of one row already give that independence.
+    constexpr int RW = (NRHS == 1) ? 2 : 1;
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
       const int s = it % S;
@@ -134,51 +139,75 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
       const int64_t row0 = tile * TR;
       const int rows = static_cast<int>(min(static_cast<int64_t>(TR), a.n - row0));
       const float* tF = sF + static_cast<size_t>(s) * TR * ldr;
-      for (int rr = warp; rr < rows; rr += kConsumerWarps) {
-        float4 f[C];
+      for (int rr = warp; rr < rows; rr += RW * kConsumerWarps) {
+        float4 f[RW][C];
+        bool valid[RW];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const int col = 4 * lane + 128 * j;
-          f[j] = (col < ldr) ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(rr) * ldr + col)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < RW; ++q) {
+          const int row = rr + q * kConsumerWarps;
+          valid[q] = row < rows;
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int col = 4 * lane + 128 * j;
+            f[q][j] = (valid[q] && col < ldr)
+                          ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(row) * ldr + col)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
           const float* vw = sV + static_cast<size_t>((s * NRHS + k) * 2) * TR;
           const float* vold = vw + TR;
-          float scale = 0.f;
+          float scale[RW];
           if (MODE == kPassAxpy) {
-            scale = vold[rr];
-          } else {
-            float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-              d0 = fmaf(f[j].x, t[k][j][0], d0);
-              d1 = fmaf(f[j].y, t[k][j][1], d1);
-              d0 = fmaf(f[j].z, t[k][j][2], d0);
-              d1 = fmaf(f[j].w, t[k][j][3], d1);
+            for (int q = 0; q < RW; ++q) scale[q] = valid[q] ? vold[rr + q * kConsumerWarps] : 0.f;
+          } else {
+            float dot[RW];
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+              float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+              for (int j = 0; j < C; ++j) {
+                d0 = fmaf(f[q][j].x, t[k][j][0], d0);
+                d1 = fmaf(f[q][j].y, t[k][j][1], d1);
+                d2 = fmaf(f[q][j].z, t[k][j][2], d2);
+                d3 = fmaf(f[q][j].w, t[k][j][3], d3);
+              }
+              dot[q] = (d0 + d1) + (d2 + d3);
             }
-            const float dot = warp_sum(d0 + d1);
-            const float wi = vw[rr];
-            if (has_old[k] && lane == 0)
-              res[k] += fabs(static_cast<double>(vold[rr]) * static_cast<double>(dot) -
-                             static_cast<double>(wi));
-            if (MODE == kPassUpdate) {
-              scale = wi / dot;
-              if (lane == 0) {
-                a.rhs[k].out[row0 + rr] = scale;
-                if (!(dot > 0.f) || !isfinite(scale)) flag |= LSF_ERR_NONFINITE;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+              for (int q = 0; q < RW; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+              const int row = rr + q * kConsumerWarps;
+              scale[q] = 0.f;
+              if (!valid[q]) continue;
+              const float wi = vw[row];
+              if (has_old[k] && lane == 0)
+                res[k] += fabs(static_cast<double>(vold[row]) * static_cast<double>(dot[q]) -
+                               static_cast<double>(wi));
+              if (MODE == kPassUpdate) {
+                scale[q] = wi * __frcp_rn(dot[q]);
+                if (lane == 0) {
+                  a.rhs[k].out[row0 + row] = scale[q];
+                  if (!(dot[q] > 0.f) || !isfinite(scale[q])) flag |= LSF_ERR_NONFINITE;
+                }
               }
             }
           }
           if (kAcc) {
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-              acc[k][j][0] = fmaf(scale, f[j].x, acc[k][j][0]);
-              acc[k][j][1] = fmaf(scale, f[j].y, acc[k][j][1]);
-              acc[k][j][2] = fmaf(scale, f[j].z, acc[k][j][2]);
-              acc[k][j][3] = fmaf(scale, f[j].w, acc[k][j][3]);
-            }
+            for (int q = 0; q < RW; ++q)
+#pragma unroll
+              for (int j = 0; j < C; ++j) {
+                acc[k][j][0] = fmaf(scale[q], f[q][j].x, acc[k][j][0]);
+                acc[k][j][1] = fmaf(scale[q], f[q][j].y, acc[k][j][1]);
+                acc[k][j][2] = fmaf(scale[q], f[q][j].z, acc[k][j][2]);
+                acc[k][j][3] = fmaf(scale[q], f[q][j].w, acc[k][j][3]);
+              }
           }
         }
       }
@@ -230,7 +259,23 @@ int launch_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaS
   return check_launch("pass_kernel");
 }
 
+int g_tile_bytes = 56 * 1024;
+int g_max_stages = 8;
+
 }  // namespace
+
+int set_pass_tiling(int tile_bytes, int max_stages) {
+  if (tile_bytes < 512 || tile_bytes > 128 * 1024 || max_stages < 2 || max_stages > 16)
+    return fail(LSF_ERR_ARG, "pass tiling: tile_bytes in [512, 131072], stages in [2, 16]");
+  g_tile_bytes = tile_bytes;
+  g_max_stages = max_stages;
+  return LSF_OK;
+}
+
+void get_pass_tiling(int* tile_bytes, int* max_stages) {
+  *tile_bytes = g_tile_bytes;
+  *max_stages = g_max_stages;
+}
 
 double pass_bytes(int mode, int nrhs, int64_t n, int ldr, bool with_old) {
   double per_row = 4.0 * ldr;
@@ -248,9 +293,11 @@ int launch_pass(int mode, int nrhs, PassArgs a, cudaStream_t st) {
   if (reinterpret_cast<uintptr_t>(a.F) % 16 != 0)
     return fail(LSF_ERR_ARG, "pass: features must be 16-byte aligned");
   const int64_t row_bytes = 4LL * a.ldr;
-  // Tile of consecutive rows: about 32 KB, but small enough to give every SM work.
-  int64_t tr = std::max<int64_t>(1, (32 * 1024) / row_bytes);
-  if (tr >= kConsumerWarps) tr -= tr % kConsumerWarps;  // whole rows for every consumer warp
+  // Tile of consecutive rows: about g_tile_bytes, a whole number of rows for
+  // every consumer warp, but small enough to give every SM work.
+  const int64_t unit = (nrhs == 1 ? 2 : 1) * kConsumerWarps;
+  int64_t tr = std::max<int64_t>(1, g_tile_bytes / row_bytes);
+  if (tr >= unit) tr -= tr % unit;
   const int64_t want_tiles = 2LL * dev.sms;
   if ((a.n + tr - 1) / tr < want_tiles) tr = std::max<int64_t>(1, (a.n + want_tiles - 1) / want_tiles);
   tr = std::min<int64_t>(tr, 256);
@@ -259,7 +306,7 @@ int launch_pass(int mode, int nrhs, PassArgs a, cudaStream_t st) {
   const size_t stage_bytes = static_cast<size_t>(tr * row_bytes) + static_cast<size_t>(nrhs) * 2 * tr * 4;
   const size_t static_smem = 1024;  // s_res and flags, with margin
   const size_t budget = static_cast<size_t>(dev.smem_optin) - static_smem;
-  int S = static_cast<int>(std::min<size_t>(8, (budget - 256) / stage_bytes));
+  int S = static_cast<int>(std::min<size_t>(static_cast<size_t>(g_max_stages), (budget - 256) / stage_bytes));
   if (S < 2) return fail(LSF_ERR_UNSUPPORTED, "pass: tile does not fit in shared memory");
   a.nstages = S;
   size_t smem = 128 * ((16 * S + 127) / 128) + S * stage_bytes;

@@ -39,6 +39,10 @@ struct PassArgs {
 // bytes_moved is the algorithmic traffic of the launch, recorded for profiling.
 int launch_pass(int mode, int nrhs, PassArgs args, cudaStream_t st);
 
+// Target tile size and maximum ring depth of the stored-feature pass (tuning).
+int set_pass_tiling(int tile_bytes, int max_stages);
+void get_pass_tiling(int* tile_bytes, int* max_stages);
+
 // Algorithmic bytes of one pass launch.
 double pass_bytes(int mode, int nrhs, int64_t n, int ldr, bool with_old);
 

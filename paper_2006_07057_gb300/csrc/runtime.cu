@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "pass.cuh"
 
 namespace lsf {
 
@@ -217,6 +218,16 @@ int lsf_profile_read(int kernel_class, double* total_ms, int64_t* launches, doub
   *total_ms = ms;
   *launches = cnt;
   *bytes = by;
+  return LSF_OK;
+}
+
+int lsf_set_pass_tiling(int tile_bytes, int max_stages) {
+  return set_pass_tiling(tile_bytes, max_stages);
+}
+
+int lsf_get_pass_tiling(int* tile_bytes, int* max_stages) {
+  if (!tile_bytes || !max_stages) return fail(LSF_ERR_ARG, "lsf_get_pass_tiling: NULL output");
+  get_pass_tiling(tile_bytes, max_stages);
   return LSF_OK;
 }
 

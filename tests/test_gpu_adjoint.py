@@ -1,0 +1,81 @@
+"""Adjoint kernels vs the oracle's envelope gradient (Prop. 3.3), through the C-ABI.
+
+The device and the oracle differentiate the same final iterate (same
+iterations, same theta held fixed), so the comparison is direct. Tolerance:
+relative error in the l2 norm of each gradient block 1e-4 (points) and
+elementwise 2e-4 (1 + |g|) for the weight gradients eps log u, which inherit
+the potentials' error. The oracle's formula itself is pinned against central
+differences at convergence in test_oracle_pins.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import oracle as o
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2006_07057_gb300 as m
+    m.lib()
+    return m
+
+
+def run_both(lsf, p, debiased):
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k))).cuda() for k in "XYabZ"}
+    prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps)
+    prob.run(p.iters, debiased=debiased)
+    g = [x.double().cpu().numpy() for x in prob.gradient()]
+    st = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=debiased)
+    ref = o.gradient(p.X, p.Y, p.a, p.b, st["theta"], st, debiased=debiased)
+    ref = ref["W_bar" if debiased else "W"]
+    return prob, g, ref
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("debiased", [False, True])
+@pytest.mark.parametrize("n,m,d,r,eps,iters", [
+    (1000, 1000, 2, 100, 0.5, 100),     # tiny workload shape
+    (700, 900, 3, 256, 0.2, 60),
+    (300, 257, 16, 1024, 1.0, 40),      # d = 16: warp-per-row kernel at its largest C
+    (200, 190, 48, 512, 1.0, 30),       # d = 48: tiled contraction, partial column tile
+    (1024, 1024, 128, 1024, 1.0, 50),   # differentiation workload shape at reduced n
+])
+def test_gradient_matches_oracle(lsf, n, m, d, r, eps, iters, debiased):
+    if d == 128:
+        p = synth.diff_problem(seed=0, n=n, iters=iters)
+    else:
+        p = synth.small_problem(31 + d, n, m, d, r, eps, iters, weights="dirichlet")
+    prob, (gX, gY, ga, gb), ref = run_both(lsf, p, debiased)
+    assert prob.values()["status"] == 0
+    assert rel_l2(gX, ref["X"]) <= 1e-4, rel_l2(gX, ref["X"])
+    assert rel_l2(gY, ref["Y"]) <= 1e-4, rel_l2(gY, ref["Y"])
+    assert np.all(np.abs(ga - ref["a"]) <= 2e-4 * (1 + np.abs(ref["a"])))
+    assert np.all(np.abs(gb - ref["b"]) <= 2e-4 * (1 + np.abs(ref["b"])))
+
+
+def test_autograd_function_matches_direct_gradient(lsf):
+    p = synth.small_problem(41, 500, 400, 3, 128, 0.3, 40, weights="dirichlet")
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k))).cuda() for k in "XYabZ"}
+    X = t["X"].clone().requires_grad_(True)
+    Y = t["Y"].clone().requires_grad_(True)
+    a = t["a"].clone().requires_grad_(True)
+    b = t["b"].clone().requires_grad_(True)
+    W = lsf.SinkhornDivergenceFn.apply(X, Y, a, b, t["Z"], p.eps, p.iters, True)
+    (2.0 * W).backward()
+    prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps)
+    prob.run(p.iters, debiased=True)
+    gX, gY, ga, gb = prob.gradient()
+    assert abs(W.item() - prob.values()["W_bar"]) <= 1e-6 * abs(prob.values()["W_bar"]) + 1e-7
+    torch.testing.assert_close(X.grad, 2.0 * gX)
+    torch.testing.assert_close(Y.grad, 2.0 * gY)
+    torch.testing.assert_close(a.grad, 2.0 * ga)
+    torch.testing.assert_close(b.grad, 2.0 * gb)
