@@ -188,6 +188,30 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  const lsf_scalings* s_yy, lsf_result* result, double* wbar,
                  void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * lsf_solve for callers that cannot allocate device memory. The paper has no
+ * counterpart; this exists for the library's users.
+ *
+ * Who needs it: code that runs inside a framework whose memory pool owns all of
+ * the device memory (an outside cudaMalloc breaks the pool's accounting and
+ * synchronises the whole device), or a latency-bound serving loop that must not
+ * block on the allocator. Such a caller still passes its inputs and outputs
+ * exactly as for lsf_solve, but no workspace.
+ *
+ * Scratch: a fixed 2 MiB array in the library's device image (kept by every GPU
+ * that loads the library until the process exits). Problems whose
+ * lsf_workspace_bytes(theta->ldr) exceeds 2 MiB are rejected with
+ * LSF_ERR_UNSUPPORTED and a message; nothing is allocated, ever.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture. Every call shares the one array: the solve clears
+ * the parts that must start at zero, and two calls that can overlap on the GPU
+ * (different streams, or different host threads) race on it and give wrong
+ * results. Results, errors and device status are those of lsf_solve.
+ */
+int lsf_solve_noalloc(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
+                      int mode, const lsf_scalings* out, lsf_result* result, void* stream);
+
 /* ---------------------------------------------------------------- adjoint */
 
 /*

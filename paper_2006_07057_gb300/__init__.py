@@ -192,6 +192,19 @@ def lsf_solve(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, out: Scal
                           workspace.numel(), _stream(stream)), "lsf_solve")
 
 
+def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, out: Scalings,
+                      result, stream=None):
+    """lsf_solve without a workspace, for callers that cannot allocate device memory.
+
+    The scratch comes from a fixed 2 MiB array inside the library; calls that can
+    overlap on the GPU share it and must not run concurrently.
+    """
+    th, cx, cy, so = theta.as_c(), x.as_c(), y.as_c(), out.as_c()
+    check(lib().lsf_solve_noalloc(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy),
+                                  int(iters), MODES[mode], ctypes.byref(so), _p(result),
+                                  _stream(stream)), "lsf_solve_noalloc")
+
+
 def lsf_debiased(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, s_xy: Scalings,
                  s_xx: Scalings, s_yy: Scalings, result, wbar, workspace, stream=None):
     th, cx, cy = theta.as_c(), x.as_c(), y.as_c()

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "lsf_divergence": (c_int, [_P(LsfTheta), c_int, _P(_P(LsfCloud)), _P(_P(LsfCloud)),
                                _P(_P(LsfScalings)), _P(c_void_p), _P(c_double), c_void_p,
                                c_void_p, c_size_t, c_void_p]),
+    "lsf_solve_noalloc": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
+                                  _P(LsfScalings), c_void_p, c_void_p]),
     "lsf_debiased": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                              _P(LsfScalings), _P(LsfScalings), _P(LsfScalings), c_void_p,
                              c_void_p, c_void_p, c_size_t, c_void_p]),
