@@ -50,7 +50,11 @@ typedef enum {
 /* Solver variants for the fused passes of Alg. 1 (Sec. 2) on K = xi zeta^T (Sec. 3.1). */
 typedef enum {
   LSF_MODE_STORED = 0,     /* stream stored shifted features F (HBM-bound)            */
-  LSF_MODE_RECOMPUTE = 1   /* recompute features from X, U in registers (ALU-bound)   */
+  LSF_MODE_RECOMPUTE = 1,  /* recompute features from X, U in registers (ALU-bound)   */
+  LSF_MODE_LOG = 2         /* stored LOG features, log-domain iterates (stabilised):
+                              F holds log features (lsf_log_features), the scalings
+                              u, v hold log u~, log v~, t_u, t_v hold log t, and the
+                              global factor M is 0                                    */
 } lsf_mode;
 
 /* Feature parameters theta = (U, c), shared by every term of Eq. (2). Device pointers. */
@@ -138,6 +142,16 @@ int lsf_anchors(const float* Z, int r, int d, double q, double sigma, double eps
 int lsf_features(const float* X, int64_t n, const lsf_theta* theta,
                  float* F, float* shift, float* spread, void* stream);
 
+/*
+ * Log form of the stored features, for LSF_MODE_LOG: L[i*ldr + k] = L_ik - shift[i]
+ * (<= 0) for k < r and -inf for r <= k < ldr. Same arguments as lsf_features.
+ * Used when the within-row spread max_k L_ik - min_k L_ik leaves the FP32 range
+ * of exp (the shifted features would underflow to 0 and a scaling could divide
+ * by zero).
+ */
+int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta,
+                     float* L, float* shift, float* spread, void* stream);
+
 /* As lsf_features but writes only shift (and spread): the RECOMPUTE prologue. */
 int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta,
                   float* shift, float* spread, void* stream);
@@ -170,10 +184,11 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
  *   result[t].W = eps (sum_i a_i log u_i + sum_j b_j log v_j)   (FP64 compensated sum)
  *   *combined   = sum_t coef[t] * result[t].W    (combined may be NULL)
  * With coef = {1, -1/2, -1/2} over (xy, xx, yy) this is Eq. (2).
+ * mode: the lsf_mode the scalings were produced in (LSF_MODE_LOG scalings are logs).
  */
 int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* xs,
                    const lsf_cloud* const* ys, const lsf_scalings* const* s,
-                   lsf_result* const* result, const double* coef, double* combined,
+                   lsf_result* const* result, const double* coef, double* combined, int mode,
                    void* workspace, size_t ws_bytes, void* stream);
 
 /*
@@ -198,9 +213,9 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
  * block on the allocator. Such a caller still passes its inputs and outputs
  * exactly as for lsf_solve, but no workspace.
  *
- * Scratch: a fixed 2 MiB array in the library's device image (kept by every GPU
+ * Scratch: a fixed 8 MiB array in the library's device image (kept by every GPU
  * that loads the library until the process exits). Problems whose
- * lsf_workspace_bytes(theta->ldr) exceeds 2 MiB are rejected with
+ * lsf_workspace_bytes(theta->ldr) exceeds 8 MiB are rejected with
  * LSF_ERR_UNSUPPORTED and a message; nothing is allocated, ever.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
@@ -211,6 +226,71 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
  */
 int lsf_solve_noalloc(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
                       int mode, const lsf_scalings* out, lsf_result* result, void* stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/*
+ * Many independent problems W(a_p, b_p) (Eq. 6 after Alg. 1 on each problem's
+ * K_p = xi_p zeta_p^T) solved together by one persistent, cooperative kernel:
+ * every half iteration streams the rows of all problems' features through the
+ * same shared-memory ring, so small problems do not leave SMs idle and no
+ * kernel is launched per problem and per half iteration. All problems of one
+ * batch share ldr (group problems by feature width); n, m, d, r <= ldr and eps
+ * may differ. Features are stored (lsf_features) and stay resident.
+ * Device pointers in each record; result: one lsf_result per problem (W,
+ * residual, log_scale, status filled in).
+ */
+typedef struct {
+  const float* Fx;       /* n x ldr shifted features of X   */
+  const float* Fy;       /* m x ldr shifted features of Y   */
+  const float* shift_x;  /* n                              */
+  const float* shift_y;  /* m                              */
+  const float* a;        /* n weights                      */
+  const float* b;        /* m weights                      */
+  int64_t n, m;
+  double eps;
+  float* u;              /* n   u~ (output)                */
+  float* v;              /* m   v~ (output)                */
+  float* t_u;            /* ldr (output)                   */
+  float* t_v;            /* ldr (output)                   */
+  lsf_result* result;    /* 1 record (output)              */
+} lsf_batch_problem;
+
+/* Host description of a batch plan (filled by lsf_batch_plan). */
+typedef struct {
+  int count;          /* problems                                  */
+  int ldr;            /* common row stride                         */
+  int tile_rows;      /* rows per shared-memory tile               */
+  int stages;         /* copy-ring depth                           */
+  int grid;           /* CTAs of the persistent kernel (co-resident) */
+  int64_t tiles_x;    /* tiles over all X-side rows                */
+  int64_t tiles_y;    /* tiles over all Y-side rows                */
+  int64_t rows_x;     /* sum of n over the batch                   */
+  int64_t rows_y;     /* sum of m over the batch                   */
+  size_t plan_bytes;  /* device plan size                          */
+  size_t smem_bytes;  /* dynamic shared memory of the kernel       */
+} lsf_batch_info;
+
+/*
+ * Plan a batch: choose the tiling (tile_bytes = 0 picks the default; the
+ * autotuner passes candidates), partition the concatenated tiles of all problems
+ * over the CTAs, and lay out the device plan (problem table, tile tables,
+ * partial buffers, arrival counters, round flags). With plan == NULL only
+ * *info is filled (to size the buffer); otherwise the plan (info->plan_bytes,
+ * device, 256-byte aligned) is written with a copy that completes before
+ * return. probs: host array of `count` records.
+ */
+int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int tile_bytes,
+                   lsf_batch_info* info, void* plan, size_t plan_bytes, void* stream);
+
+/*
+ * Run `iters` iterations of Alg. 1 on every problem of a planned batch, then the
+ * residual pass and Eq. (6): a start kernel (v = 1 per problem), one persistent
+ * cooperative kernel for all half iterations (problems advance independently,
+ * ordered by per-problem round flags with bounded waits), and a reduction
+ * kernel. Only kernel launches: capturable in a CUDA graph.
+ */
+int lsf_solve_batched(const lsf_batch_info* info, void* plan, int iters, void* stream);
 
 /* ---------------------------------------------------------------- adjoint */
 
@@ -223,12 +303,14 @@ int lsf_solve_noalloc(const lsf_theta* theta, const lsf_cloud* x, const lsf_clou
  * With debiased != 0 the gradient is that of Eq. (2): the self terms W(a,a),
  * W(b,b) (kernel xi xi^T, X on both sides) enter with weight -1/2, using
  * s_xx, s_yy and result[1], result[2].
+ * mode: LSF_MODE_STORED (F = xi~) or LSF_MODE_LOG (F, scalings and r-vectors
+ * in log form); the recompute mode keeps no features and is not supported.
  * gX (n x d), gY (m x d), ga (n), gb (m): device outputs (any may be NULL).
  * result: device array of 1 (or 3 when debiased) lsf_result from the solve.
  */
 int lsf_gradient(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  const lsf_scalings* s_xy, const lsf_scalings* s_xx,
-                 const lsf_scalings* s_yy, const lsf_result* result, int debiased,
+                 const lsf_scalings* s_yy, const lsf_result* result, int debiased, int mode,
                  float* gX, float* gY, float* ga, float* gb, void* stream);
 
 /* ---------------------------------------------------------------- tuning */
@@ -252,6 +334,8 @@ typedef enum {
   LSF_KERNEL_PASS_RECOMPUTE, /* fused Sinkhorn passes (recompute)         */
   LSF_KERNEL_FEATURES,       /* feature build and row shifts              */
   LSF_KERNEL_OTHER,          /* small kernels: init, reductions, adjoint  */
+  LSF_KERNEL_PASS_LOG,       /* fused Sinkhorn passes (log domain)        */
+  LSF_KERNEL_BATCHED,        /* batched persistent solver                 */
   LSF_KERNEL_NCLASSES
 } lsf_kernel_class;
 

@@ -20,12 +20,21 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_FEATURES,  # noqa: F401
-                       LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_RECOMPUTE,
-                       LSF_MODE_RECOMPUTE, LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError,
-                       LsfResult, LsfScalings, LsfTheta, check, header_symbols, lib)
+from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_BATCHED,  # noqa: F401
+                       LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
+                       LsfBatchInfo, LsfBatchProblem,
+                       LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
+                       LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
+                       LsfTheta, check, header_symbols, lib)
 
-MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE}
+MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG}
+
+# "auto" routes a problem straight to the log domain when the within-row
+# log-feature spread exceeds this many nats. Shifted features only underflow
+# harmlessly below that (most problems with spreads of several hundred nats still
+# solve in FP32 scaling form); the decisive check is the device status: a run
+# that reports a non-finite scaling is repeated in the log domain.
+LOG_SPREAD = 4000.0
 
 RESULT_DTYPE = np.dtype([("W", "<f8"), ("residual", "<f8"), ("log_scale", "<f8"),
                          ("status", "<i4"), ("iters", "<i4")])
@@ -156,6 +165,19 @@ def lsf_features(X, theta: Theta, F=None, shift=None, spread=None, stream=None):
     return F, shift
 
 
+def lsf_log_features(X, theta: Theta, L=None, shift=None, spread=None, stream=None):
+    _f32(X)
+    n = X.shape[0]
+    if L is None:
+        L = torch.empty(n, theta.ldr, dtype=torch.float32, device=X.device)
+    if shift is None:
+        shift = torch.empty(n, dtype=torch.float32, device=X.device)
+    th = theta.as_c()
+    check(lib().lsf_log_features(_p(X), n, ctypes.byref(th), _p(L), _p(shift), _p(spread),
+                                 _stream(stream)), "lsf_log_features")
+    return L, shift
+
+
 def lsf_row_shift(X, theta: Theta, shift=None, spread=None, stream=None):
     _f32(X)
     n = X.shape[0]
@@ -196,7 +218,7 @@ def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, o
                       result, stream=None):
     """lsf_solve without a workspace, for callers that cannot allocate device memory.
 
-    The scratch comes from a fixed 2 MiB array inside the library; calls that can
+    The scratch comes from a fixed 8 MiB array inside the library; calls that can
     overlap on the GPU share it and must not run concurrently.
     """
     th, cx, cy, so = theta.as_c(), x.as_c(), y.as_c(), out.as_c()
@@ -216,7 +238,7 @@ def lsf_debiased(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, s_xy: 
 
 
 def lsf_divergence(theta: Theta, xs, ys, ss, results, coef=None, combined=None, workspace=None,
-                   stream=None):
+                   stream=None, mode: str = "stored"):
     k = len(xs)
     th = theta.as_c()
     cx = [c.as_c() for c in xs]
@@ -228,13 +250,13 @@ def lsf_divergence(theta: Theta, xs, ys, ss, results, coef=None, combined=None, 
     PR = (ctypes.c_void_p * k)(*[r.data_ptr() for r in results])
     co = (ctypes.c_double * k)(*(coef if coef is not None else [1.0] * k))
     check(lib().lsf_divergence(ctypes.byref(th), k, PX, PY, PS, PR, co, _p(combined),
-                               _p(workspace), workspace.numel(), _stream(stream)),
+                               MODES[mode], _p(workspace), workspace.numel(), _stream(stream)),
           "lsf_divergence")
 
 
 def lsf_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: Scalings | None,
                  s_yy: Scalings | None, result, debiased: bool, gX=None, gY=None, ga=None,
-                 gb=None, stream=None):
+                 gb=None, stream=None, mode: str = "stored"):
     th, cx, cy = theta.as_c(), x.as_c(), y.as_c()
     a = s_xy.as_c()
     b = s_xx.as_c() if s_xx is not None else None
@@ -242,7 +264,8 @@ def lsf_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: Scaling
     check(lib().lsf_gradient(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy),
                              ctypes.byref(a), ctypes.byref(b) if b else None,
                              ctypes.byref(c) if c else None, _p(result), int(bool(debiased)),
-                             _p(gX), _p(gY), _p(ga), _p(gb), _stream(stream)), "lsf_gradient")
+                             MODES[mode], _p(gX), _p(gY), _p(ga), _p(gb), _stream(stream)),
+          "lsf_gradient")
 
 
 def lsf_set_pass_tiling(tile_bytes: int, max_stages: int) -> None:
@@ -290,22 +313,27 @@ class SinkhornProblem:
     """One divergence problem kept resident on the device.
 
     Builds theta (R from both clouds, q and sigma from Lemma 1, anchors
-    U = sigma Z), the row shifts and, in stored mode, the shifted features of
-    both clouds; allocates scalings for the three solves of Eq. (2), result
-    records and the workspace. ``run`` launches the solve asynchronously;
-    ``values`` reads the scalars back.
+    U = sigma Z), the row shifts and the stored features of both clouds
+    (shifted features for ``mode="stored"``, their logs for ``mode="log"``,
+    none for ``mode="recompute"``); allocates scalings for the three solves of
+    Eq. (2), result records and the workspace. ``run`` launches the solve
+    asynchronously; ``values`` reads the scalars back.
+
+    ``mode="auto"`` starts in the scaling domain and moves to the log domain
+    when the within-row log-feature spread exceeds ``LOG_SPREAD`` or when a run
+    reports a non-finite scaling (the run is then repeated in the log domain).
     """
 
     def __init__(self, X, Y, a, b, Z, eps: float, mode: str = "stored", ldr: int | None = None,
-                 theta: Theta | None = None, stream=None):
-        if mode not in MODES:
-            raise ValueError(f"mode must be one of {sorted(MODES)}")
+                 theta: Theta | None = None, stream=None, scalings: bool = True):
+        if mode not in MODES and mode != "auto":
+            raise ValueError(f"mode must be one of {sorted(MODES) + ['auto']}")
         for t in (X, Y, a, b, Z):
             _f32(t)
         self.X, self.Y, self.a, self.b, self.Z = X, Y, a, b, Z
         self.eps = float(eps)
-        self.mode = mode
         self.stream = stream
+        self.auto = mode == "auto"
         dev = X.device
         n, d = X.shape
         m = Y.shape[0]
@@ -319,30 +347,61 @@ class SinkhornProblem:
         self.theta = theta
         ldr = theta.ldr
         self.spread = torch.zeros(1, dtype=torch.float32, device=dev)
-        if mode == "stored":
-            Fx, sx = lsf_features(X, theta, spread=self.spread, stream=stream)
-            Fy, sy = lsf_features(Y, theta, spread=self.spread, stream=stream)
-        else:
-            Fx = Fy = None
-            sx = lsf_row_shift(X, theta, spread=self.spread, stream=stream)
-            sy = lsf_row_shift(Y, theta, spread=self.spread, stream=stream)
-        self.x = Cloud(X, Fx, sx, a)
-        self.y = Cloud(Y, Fy, sy, b)
+        self.mode = "stored" if self.auto else mode
+        self._build_features()
+        if self.auto and float(self.spread.item()) > LOG_SPREAD:
+            self.switch_mode("log")
+        self.debiased = None
+        self.iters = None
+        if not scalings:
+            return
         self.s_xy = Scalings.alloc(n, m, ldr, dev)
         self.s_xx = Scalings.alloc(n, n, ldr, dev)
         self.s_yy = Scalings.alloc(m, m, ldr, dev)
         self.results = alloc_results(3, dev)
         self.wbar = torch.zeros(1, dtype=torch.float64, device=dev)
         self.workspace = alloc_workspace(ldr, dev)
-        self.debiased = None
+
+    def _build_features(self):
+        X, Y, th, st = self.X, self.Y, self.theta, self.stream
+        if self.mode == "stored":
+            Fx, sx = lsf_features(X, th, spread=self.spread, stream=st)
+            Fy, sy = lsf_features(Y, th, spread=self.spread, stream=st)
+        elif self.mode == "log":
+            Fx, sx = lsf_log_features(X, th, spread=self.spread, stream=st)
+            Fy, sy = lsf_log_features(Y, th, spread=self.spread, stream=st)
+        else:
+            Fx = Fy = None
+            sx = lsf_row_shift(X, th, spread=self.spread, stream=st)
+            sy = lsf_row_shift(Y, th, spread=self.spread, stream=st)
+        self.x = Cloud(X, Fx, sx, self.a)
+        self.y = Cloud(Y, Fy, sy, self.b)
+
+    def switch_mode(self, mode: str) -> None:
+        """Rebuild the features for another solver mode (same theta)."""
+        if mode != self.mode:
+            self.mode = mode
+            self._build_features()
 
     def result_view(self, k: int) -> torch.Tensor:
         return self.results[k * RESULT_BYTES:(k + 1) * RESULT_BYTES]
 
     def run(self, iters: int, debiased: bool = True) -> None:
-        """Launch the solve (and Eq. (6)/(2) reductions) on the stream; no host sync."""
+        """Launch the solve (and Eq. (6)/(2) reductions) on the stream.
+
+        No host synchronisation, except in ``auto`` mode, which reads the status
+        back to decide whether to repeat the run in the log domain.
+        """
         self.debiased = bool(debiased)
-        if debiased:
+        self.iters = iters
+        self._launch(iters)
+        if self.auto and self.mode != "log":
+            if read_results(self.results)[0]["status"] & LSF_ERR_NONFINITE:
+                self.switch_mode("log")
+                self._launch(iters)
+
+    def _launch(self, iters: int) -> None:
+        if self.debiased:
             lsf_debiased(self.theta, self.x, self.y, iters, self.mode, self.s_xy, self.s_xx,
                          self.s_yy, self.results, self.wbar, self.workspace, self.stream)
         else:
@@ -350,34 +409,45 @@ class SinkhornProblem:
             lsf_solve(self.theta, self.x, self.y, iters, self.mode, self.s_xy, r0,
                       self.workspace, self.stream)
             lsf_divergence(self.theta, [self.x], [self.y], [self.s_xy], [r0], [1.0], self.wbar,
-                           self.workspace, self.stream)
+                           self.workspace, self.stream, mode=self.mode)
 
     def values(self) -> dict:
         """Host copy of the results of the last run (synchronises)."""
         recs = read_results(self.results)
         out = {"W_xy": recs[0]["W"], "res_xy": recs[0]["residual"], "status": recs[0]["status"],
-               "iters": recs[0]["iters"], "records": recs}
+               "iters": recs[0]["iters"], "records": recs, "mode": self.mode}
         out["W"] = float(self.wbar.item())
         if self.debiased:
             out.update(W_xx=recs[1]["W"], W_yy=recs[2]["W"], res_xx=recs[1]["residual"],
                        res_yy=recs[2]["residual"], W_bar=out["W"])
         return out
 
+    def log_potentials(self, which: str = "xy"):
+        """log u, log v of a solve (undoing the row shifts and the global factor M)."""
+        k = {"xy": 0, "xx": 1, "yy": 2}[which]
+        s = {"xy": self.s_xy, "xx": self.s_xx, "yy": self.s_yy}[which]
+        xs = self.x.shift if which in ("xy", "xx") else self.y.shift
+        ys = self.y.shift if which in ("xy", "yy") else self.x.shift
+        M = read_results(self.results)[k]["log_scale"]
+        lu = s.u.double() if self.mode == "log" else torch.log(s.u.double())
+        lv = s.v.double() if self.mode == "log" else torch.log(s.v.double())
+        return lu - xs.double() - M, lv - ys.double() + M
+
     def gradient(self, debiased: bool | None = None):
         """Envelope gradient of the last run w.r.t. X, Y, a, b (theta fixed)."""
         deb = self.debiased if debiased is None else bool(debiased)
         if deb and not self.debiased:
             raise ValueError("the debiased gradient needs a debiased run")
+        if self.mode == "recompute":
+            raise NotImplementedError("the adjoint reads stored features")
         dev = self.X.device
         gX = torch.empty_like(self.X)
         gY = torch.empty_like(self.Y)
         ga = torch.empty(self.x.n, dtype=torch.float32, device=dev)
         gb = torch.empty(self.y.n, dtype=torch.float32, device=dev)
-        if self.mode != "stored":
-            raise NotImplementedError("the adjoint reads stored features")
         lsf_gradient(self.theta, self.x, self.y, self.s_xy, self.s_xx if deb else None,
                      self.s_yy if deb else None, self.results, deb, gX, gY, ga, gb,
-                     self.stream)
+                     self.stream, mode=self.mode)
         return gX, gY, ga, gb
 
 
@@ -410,3 +480,83 @@ class SinkhornDivergenceFn(torch.autograd.Function):
     def backward(ctx, g):
         gX, gY, ga, gb = ctx.prob.gradient()
         return gX * g, gY * g, ga * g, gb * g, None, None, None, None
+
+
+# ---------------------------------------------------------------- batched solver
+
+def lsf_batch_plan(records, ldr: int, tile_bytes: int = 0, stream=None):
+    """Plan a batch; returns (info, plan tensor). records: list of LsfBatchProblem."""
+    arr = (LsfBatchProblem * len(records))(*records)
+    info = LsfBatchInfo()
+    check(lib().lsf_batch_plan(arr, len(records), int(ldr), int(tile_bytes), ctypes.byref(info),
+                               None, 0, _stream(stream)), "lsf_batch_plan")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buf = torch.empty(info.plan_bytes + 256, dtype=torch.uint8, device=dev)
+    off = (-buf.data_ptr()) % 256
+    plan = buf[off:off + info.plan_bytes]
+    check(lib().lsf_batch_plan(arr, len(records), int(ldr), int(tile_bytes), ctypes.byref(info),
+                               _p(plan), plan.numel(), _stream(stream)), "lsf_batch_plan")
+    return info, plan
+
+
+def lsf_solve_batched(info, plan, iters: int, stream=None) -> None:
+    check(lib().lsf_solve_batched(ctypes.byref(info), _p(plan), int(iters), _stream(stream)),
+          "lsf_solve_batched")
+
+
+class BatchedSolver:
+    """Many independent problems W(a_p, b_p), all sharing one feature width ldr.
+
+    Builds each problem's theta and stored features (one launch per cloud), then
+    solves all problems with the persistent batched kernel. ``problems``: list of
+    objects with X, Y, a, b, Z (CUDA float32 tensors) and eps. ``tile_bytes=None``
+    asks the autotuner.
+    """
+
+    def __init__(self, problems, ldr: int | None = None, tile_bytes: int | None = None,
+                 stream=None):
+        self.stream = stream
+        rs = {int(p.Z.shape[0]) for p in problems}
+        self.ldr = ldr if ldr is not None else ldr_for(max(rs))
+        self.problems = []
+        recs = []
+        dev = problems[0].X.device
+        self.results = alloc_results(len(problems), dev)
+        for k, p in enumerate(problems):
+            prob = SinkhornProblem(p.X, p.Y, p.a, p.b, p.Z, p.eps, mode="stored", ldr=self.ldr,
+                                   stream=stream, scalings=False)
+            s = Scalings.alloc(prob.x.n, prob.y.n, self.ldr, dev)
+            prob.s_xy = s
+            self.problems.append(prob)
+            recs.append(LsfBatchProblem(
+                _p(prob.x.F).value, _p(prob.y.F).value, _p(prob.x.shift).value,
+                _p(prob.y.shift).value, _p(prob.x.w).value, _p(prob.y.w).value, prob.x.n,
+                prob.y.n, float(p.eps), _p(s.u).value, _p(s.v).value, _p(s.t_u).value,
+                _p(s.t_v).value, self.results.data_ptr() + k * RESULT_BYTES))
+        self.records = recs
+        if tile_bytes is None:
+            from .autotune import best_batch_tile
+            tile_bytes = best_batch_tile(self)
+        self.tile_bytes = tile_bytes
+        self.info, self.plan = lsf_batch_plan(recs, self.ldr, tile_bytes, stream)
+        self.graph = None
+
+    def run(self, iters: int) -> None:
+        lsf_solve_batched(self.info, self.plan, iters, self.stream)
+
+    def capture(self, iters: int) -> None:
+        """Capture one batched solve (start, persistent kernel, reduction) in a CUDA graph."""
+        self.run(iters)  # warm-up outside the capture (module loading, attributes)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                lsf_solve_batched(self.info, self.plan, iters, s)
+        self.graph = g
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def values(self) -> list[dict]:
+        return read_results(self.results)

@@ -29,11 +29,14 @@ LSF_ERR_UNSUPPORTED = 32
 
 LSF_MODE_STORED = 0
 LSF_MODE_RECOMPUTE = 1
+LSF_MODE_LOG = 2
 
 LSF_KERNEL_PASS = 0
 LSF_KERNEL_PASS_RECOMPUTE = 1
 LSF_KERNEL_FEATURES = 2
 LSF_KERNEL_OTHER = 3
+LSF_KERNEL_PASS_LOG = 4
+LSF_KERNEL_BATCHED = 5
 
 
 class LsfTheta(ctypes.Structure):
@@ -57,6 +60,19 @@ class LsfResult(ctypes.Structure):
 
 RESULT_BYTES = ctypes.sizeof(LsfResult)
 
+
+class LsfBatchProblem(ctypes.Structure):
+    _fields_ = [("Fx", c_void_p), ("Fy", c_void_p), ("shift_x", c_void_p), ("shift_y", c_void_p),
+                ("a", c_void_p), ("b", c_void_p), ("n", c_int64), ("m", c_int64),
+                ("eps", c_double), ("u", c_void_p), ("v", c_void_p), ("t_u", c_void_p),
+                ("t_v", c_void_p), ("result", c_void_p)]
+
+
+class LsfBatchInfo(ctypes.Structure):
+    _fields_ = [("count", c_int), ("ldr", c_int), ("tile_rows", c_int), ("stages", c_int),
+                ("grid", c_int), ("tiles_x", c_int64), ("tiles_y", c_int64), ("rows_x", c_int64),
+                ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t)]
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "lsf_version": (c_int, []),
@@ -68,20 +84,25 @@ _SIGNATURES = {
     "lsf_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
                              c_void_p]),
     "lsf_row_shift": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p]),
+    "lsf_log_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
+                                 c_void_p]),
     "lsf_workspace_bytes": (c_int, [c_int, _P(c_size_t)]),
     "lsf_solve": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                           _P(LsfScalings), c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_divergence": (c_int, [_P(LsfTheta), c_int, _P(_P(LsfCloud)), _P(_P(LsfCloud)),
                                _P(_P(LsfScalings)), _P(c_void_p), _P(c_double), c_void_p,
-                               c_void_p, c_size_t, c_void_p]),
+                               c_int, c_void_p, c_size_t, c_void_p]),
     "lsf_solve_noalloc": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                                   _P(LsfScalings), c_void_p, c_void_p]),
     "lsf_debiased": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                              _P(LsfScalings), _P(LsfScalings), _P(LsfScalings), c_void_p,
                              c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_gradient": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), _P(LsfScalings),
-                             _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_void_p,
-                             c_void_p, c_void_p, c_void_p, c_void_p]),
+                             _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_int,
+                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lsf_batch_plan": (c_int, [_P(LsfBatchProblem), c_int, c_int, c_int, _P(LsfBatchInfo),
+                               c_void_p, c_size_t, c_void_p]),
+    "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),
     "lsf_set_pass_tiling": (c_int, [c_int, c_int]),
     "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),
     "lsf_profile_enable": (c_int, [c_int]),

@@ -10,6 +10,8 @@
 // Terms p for the X cloud: W(a,b): (u~_xy, t_v_xy) with coef 1; debiased adds
 // W(a,a) (kernel xi xi^T): (u~_xx, t_v_xx) and (v~_xx, t_u_xx) with coef -1/2.
 // The Y cloud is symmetric. Weights: grad a = eps log u (Eq. 5, alpha* = eps log u*).
+// In the log domain (LOGD) F, alpha and T hold logs and each term is formed as
+// exp(L~_ik + f_i + lt_k), a coupling mass that stays in range.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -35,7 +37,7 @@ struct AdjArgs {
 
 // Warp-per-row: lane l owns columns 4l + 128j; U^T (d x ldr) and the T vectors
 // sit in shared memory; the d + 1 row sums are butterfly reductions.
-template <int C>
+template <int C, bool LOGD>
 __global__ void __launch_bounds__(256) adjoint_rows_kernel(const AdjArgs a) {
   extern __shared__ __align__(16) float sm[];
   float* sUT = sm;                                        // [d][ldr]
@@ -56,7 +58,8 @@ __global__ void __launch_bounds__(256) adjoint_rows_kernel(const AdjArgs a) {
        i += warps) {
     float al[kMaxTerms];
 #pragma unroll
-    for (int p = 0; p < kMaxTerms; ++p) al[p] = (p < a.nterms) ? a.coef[p] * a.alpha[p][i] : 0.f;
+    for (int p = 0; p < kMaxTerms; ++p)
+      al[p] = (p < a.nterms) ? (LOGD ? a.alpha[p][i] : a.coef[p] * a.alpha[p][i]) : 0.f;
     float rs = 0.f;
     float g[kRowsDMax];
 #pragma unroll
@@ -67,16 +70,31 @@ __global__ void __launch_bounds__(256) adjoint_rows_kernel(const AdjArgs a) {
       const int col = 4 * lane + 128 * j;
       if (col >= ldr) continue;
       const float4 f = *reinterpret_cast<const float4*>(Fi + col);
-      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (LOGD) {
 #pragma unroll
-      for (int p = 0; p < kMaxTerms; ++p) {
-        if (p < a.nterms) {
-          const float4 t = *reinterpret_cast<const float4*>(sT + static_cast<size_t>(p) * ldr + col);
-          w.x = fmaf(al[p], t.x, w.x); w.y = fmaf(al[p], t.y, w.y);
-          w.z = fmaf(al[p], t.z, w.z); w.w = fmaf(al[p], t.w, w.w);
+        for (int p = 0; p < kMaxTerms; ++p) {
+          if (p < a.nterms) {
+            const float4 t = *reinterpret_cast<const float4*>(sT + static_cast<size_t>(p) * ldr + col);
+            const float c = a.coef[p];
+            A.x = fmaf(c, ex2_approx((f.x + al[p] + t.x) * kLog2e), A.x);
+            A.y = fmaf(c, ex2_approx((f.y + al[p] + t.y) * kLog2e), A.y);
+            A.z = fmaf(c, ex2_approx((f.z + al[p] + t.z) * kLog2e), A.z);
+            A.w = fmaf(c, ex2_approx((f.w + al[p] + t.w) * kLog2e), A.w);
+          }
         }
+      } else {
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < kMaxTerms; ++p) {
+          if (p < a.nterms) {
+            const float4 t = *reinterpret_cast<const float4*>(sT + static_cast<size_t>(p) * ldr + col);
+            w.x = fmaf(al[p], t.x, w.x); w.y = fmaf(al[p], t.y, w.y);
+            w.z = fmaf(al[p], t.z, w.z); w.w = fmaf(al[p], t.w, w.w);
+          }
+        }
+        A = make_float4(f.x * w.x, f.y * w.y, f.z * w.z, f.w * w.w);
       }
-      const float4 A = make_float4(f.x * w.x, f.y * w.y, f.z * w.z, f.w * w.w);
       rs += (A.x + A.y) + (A.z + A.w);
 #pragma unroll
       for (int dd = 0; dd < kRowsDMax; ++dd) {
@@ -102,6 +120,7 @@ __global__ void __launch_bounds__(256) adjoint_rows_kernel(const AdjArgs a) {
 // the n x d result, k-tiles of 32 features. A_ik is formed while staging F.
 constexpr int kBM = 64, kBN = 128, kBK = 32;
 
+template <bool LOGD>
 __global__ void __launch_bounds__(256) adjoint_gemm_kernel(const AdjArgs a) {
   __shared__ __align__(16) float As[kBK][kBM + 4];
   __shared__ __align__(16) float Bs[kBK][kBN];
@@ -115,7 +134,7 @@ __global__ void __launch_bounds__(256) adjoint_gemm_kernel(const AdjArgs a) {
   for (int idx = tid; idx < kMaxTerms * kBM; idx += blockDim.x) {
     const int p = idx / kBM, rr = idx - p * kBM;
     const int64_t i = m0 + rr;
-    sAl[p][rr] = (p < a.nterms && i < a.n) ? a.coef[p] * a.alpha[p][i] : 0.f;
+    sAl[p][rr] = (p < a.nterms && i < a.n) ? (LOGD ? a.alpha[p][i] : a.coef[p] * a.alpha[p][i]) : 0.f;
   }
   __syncthreads();
   // loader roles: A tile: row lr = tid / 4, k-offset lk = (tid % 4) * 8 (8 values)
@@ -135,11 +154,19 @@ __global__ void __launch_bounds__(256) adjoint_gemm_kernel(const AdjArgs a) {
       const int k = k0 + lk + q;
       float v = 0.f;
       if (arow < a.n && k < ldr) {
-        float w = 0.f;
+        const float fv = __ldg(a.F + arow * ldr + k);
+        if (LOGD) {
 #pragma unroll
-        for (int p = 0; p < kMaxTerms; ++p)
-          if (p < a.nterms) w = fmaf(sAl[p][lr], __ldg(a.T[p] + k), w);
-        v = __ldg(a.F + arow * ldr + k) * w;
+          for (int p = 0; p < kMaxTerms; ++p)
+            if (p < a.nterms)
+              v = fmaf(a.coef[p], ex2_approx((fv + sAl[p][lr] + __ldg(a.T[p] + k)) * kLog2e), v);
+        } else {
+          float w = 0.f;
+#pragma unroll
+          for (int p = 0; p < kMaxTerms; ++p)
+            if (p < a.nterms) w = fmaf(sAl[p][lr], __ldg(a.T[p] + k), w);
+          v = fv * w;
+        }
       }
       As[lk + q][lr] = v;
       rs_part += v;
@@ -195,6 +222,7 @@ struct WeightArgs {
   int64_t n;
   double eps;
   float* g;
+  int is_log;  // the scalings hold logs
 };
 
 __global__ void weight_grad_kernel(const WeightArgs a) {
@@ -203,12 +231,14 @@ __global__ void weight_grad_kernel(const WeightArgs a) {
     double v = 0.0;
     for (int p = 0; p < a.nterms; ++p) {
       const double M = a.res[p]->log_scale;
-      v += a.coef[p] * (static_cast<double>(logf(a.s[p][i])) - a.shift[i] - a.sign[p] * M);
+      const double ls = a.is_log ? static_cast<double>(a.s[p][i]) : static_cast<double>(logf(a.s[p][i]));
+      v += a.coef[p] * (ls - a.shift[i] - a.sign[p] * M);
     }
     a.g[i] = static_cast<float>(a.eps * v);
   }
 }
 
+template <bool LOGD>
 int launch_points(const AdjArgs& a, cudaStream_t st) {
   if (a.d <= kRowsDMax) {
     const int C = (a.ldr + 127) / 128;
@@ -219,9 +249,9 @@ int launch_points(const AdjArgs& a, cudaStream_t st) {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 4.0 * a.n * (a.ldr + 2 * a.d + a.nterms));
 #define LSF_ADJ_CASE(CC)                                                                    \
   case CC: {                                                                                \
-    cudaFuncSetAttribute(adjoint_rows_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)smem);                                                        \
-    adjoint_rows_kernel<CC><<<(unsigned)grid, 256, smem, st>>>(a);                          \
+    cudaFuncSetAttribute(adjoint_rows_kernel<CC, LOGD>,                                     \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    adjoint_rows_kernel<CC, LOGD><<<(unsigned)grid, 256, smem, st>>>(a);                    \
   } break;
     switch (C <= 1 ? 1 : C <= 2 ? 2 : C <= 4 ? 4 : 8) {
       LSF_ADJ_CASE(1)
@@ -234,7 +264,7 @@ int launch_points(const AdjArgs& a, cudaStream_t st) {
   }
   dim3 grid(static_cast<unsigned>((a.n + kBM - 1) / kBM), static_cast<unsigned>((a.d + kBN - 1) / kBN));
   LaunchScope ls(st, LSF_KERNEL_OTHER, 4.0 * a.n * (a.ldr + 2 * a.d + a.nterms));
-  adjoint_gemm_kernel<<<grid, 256, 0, st>>>(a);
+  adjoint_gemm_kernel<LOGD><<<grid, 256, 0, st>>>(a);
   return check_launch("adjoint_gemm_kernel");
 }
 
@@ -253,13 +283,16 @@ using namespace lsf;
 extern "C" int lsf_gradient(const lsf_theta* th, const lsf_cloud* x, const lsf_cloud* y,
                             const lsf_scalings* s_xy, const lsf_scalings* s_xx,
                             const lsf_scalings* s_yy, const lsf_result* result, int debiased,
-                            float* gX, float* gY, float* ga, float* gb, void* stream) {
+                            int mode, float* gX, float* gY, float* ga, float* gb, void* stream) {
   if (!th || !x || !y || !s_xy || !result) return fail(LSF_ERR_ARG, "lsf_gradient: NULL argument");
   if (debiased && (!s_xx || !s_yy))
     return fail(LSF_ERR_ARG, "lsf_gradient: the debiased gradient needs s_xx and s_yy");
   if (th->r < 1 || th->d < 1 || th->r > th->ldr || th->ldr % 4 != 0 || th->ldr > 1024 || !th->U)
     return fail(LSF_ERR_ARG, "lsf_gradient: bad theta");
   if (x->n < 1 || y->n < 1) return fail(LSF_ERR_ARG, "lsf_gradient: empty measure");
+  if (mode != LSF_MODE_STORED && mode != LSF_MODE_LOG)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_gradient: needs stored (or stored log) features");
+  const bool logd = mode == LSF_MODE_LOG;
   if ((gX && (!x->F || !x->X)) || (gY && (!y->F || !y->X)))
     return fail(LSF_ERR_ARG, "lsf_gradient: point gradients need X and stored features F");
   if ((x->F && reinterpret_cast<uintptr_t>(x->F) % 16) || (y->F && reinterpret_cast<uintptr_t>(y->F) % 16))
@@ -288,12 +321,12 @@ extern "C" int lsf_gradient(const lsf_theta* th, const lsf_cloud* x, const lsf_c
         a.alpha[2] = self->v; a.T[2] = self->t_u; a.coef[2] = -0.5f;
         a.nterms = 3;
       }
-      int rc = launch_points(a, st);
+      int rc = logd ? launch_points<true>(a, st) : launch_points<false>(a, st);
       if (rc != LSF_OK) return rc;
     }
     if (gw) {
       WeightArgs w{};
-      w.shift = cl->shift; w.n = cl->n; w.eps = th->eps; w.g = gw;
+      w.shift = cl->shift; w.n = cl->n; w.eps = th->eps; w.g = gw; w.is_log = logd ? 1 : 0;
       w.s[0] = side == 0 ? s_xy->u : s_xy->v;
       w.res[0] = rxy;
       w.sign[0] = side == 0 ? 1.0 : -1.0;

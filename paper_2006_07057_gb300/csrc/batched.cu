@@ -1,0 +1,618 @@
+// Batched solver: many independent problems, Alg. 1 on each, one persistent
+// cooperative kernel for all half iterations.
+//
+// Rows of all problems' features on one side are cut into tiles that never
+// straddle two problems; the tile list of a side is split into contiguous ranges,
+// one per CTA, identical in every round on that side. A round is one half
+// iteration of every problem (round 0: t_v = zeta~^T v~ from the start vector;
+// odd rounds: u-halves on the X side; even rounds: v-halves on the Y side; the
+// last round: the residual pass on the X side). The copy ring streams the tiles
+// of all rounds back to back, so the next round's features are in flight while
+// the current one finishes. Consumers work as in the single-problem stored pass;
+// when their tile moves to another problem they flush their partial r-vector for
+// the old one and take the new one's right-hand side once that problem has
+// finished the previous round (per-problem round flag, bounded wait). The last
+// warp to flush a problem sums its partials in a fixed order, writes the new
+// r-vector and raises the flag: problems advance independently, and results do
+// not depend on timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "reduce.cuh"
+#include "ring.cuh"
+
+namespace lsf {
+namespace {
+
+struct BProb {
+  const float* F[2];      // side 0: X (xi~), side 1: Y (zeta~)
+  const float* w[2];      // a, b
+  const float* shift[2];
+  float* s[2];            // u~, v~
+  float* t[2];            // t_u = xi~^T u~ (written by X rounds), t_v = zeta~^T v~
+  lsf_result* result;
+  int64_t n[2];
+  double eps;
+  float* part[2];         // [nslots][kConsumerWarps][ldr] partial r-vectors
+  double* rpart;          // [nslots_x][kConsumerWarps] residual partials
+  int first_cta[2];
+  int nslots[2];          // slots first_cta .. last owner (empty CTAs in between stay zero)
+  int nown[2];            // CTAs that own tiles of this problem: each flushes once per round
+};
+
+struct BTile {
+  int p;
+  int rows;
+  int64_t row0;
+};
+
+struct BatchArgs {
+  BProb* probs;
+  const BTile* tiles[2];
+  int64_t ntiles[2];
+  unsigned* counter;  // [count] warp arrivals of the current round
+  unsigned* flag;     // [count] rounds completed
+  int count;
+  int ldr;
+  int tile_rows;
+  int nstages;
+  int rounds;
+};
+
+__device__ __forceinline__ int round_side(int r, int rounds) {
+  if (r == 0) return 1;               // start: t_v from v~
+  if (r == rounds - 1) return 0;      // residual on X
+  return (r & 1) ? 0 : 1;             // u-halves on X, v-halves on Y
+}
+__device__ __forceinline__ int round_mode(int r, int rounds) {
+  if (r == 0) return kPassAxpy;
+  if (r == rounds - 1) return kPassDot;
+  return kPassUpdate;
+}
+__device__ __forceinline__ void tile_range(int64_t ntiles, int64_t* lo, int64_t* hi) {
+  *lo = ntiles * blockIdx.x / gridDim.x;
+  *hi = ntiles * (blockIdx.x + 1) / gridDim.x;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int C>
+__global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArgs A) {
+  constexpr int RW = 8 / C;
+  constexpr int SH = RowFold<RW>::kShift;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int ldr = A.ldr;
+  const Ring ring = ring_layout(smem, A.nstages, A.tile_rows, ldr);
+  const int S = ring.S;
+  const int TR = ring.TR;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  __shared__ int s_flag;
+  if (threadIdx.x == 0) {
+    ring_init(ring, kConsumerWarps);
+    fence_mbarrier_init();
+    s_flag = 0;
+  }
+  __syncthreads();
+  int flag = 0;
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    int it = 0;
+    bool dead = false;
+    for (int r = 0; r < A.rounds && !dead; ++r) {
+      const int side = round_side(r, A.rounds);
+      const bool copy_w = round_mode(r, A.rounds) != kPassAxpy;
+      int64_t lo, hi;
+      tile_range(A.ntiles[side], &lo, &hi);
+      for (int64_t ti = lo; ti < hi; ++ti, ++it) {
+        const int s = it % S;
+        const uint32_t ph = static_cast<uint32_t>(it / S) & 1u;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&ring.empty[s], ph ^ 1u) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          flag |= LSF_ERR_TIMEOUT;
+          dead = true;
+          break;
+        }
+        const BTile tl = A.tiles[side][ti];
+        const BProb& pb = A.probs[tl.p];
+        if (lane == 0) {
+          const uint32_t bytes = static_cast<uint32_t>(tl.rows) * static_cast<uint32_t>(ldr) * 4u;
+          mbar_arrive_expect_tx(&ring.full[s], bytes);
+          bulk_copy_g2s(ring.sF + static_cast<size_t>(s) * TR * ldr, pb.F[side] + tl.row0 * ldr, bytes,
+                        &ring.full[s]);
+        }
+        if (copy_w) {
+          float* dw = ring.sV + static_cast<size_t>(s * 2) * TR;
+          const float* w = pb.w[side];
+          for (int i = lane; i < tl.rows; i += 32) cp_async_4(dw + i, w + tl.row0 + i);
+        }
+        cp_async_mbar_arrive(&ring.full[s]);
+      }
+    }
+    const int used = min(it, S);
+    for (int j = 0; j < used; ++j) {
+      const int itj = it - 1 - j;
+      if (lane == 0 && !mbar_wait_bounded(&ring.full[itj % S], static_cast<uint32_t>(itj / S) & 1u))
+        flag |= LSF_ERR_TIMEOUT;
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int myq = (lane >> SH) & (RW - 1);
+    const bool owner = (lane & ((1 << SH) - 1)) == 0;
+    int it = 0;
+    bool dead = false;
+    for (int r = 0; r < A.rounds && !dead; ++r) {
+      const int side = round_side(r, A.rounds);
+      const int mode = round_mode(r, A.rounds);
+      int64_t lo, hi;
+      tile_range(A.ntiles[side], &lo, &hi);
+      int cur = -1;
+      float t[C][4], acc[C][4];
+      double res = 0.0;
+      auto flush = [&](int p) {
+        // this warp's partial r-vector (and residual) for problem p, this round
+        const BProb& pb = A.probs[p];
+        const int slot = static_cast<int>(blockIdx.x) - pb.first_cta[side];
+        float* dst = pb.part[side] + (static_cast<size_t>(slot) * kConsumerWarps + warp) * ldr;
+        if (mode != kPassDot) {
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int col = 4 * lane + 128 * j;
+            if (col < ldr)
+              *reinterpret_cast<float4*>(dst + col) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+          }
+        } else {
+          double rr = res;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+          if (lane == 0) pb.rpart[static_cast<size_t>(slot) * kConsumerWarps + warp] = rr;
+        }
+        __threadfence();
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+          const unsigned need = static_cast<unsigned>(pb.nown[side]) * kConsumerWarps;
+          last = (atomicAdd(&A.counter[p], 1u) == need - 1u) ? 1u : 0u;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return;
+        __threadfence();
+        const int nparts = pb.nslots[side] * kConsumerWarps;
+        if (mode != kPassDot) {
+          float* tout = pb.t[side];
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int col = 4 * lane + 128 * j;
+            if (col >= ldr) continue;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int q = 0; q < nparts; ++q) {
+              const float4 v = __ldcg(reinterpret_cast<const float4*>(pb.part[side] + static_cast<size_t>(q) * ldr + col));
+              s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+            }
+            *reinterpret_cast<float4*>(tout + col) =
+                make_float4(static_cast<float>(s0), static_cast<float>(s1), static_cast<float>(s2),
+                            static_cast<float>(s3));
+          }
+        } else if (lane == 0) {
+          double tot = 0.0;
+          for (int q = 0; q < nparts; ++q) tot += __ldcg(pb.rpart + q);
+          pb.result->residual = tot;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+          A.counter[p] = 0u;
+          __threadfence();
+          st_release(&A.flag[p], static_cast<unsigned>(r + 1));
+        }
+      };
+
+      for (int64_t ti = lo; ti < hi && !dead; ++ti, ++it) {
+        const int s = it % S;
+        if (!ring_wait_full(ring, it, lane)) {
+          flag |= LSF_ERR_TIMEOUT;
+          dead = true;
+          break;
+        }
+        const BTile tl = A.tiles[side][ti];
+        if (tl.p != cur) {
+          if (cur >= 0) flush(cur);
+          cur = tl.p;
+          // wait until problem cur has finished the previous round
+          int ok = 1;
+          if (lane == 0 && r > 0) {
+            const unsigned* fp = A.flag + cur;
+            if (ld_acquire(fp) < static_cast<unsigned>(r)) {
+              const uint64_t t0 = globaltimer_ns();
+              while (ld_acquire(fp) < static_cast<unsigned>(r)) {
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                  ok = 0;
+                  break;
+                }
+              }
+            }
+          }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            flag |= LSF_ERR_TIMEOUT;
+            dead = true;
+          }
+          const BProb& pb = A.probs[cur];
+          const float* tin = pb.t[1 - side];
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int col = 4 * lane + 128 * j;
+            float4 tv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mode != kPassAxpy && col < ldr) tv = __ldcg(reinterpret_cast<const float4*>(tin + col));
+            t[j][0] = tv.x; t[j][1] = tv.y; t[j][2] = tv.z; t[j][3] = tv.w;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+          }
+          res = 0.0;
+        }
+        if (!dead) {
+          const BProb& pb = A.probs[cur];
+          const int rows = tl.rows;
+          const float* tF = ring.sF + static_cast<size_t>(s) * TR * ldr;
+          const float* vw = ring.sV + static_cast<size_t>(s * 2) * TR;
+          float* sc_out = pb.s[side];
+          for (int rr = warp * RW; rr < rows; rr += RW * kConsumerWarps) {
+            float4 f[RW][C];
+#pragma unroll
+            for (int q = 0; q < RW; ++q)
+#pragma unroll
+              for (int j = 0; j < C; ++j) {
+                const int col = 4 * lane + 128 * j;
+                f[q][j] = (rr + q < rows && col < ldr)
+                              ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(rr + q) * ldr + col)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+            float scale[RW];
+            if (mode == kPassAxpy) {
+              // the given start vector, written before this kernel
+              float g = 0.f;
+              const int row = rr + myq;
+              if (owner && row < rows) g = sc_out[tl.row0 + row];
+#pragma unroll
+              for (int q = 0; q < RW; ++q) scale[q] = __shfl_sync(0xffffffffu, g, q << SH);
+            } else {
+              float p[RW];
+#pragma unroll
+              for (int q = 0; q < RW; ++q) {
+                float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                  d0 = fmaf(f[q][j].x, t[j][0], d0);
+                  d1 = fmaf(f[q][j].y, t[j][1], d1);
+                  d0 = fmaf(f[q][j].z, t[j][2], d0);
+                  d1 = fmaf(f[q][j].w, t[j][3], d1);
+                }
+                p[q] = d0 + d1;
+              }
+              const float dot = fold_rows<RW>(p, lane, OpAdd());
+              const int row = rr + myq;
+              float sc = 0.f;
+              if (row < rows) {
+                const float wi = vw[row];
+                if (mode == kPassDot) {
+                  // residual: the previous scaling was written by this same lane in
+                  // the last u-half (the X-side partition is the same every round)
+                  if (owner)
+                    res += fabs(static_cast<double>(sc_out[tl.row0 + row]) * static_cast<double>(dot) -
+                                static_cast<double>(wi));
+                } else {
+                  sc = wi * __frcp_rn(dot);
+                  if (owner) {
+                    sc_out[tl.row0 + row] = sc;
+                    if (!(dot > 0.f) || !isfinite(sc)) {
+                      flag |= LSF_ERR_NONFINITE;
+                      atomicOr(&pb.result->status, LSF_ERR_NONFINITE);
+                    }
+                  }
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < RW; ++q) scale[q] = __shfl_sync(0xffffffffu, sc, q << SH);
+            }
+            if (mode != kPassDot) {
+#pragma unroll
+              for (int q = 0; q < RW; ++q)
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                  acc[j][0] = fmaf(scale[q], f[q][j].x, acc[j][0]);
+                  acc[j][1] = fmaf(scale[q], f[q][j].y, acc[j][1]);
+                  acc[j][2] = fmaf(scale[q], f[q][j].z, acc[j][2]);
+                  acc[j][3] = fmaf(scale[q], f[q][j].w, acc[j][3]);
+                }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring.empty[s]);
+      }
+      if (cur >= 0 && !dead) flush(cur);
+    }
+  }
+  if (flag) atomicOr(&s_flag, flag);
+  __syncthreads();
+  // timeouts are reported on every problem's record (which problem stalled is not known)
+  if ((s_flag & LSF_ERR_TIMEOUT) && threadIdx.x == 0)
+    for (int p = 0; p < A.count; ++p) atomicOr(&A.probs[p].result->status, LSF_ERR_TIMEOUT);
+}
+
+// v = 1 per problem: v~ = exp(shift_y - M_p); also resets the round state.
+__global__ void __launch_bounds__(256) batched_start_kernel(BProb* probs, unsigned* counter,
+                                                            unsigned* flag, int iters) {
+  const BProb pb = probs[blockIdx.x];
+  __shared__ float s_m[8];
+  float m = -INFINITY;
+  for (int64_t j = threadIdx.x; j < pb.n[1]; j += blockDim.x) m = fmaxf(m, pb.shift[1][j]);
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float M = s_m[0];
+  for (int w = 1; w < 8; ++w) M = fmaxf(M, s_m[w]);
+  for (int64_t j = threadIdx.x; j < pb.n[1]; j += blockDim.x) pb.s[1][j] = expf(pb.shift[1][j] - M);
+  if (threadIdx.x == 0) {
+    pb.result->W = 0.0;
+    pb.result->residual = 0.0;
+    pb.result->log_scale = static_cast<double>(M);
+    pb.result->status = 0;
+    pb.result->iters = iters;
+    counter[blockIdx.x] = 0u;
+    flag[blockIdx.x] = 0u;
+  }
+}
+
+// Eq. (6) per problem with an FP64 compensated sum (one block per problem).
+__global__ void __launch_bounds__(256) batched_divergence_kernel(const BProb* probs) {
+  const BProb pb = probs[blockIdx.x];
+  const double M = pb.result->log_scale;
+  KahanSum acc;
+  for (int side = 0; side < 2; ++side) {
+    const double sign = side == 0 ? 1.0 : -1.0;
+    for (int64_t i = threadIdx.x; i < pb.n[side]; i += blockDim.x)
+      acc.add(static_cast<double>(pb.w[side][i]) *
+              (static_cast<double>(logf(pb.s[side][i])) - pb.shift[side][i] - sign * M));
+  }
+  __shared__ double s_w[8];
+  double v = acc.value();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    KahanSum tot;
+    for (int w = 0; w < 8; ++w) tot.add(s_w[w]);
+    pb.result->W = pb.eps * tot.value();
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct PlanLayout {
+  size_t probs, tiles_x, tiles_y, counter, flag, part_x, part_y, rpart, total;
+};
+
+}  // namespace
+}  // namespace lsf
+
+using namespace lsf;
+
+extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int tile_bytes,
+                              lsf_batch_info* info, void* plan, size_t plan_bytes, void* stream) {
+  if (!probs || !info) return fail(LSF_ERR_ARG, "lsf_batch_plan: NULL argument");
+  if (count < 1) return fail(LSF_ERR_ARG, "lsf_batch_plan: count must be >= 1");
+  if (ldr < 4 || ldr % 4 != 0 || ldr > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: ldr must be a multiple of 4 in [4, 1024]");
+  for (int p = 0; p < count; ++p) {
+    const lsf_batch_problem& q = probs[p];
+    if (q.n < 1 || q.m < 1) return fail(LSF_ERR_ARG, "problem %d: empty measure", p);
+    if (!q.Fx || !q.Fy || !q.shift_x || !q.shift_y || !q.a || !q.b || !q.u || !q.v || !q.t_u ||
+        !q.t_v || !q.result)
+      return fail(LSF_ERR_ARG, "problem %d: NULL pointer", p);
+    if (reinterpret_cast<uintptr_t>(q.Fx) % 16 || reinterpret_cast<uintptr_t>(q.Fy) % 16 ||
+        reinterpret_cast<uintptr_t>(q.t_u) % 16 || reinterpret_cast<uintptr_t>(q.t_v) % 16)
+      return fail(LSF_ERR_ARG, "problem %d: F and t vectors must be 16-byte aligned", p);
+    if (!(q.eps > 0.0)) return fail(LSF_ERR_ARG, "problem %d: eps must be > 0", p);
+  }
+  const DeviceInfo& dev = device_info();
+  const int C = pass_columns(ldr);
+  const int RW = 8 / C;
+  const int64_t row_bytes = 4LL * ldr;
+  const int64_t unit = static_cast<int64_t>(RW) * kConsumerWarps;
+  int tb = tile_bytes > 0 ? tile_bytes : 44 * 1024;
+  int64_t tr = std::max<int64_t>(unit, (tb / row_bytes) / unit * unit);
+  tr = std::min<int64_t>(tr, 1024);
+  const size_t stage_bytes = static_cast<size_t>(tr * row_bytes) + 2 * tr * 4;
+  const size_t budget = static_cast<size_t>(dev.smem_optin) - 4096;
+  int S = static_cast<int>(std::min<size_t>(8, (budget - 256) / stage_bytes));
+  if (S < 2) return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: tile does not fit in shared memory");
+  const size_t smem = ring_bytes(S, tr, ldr, 1);
+
+  // co-resident grid (the kernel's CTAs wait on one another)
+  int per_sm = 0;
+  cudaFuncSetAttribute(batched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(batched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(batched_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*kern)(BatchArgs) = C == 1 ? batched_kernel<1> : C == 2 ? batched_kernel<2>
+                          : C == 4 ? batched_kernel<4> : batched_kernel<8>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPassThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: kernel cannot be resident");
+  const int grid = dev.sms * std::min(per_sm, 1);
+
+  // tiles and CTA partition per side
+  std::vector<BTile> tiles[2];
+  for (int side = 0; side < 2; ++side)
+    for (int p = 0; p < count; ++p) {
+      const int64_t n = side == 0 ? probs[p].n : probs[p].m;
+      for (int64_t r0 = 0; r0 < n; r0 += tr)
+        tiles[side].push_back(BTile{p, static_cast<int>(std::min<int64_t>(tr, n - r0)), r0});
+    }
+  std::vector<int> first[2], last[2], nown[2];
+  for (int side = 0; side < 2; ++side) {
+    first[side].assign(count, -1);
+    last[side].assign(count, -1);
+    nown[side].assign(count, 0);
+    const int64_t T = static_cast<int64_t>(tiles[side].size());
+    for (int c = 0; c < grid; ++c) {
+      const int64_t lo = T * c / grid, hi = T * (c + 1) / grid;
+      int prev = -1;
+      for (int64_t ti = lo; ti < hi; ++ti) {
+        const int p = tiles[side][ti].p;
+        if (first[side][p] < 0) first[side][p] = c;
+        last[side][p] = c;
+        if (p != prev) ++nown[side][p];
+        prev = p;
+      }
+    }
+  }
+  size_t nslot_total[2] = {0, 0};
+  for (int side = 0; side < 2; ++side)
+    for (int p = 0; p < count; ++p) nslot_total[side] += last[side][p] - first[side][p] + 1;
+
+  PlanLayout L{};
+  size_t off = 0;
+  L.probs = off; off += align256(sizeof(BProb) * count);
+  L.tiles_x = off; off += align256(sizeof(BTile) * tiles[0].size());
+  L.tiles_y = off; off += align256(sizeof(BTile) * tiles[1].size());
+  L.counter = off; off += align256(sizeof(unsigned) * count);
+  L.flag = off; off += align256(sizeof(unsigned) * count);
+  L.part_x = off; off += align256(sizeof(float) * nslot_total[0] * kConsumerWarps * ldr);
+  L.part_y = off; off += align256(sizeof(float) * nslot_total[1] * kConsumerWarps * ldr);
+  L.rpart = off; off += align256(sizeof(double) * nslot_total[0] * kConsumerWarps);
+  L.total = off;
+
+  info->count = count;
+  info->ldr = ldr;
+  info->tile_rows = static_cast<int>(tr);
+  info->stages = S;
+  info->grid = grid;
+  info->tiles_x = static_cast<int64_t>(tiles[0].size());
+  info->tiles_y = static_cast<int64_t>(tiles[1].size());
+  info->rows_x = 0;
+  info->rows_y = 0;
+  for (int p = 0; p < count; ++p) {
+    info->rows_x += probs[p].n;
+    info->rows_y += probs[p].m;
+  }
+  info->plan_bytes = L.total;
+  info->smem_bytes = smem;
+  if (!plan) return LSF_OK;
+  if (plan_bytes < L.total) return fail(LSF_ERR_WORKSPACE, "batch plan needs %zu bytes", L.total);
+  if (reinterpret_cast<uintptr_t>(plan) % 256) return fail(LSF_ERR_ARG, "batch plan must be 256-byte aligned");
+
+  char* base = static_cast<char*>(plan);
+  std::vector<char> host(L.tiles_y + sizeof(BTile) * tiles[1].size(), 0);
+  BProb* hp = reinterpret_cast<BProb*>(host.data() + L.probs);
+  size_t px = 0, py = 0, pr = 0;
+  for (int p = 0; p < count; ++p) {
+    const lsf_batch_problem& q = probs[p];
+    BProb b{};
+    b.F[0] = q.Fx; b.F[1] = q.Fy;
+    b.w[0] = q.a; b.w[1] = q.b;
+    b.shift[0] = q.shift_x; b.shift[1] = q.shift_y;
+    b.s[0] = q.u; b.s[1] = q.v;
+    b.t[0] = q.t_u; b.t[1] = q.t_v;
+    b.result = q.result;
+    b.n[0] = q.n; b.n[1] = q.m;
+    b.eps = q.eps;
+    for (int side = 0; side < 2; ++side) {
+      b.first_cta[side] = first[side][p];
+      b.nslots[side] = last[side][p] - first[side][p] + 1;
+      b.nown[side] = nown[side][p];
+    }
+    b.part[0] = reinterpret_cast<float*>(base + L.part_x) + px * kConsumerWarps * ldr;
+    b.part[1] = reinterpret_cast<float*>(base + L.part_y) + py * kConsumerWarps * ldr;
+    b.rpart = reinterpret_cast<double*>(base + L.rpart) + pr * kConsumerWarps;
+    px += b.nslots[0];
+    py += b.nslots[1];
+    pr += b.nslots[0];
+    hp[p] = b;
+  }
+  std::copy(tiles[0].begin(), tiles[0].end(), reinterpret_cast<BTile*>(host.data() + L.tiles_x));
+  std::copy(tiles[1].begin(), tiles[1].end(), reinterpret_cast<BTile*>(host.data() + L.tiles_y));
+  cudaStream_t st = as_stream(stream);
+  if (cudaMemcpyAsync(plan, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(base + L.counter, 0, L.total - L.counter, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "lsf_batch_plan: copy of the plan failed");
+  return LSF_OK;
+}
+
+extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int iters, void* stream) {
+  if (!info || !plan) return fail(LSF_ERR_ARG, "lsf_solve_batched: NULL argument");
+  if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+  cudaStream_t st = as_stream(stream);
+  char* base = static_cast<char*>(plan);
+  // rebuild the layout offsets exactly as lsf_batch_plan did
+  const int count = info->count;
+  size_t off = 0;
+  const size_t o_probs = off; off += align256(sizeof(BProb) * count);
+  const size_t o_tx = off; off += align256(sizeof(BTile) * info->tiles_x);
+  const size_t o_ty = off; off += align256(sizeof(BTile) * info->tiles_y);
+  const size_t o_counter = off; off += align256(sizeof(unsigned) * count);
+  const size_t o_flag = off;
+  BatchArgs A{};
+  A.probs = reinterpret_cast<BProb*>(base + o_probs);
+  A.tiles[0] = reinterpret_cast<const BTile*>(base + o_tx);
+  A.tiles[1] = reinterpret_cast<const BTile*>(base + o_ty);
+  A.ntiles[0] = info->tiles_x;
+  A.ntiles[1] = info->tiles_y;
+  A.counter = reinterpret_cast<unsigned*>(base + o_counter);
+  A.flag = reinterpret_cast<unsigned*>(base + o_flag);
+  A.count = count;
+  A.ldr = info->ldr;
+  A.tile_rows = info->tile_rows;
+  A.nstages = info->stages;
+  A.rounds = 2 * iters + 2;
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    batched_start_kernel<<<count, 256, 0, st>>>(A.probs, A.counter, A.flag, iters);
+  }
+  int rc = check_launch("batched_start_kernel");
+  if (rc != LSF_OK) return rc;
+  const int C = pass_columns(info->ldr);
+  void (*kern)(BatchArgs) = C == 1 ? batched_kernel<1> : C == 2 ? batched_kernel<2>
+                          : C == 4 ? batched_kernel<4> : batched_kernel<8>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem_bytes);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(info->grid);
+  cfg.blockDim = dim3(kPassThreads);
+  cfg.dynamicSmemBytes = info->smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  {
+    // algorithmic bytes: every feature row once per round (X side in iters + 1
+    // rounds, Y side in iters + 1), plus weights and scalings (12 B per row)
+    const double bytes = static_cast<double>(iters + 1) *
+                         (static_cast<double>(info->rows_x) + static_cast<double>(info->rows_y)) *
+                         (4.0 * info->ldr + 12.0);
+    LaunchScope ls(st, LSF_KERNEL_BATCHED, bytes);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A);
+    if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "batched kernel launch: %s", cudaGetErrorString(e));
+  }
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    batched_divergence_kernel<<<count, 256, 0, st>>>(A.probs);
+  }
+  return check_launch("batched_divergence_kernel");
+}

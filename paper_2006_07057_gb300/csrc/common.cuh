@@ -41,7 +41,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // Workspace layout shared by the solver entry points (all offsets 256-aligned).
 struct Workspace {
-  float* part;          // [grid][2][ldr] per-CTA partial r-vectors
+  float* part;          // [grid][2][2][ldr] per-CTA partial r-vectors (log passes: max and sum)
   double* rpart;        // [grid][2] per-CTA partial residuals
   double* dpart;        // [div_grid][3] per-block partial divergences
   unsigned* counters;   // [8] arrival counters of the last-CTA reductions
@@ -51,11 +51,16 @@ struct Workspace {
 size_t workspace_bytes(int ldr);
 int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws);
 
+// Most CTAs any pass may launch: the workspace holds one partial r-vector slot per
+// CTA, so every pass launcher clamps its grid to this.
+int max_pass_ctas();
+constexpr int kMaxPassCtasPerSm = 2;
+
 constexpr int kDivGrid = 64;
 
 // ---------------------------------------------------------------- device side
 
-constexpr int kConsumerWarps = 7;  // + 1 producer warp: 2 warps per SMSP, 255 registers each
+constexpr int kConsumerWarps = 11;  // + 1 producer warp: 3 warps per SMSP, up to 168 registers
 constexpr int kPassThreads = (kConsumerWarps + 1) * 32;
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per bounded wait
 
@@ -152,6 +157,15 @@ __device__ __forceinline__ float warp_min(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+
+// Hardware base-2 exponential (MUFU ex2, flushes subnormal results to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
 
 // Order-preserving map float -> unsigned (0 sorts below every finite float).
 __device__ __forceinline__ unsigned float_key(float f) {

@@ -47,8 +47,10 @@ __global__ void anchors_kernel(const float* __restrict__ Z, int r, int d, double
 
 // Warp-per-row feature kernel. Lane l owns columns 4l + 128j + e (j < C, e < 4).
 // U is staged transposed in shared memory (d-chunk x ldr) so that lanes read
-// consecutive columns. STORE = false computes only the row shifts.
-template <int C, bool STORE>
+// consecutive columns. KIND 0 computes only the row shifts, KIND 1 stores
+// F = exp(L - shift) (padding 0), KIND 2 stores the log form L - shift
+// (padding -inf) for the log-domain passes.
+template <int C, int KIND>
 __global__ void __launch_bounds__(kFeatWarps * 32)
     features_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ U,
                     const float* __restrict__ c, int r, int ldr, float two_over_eps,
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
       mn = warp_min(mn);
       if (lane == 0) shift[i] = mx;
       local_spread = fmaxf(local_spread, mx - mn);
-      if (STORE) {
+      if (KIND == 1) {
         float* Fi = F + i * ldr;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -149,6 +151,20 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
             *reinterpret_cast<float4*>(Fi + col) = o;
           }
         }
+      } else if (KIND == 2) {
+        float* Fi = F + i * ldr;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const int col = 4 * lane + 128 * j;
+          if (col < ldr) {
+            float4 o;
+            o.x = (col + 0 < r) ? acc[q][j][0] - mx : -INFINITY;
+            o.y = (col + 1 < r) ? acc[q][j][1] - mx : -INFINITY;
+            o.z = (col + 2 < r) ? acc[q][j][2] - mx : -INFINITY;
+            o.w = (col + 3 < r) ? acc[q][j][3] - mx : -INFINITY;
+            *reinterpret_cast<float4*>(Fi + col) = o;
+          }
+        }
       }
     }
   }
@@ -157,9 +173,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
     atomicMax(spread_key, __float_as_uint(local_spread));
 }
 
-template <bool STORE>
+template <int KIND>
 int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
                     float* spread, cudaStream_t st) {
+  constexpr bool STORE = KIND != 0;
   if (!X || !th || !shift || (STORE && !F)) return fail(LSF_ERR_ARG, "features: NULL argument");
   if (!th->U || !th->c) return fail(LSF_ERR_ARG, "features: theta has NULL U or c");
   if (n < 1) return fail(LSF_ERR_ARG, "features: n must be >= 1");
@@ -184,7 +201,7 @@ int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, fl
   LaunchScope ls(st, LSF_KERNEL_FEATURES, bytes);
 #define LSF_FEAT_CASE(CC)                                                                  \
   case CC: {                                                                               \
-    auto kern = features_kernel<CC, STORE>;                                                \
+    auto kern = features_kernel<CC, KIND>;                                                \
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
     kern<<<(unsigned)grid, kFeatWarps * 32, smem, st>>>(X, n, th->d, th->U, th->c, th->r,  \
                                                         ldr, toe, F, shift, skey);         \
@@ -239,13 +256,17 @@ int lsf_anchors(const float* Z, int r, int d, double q, double sigma, double eps
 
 int lsf_features(const float* X, int64_t n, const lsf_theta* theta, float* F, float* shift,
                  float* spread, void* stream) {
-  int rc = launch_features<true>(X, n, theta, F, shift, spread, as_stream(stream));
-  return rc;
+  return launch_features<1>(X, n, theta, F, shift, spread, as_stream(stream));
+}
+
+int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta, float* L, float* shift,
+                     float* spread, void* stream) {
+  return launch_features<2>(X, n, theta, L, shift, spread, as_stream(stream));
 }
 
 int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta, float* shift,
                   float* spread, void* stream) {
-  return launch_features<false>(X, n, theta, nullptr, shift, spread, as_stream(stream));
+  return launch_features<0>(X, n, theta, nullptr, shift, spread, as_stream(stream));
 }
 
 }  // extern "C"

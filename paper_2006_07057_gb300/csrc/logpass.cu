@@ -1,0 +1,258 @@
+// Log-domain fused Sinkhorn pass (stabilised variant).
+//
+// The same half iteration of Alg. 1 as the stored-feature pass, on the log form
+// of everything, for problems whose features or scalings leave the FP32 range:
+//   stored rows  L~_ik = log phi_theta(x_i)_k - shift_i   (<= 0, padding -inf)
+//   r-vector     lt_k  = log t_k                          (padding -inf)
+//   scaling      f_i   = log u~_i
+// The row product becomes log s_i = LSE_k(L~_ik + lt_k), the division
+// f_i = log w_i - log s_i, and the transposed product
+// lt'_k = LSE_i(L~_ik + f_i). Every log-sum-exp is shifted by its maximum, so no
+// term under- or overflows.
+//
+// Layout is that of the stored pass (same copy ring; a warp takes RW = 8/C rows at
+// full width): the RW row maxima and then the shifted row sums are folded across
+// the warp by the multi-row butterfly; the column side keeps a running (max, sum)
+// pair per column, merged once per RW rows, and warps then CTAs are merged in a
+// fixed order at the end.
+#include <cuda_runtime.h>
+
+#include "reduce.cuh"
+#include "ring.cuh"
+
+namespace lsf {
+namespace {
+
+template <int C, int NRHS, int MODE>
+__global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs a) {
+  constexpr int RW = 8 / C;
+  constexpr int SH = RowFold<RW>::kShift;
+  constexpr bool kNeedT = MODE != kPassAxpy;
+  constexpr bool kAcc = MODE != kPassDot;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int ldr = a.ldr;
+  const Ring ring = ring_layout(smem, a.nstages, a.tile_rows, ldr);
+  const int S = ring.S;
+  const int TR = ring.TR;
+
+  __shared__ __align__(16) float s_lt[NRHS][128 * C];  // log t (padding -inf)
+  __shared__ double s_res[kConsumerWarps][2];
+  __shared__ int s_flag;
+  __shared__ int s_last;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    ring_init(ring, kConsumerWarps);
+    fence_mbarrier_init();
+    s_flag = 0;
+  }
+  for (int idx = threadIdx.x; idx < NRHS * 128 * C; idx += blockDim.x) {
+    const int k = idx / (128 * C), c = idx - k * 128 * C;
+    s_lt[k][c] = (kNeedT && c < ldr) ? a.rhs[k].t_in[c] : -INFINITY;
+  }
+  __syncthreads();
+
+  int flag = 0;
+  float lm[NRHS][C][4], ls[NRHS][C][4];  // running column (max, sum)
+  double res[NRHS];
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) {
+    res[k] = 0.0;
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        lm[k][j][e] = -INFINITY;
+        ls[k][j][e] = 0.f;
+      }
+  }
+  if (warp == kConsumerWarps) {
+    ring_produce<NRHS>(ring, a.F, a.n, a.ntiles, a.rhs, MODE != kPassAxpy, lane, flag);
+  } else {
+    bool has_old[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    const int myq = (lane >> SH) & (RW - 1);
+    const bool owner = (lane & ((1 << SH) - 1)) == 0;
+
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+      const int s = it % S;
+      if (!ring_wait_full(ring, it, lane)) {
+        flag |= LSF_ERR_TIMEOUT;
+        break;
+      }
+      const int64_t row0 = tile * TR;
+      const int rows = static_cast<int>(min(static_cast<int64_t>(TR), a.n - row0));
+      const float* tF = ring.sF + static_cast<size_t>(s) * TR * ldr;
+      for (int rr = warp * RW; rr < rows; rr += RW * kConsumerWarps) {
+        float4 f[RW][C];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int col = 4 * lane + 128 * j;
+            f[q][j] = (rr + q < rows && col < ldr)
+                          ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(rr + q) * ldr + col)
+                          : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+          }
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          const float* vw = ring.sV + static_cast<size_t>((s * NRHS + k) * 2) * TR;
+          const float* vold = vw + TR;
+          float fq[RW];  // the RW rows' log scalings
+          if (MODE == kPassAxpy) {
+#pragma unroll
+            for (int q = 0; q < RW; ++q) fq[q] = (rr + q < rows) ? vold[rr + q] : -INFINITY;
+          } else {
+            float p[RW];
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+              float m = -INFINITY;
+#pragma unroll
+              for (int j = 0; j < C; ++j) {
+                const float4 lt = *reinterpret_cast<const float4*>(&s_lt[k][4 * lane + 128 * j]);
+                m = fmaxf(m, fmaxf(fmaxf(f[q][j].x + lt.x, f[q][j].y + lt.y),
+                                   fmaxf(f[q][j].z + lt.z, f[q][j].w + lt.w)));
+              }
+              p[q] = m;
+            }
+            const float mrow = fold_rows<RW>(p, lane, OpMax());
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+              const float mq = __shfl_sync(0xffffffffu, mrow, q << SH);
+              float sum = 0.f;
+#pragma unroll
+              for (int j = 0; j < C; ++j) {
+                const float4 lt = *reinterpret_cast<const float4*>(&s_lt[k][4 * lane + 128 * j]);
+                sum += ex2_approx((f[q][j].x + lt.x - mq) * kLog2e) +
+                       ex2_approx((f[q][j].y + lt.y - mq) * kLog2e) +
+                       ex2_approx((f[q][j].z + lt.z - mq) * kLog2e) +
+                       ex2_approx((f[q][j].w + lt.w - mq) * kLog2e);
+              }
+              p[q] = sum;
+            }
+            const float srow = fold_rows<RW>(p, lane, OpAdd());
+            const int row = rr + myq;
+            float fi = -INFINITY;
+            if (row < rows) {
+              const float logs = mrow + logf(srow);
+              const float wi = vw[row];
+              if (has_old[k] && owner)
+                res[k] += fabs(exp(static_cast<double>(vold[row]) + static_cast<double>(logs)) -
+                               static_cast<double>(wi));
+              if (MODE == kPassUpdate) {
+                fi = logf(wi) - logs;
+                if (owner) {
+                  a.rhs[k].out[row0 + row] = fi;
+                  if (!isfinite(fi)) flag |= LSF_ERR_NONFINITE;
+                }
+                if (!isfinite(fi)) fi = -INFINITY;
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < RW; ++q) fq[q] = __shfl_sync(0xffffffffu, fi, q << SH);
+          }
+          if (kAcc) {
+            // column side: fold the RW rows into one (max, sum) per column
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                float y[RW];
+                float cm = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                  const float fv = e == 0 ? f[q][j].x : e == 1 ? f[q][j].y : e == 2 ? f[q][j].z : f[q][j].w;
+                  y[q] = fv + fq[q];
+                  cm = fmaxf(cm, y[q]);
+                }
+                if (cm != -INFINITY) {
+                  float cs = 0.f;
+#pragma unroll
+                  for (int q = 0; q < RW; ++q) cs += ex2_approx((y[q] - cm) * kLog2e);
+                  lse_merge(lm[k][j][e], ls[k][j][e], cm, cs);
+                }
+              }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ring.empty[s]);
+    }
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) {
+      double r = res[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      res[k] = r;
+    }
+  }
+  __syncthreads();
+  float* red = ring.sF;  // [kConsumerWarps][NRHS][2][ldr]
+  if (warp < kConsumerWarps) {
+    if (kAcc) {
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const int col = 4 * lane + 128 * j;
+          if (col < ldr) {
+            float* rg = red + (static_cast<size_t>(warp) * NRHS + k) * 2 * ldr;
+            *reinterpret_cast<float4*>(rg + col) =
+                make_float4(lm[k][j][0], lm[k][j][1], lm[k][j][2], lm[k][j][3]);
+            *reinterpret_cast<float4*>(rg + ldr + col) =
+                make_float4(ls[k][j][0], ls[k][j][1], ls[k][j][2], ls[k][j][3]);
+          }
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) s_res[warp][k] = res[k];
+  }
+  if (flag) atomicOr(&s_flag, flag);
+  __syncthreads();
+  finish_pass_log<NRHS, kAcc>(red, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.rpart,
+                              a.counter, a.status, s_flag, &s_last);
+}
+
+template <int C, int NRHS>
+int launch_log_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {
+  void (*kern)(PassArgs) = nullptr;
+  if (mode == kPassUpdate) kern = logpass_kernel<C, NRHS, kPassUpdate>;
+  else if (mode == kPassAxpy) kern = logpass_kernel<C, NRHS, kPassAxpy>;
+  else kern = logpass_kernel<C, NRHS, kPassDot>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "logpass: smem attribute: %s", cudaGetErrorString(e));
+  kern<<<grid, kPassThreads, smem, st>>>(a);
+  return check_launch("logpass_kernel");
+}
+
+template <int NRHS>
+int launch_log_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {
+  switch (pass_columns(a.ldr)) {
+    case 1: return launch_log_c_nrhs<1, NRHS>(mode, a, grid, smem, st);
+    case 2: return launch_log_c_nrhs<2, NRHS>(mode, a, grid, smem, st);
+    case 4: return launch_log_c_nrhs<4, NRHS>(mode, a, grid, smem, st);
+    default: return launch_log_c_nrhs<8, NRHS>(mode, a, grid, smem, st);
+  }
+}
+
+}  // namespace
+
+int launch_logpass(int mode, int nrhs, PassArgs a, cudaStream_t st) {
+  size_t smem = 0;
+  unsigned grid = 0;
+  int rc = plan_pass(a, nrhs, 2 * a.ldr, &smem, &grid);
+  if (rc != LSF_OK) return rc;
+  bool with_old = false;
+  for (int k = 0; k < nrhs; ++k) with_old |= a.rhs[k].old != nullptr;
+  LaunchScope ls(st, LSF_KERNEL_PASS_LOG, pass_bytes(mode, nrhs, a.n, a.ldr, with_old));
+  if (nrhs == 1) return launch_log_nrhs<1>(mode, a, grid, smem, st);
+  return launch_log_nrhs<2>(mode, a, grid, smem, st);
+}
+
+}  // namespace lsf

@@ -39,6 +39,25 @@ struct PassArgs {
 // bytes_moved is the algorithmic traffic of the launch, recorded for profiling.
 int launch_pass(int mode, int nrhs, PassArgs args, cudaStream_t st);
 
+// Shape of a stored-pass consumer step for C float4 columns per lane: it works
+// on kTilesPerStep consecutive ring stages at once (8 / C rows of each).
+template <int C>
+struct PassShape {
+  static constexpr int kTilesPerStep = C == 8 ? 2 : 1;
+};
+
+// float4 columns per lane of a stored pass (1, 2, 4 or 8) for a row stride ldr;
+// a consumer warp takes 8 / that many rows at once.
+int pass_columns(int ldr);
+
+// Choose tile rows, ring depth, dynamic shared memory and grid for a pass over F.
+// red_floats_per_warp_rhs: floats per consumer warp and right-hand side of the
+// end-of-launch reduction buffer (ldr, or 2 ldr for the log-domain pass).
+int plan_pass(PassArgs& a, int nrhs, int red_floats_per_warp_rhs, size_t* smem, unsigned* grid);
+
+// Log-domain pass (same ring, log-sum-exp arithmetic); see logpass.cu.
+int launch_logpass(int mode, int nrhs, PassArgs args, cudaStream_t st);
+
 // Target tile size and maximum ring depth of the stored-feature pass (tuning).
 int set_pass_tiling(int tile_bytes, int max_stages);
 void get_pass_tiling(int* tile_bytes, int* max_stages);

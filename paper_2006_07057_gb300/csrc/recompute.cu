@@ -29,13 +29,6 @@ namespace {
 constexpr int kRcThreads = 256;
 constexpr int kRcWarps = kRcThreads / 32;
 constexpr int kRcRB = 8;  // rows per group per batch
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // Row data slots per row in shared memory: x[D], B, then per rhs (w, old).
 template <int D, int NRHS>
@@ -260,7 +253,9 @@ int launch_gdn(int mode, const RecomputeArgs& a, cudaStream_t st) {
   if (per_sm < 1) per_sm = 1;
   const int64_t rpb = NG * kRcRB;
   const int64_t nbatch = (a.n + rpb - 1) / rpb;
-  const int64_t grid = std::min<int64_t>(static_cast<int64_t>(device_info().sms) * per_sm, nbatch);
+  // one workspace partial slot per CTA: never more CTAs than the workspace holds
+  const int64_t cap = std::min<int64_t>(static_cast<int64_t>(device_info().sms) * per_sm, max_pass_ctas());
+  const int64_t grid = std::min<int64_t>(cap, nbatch);
   kern<<<static_cast<unsigned>(grid), kRcThreads, smem, st>>>(a, mode);
   return check_launch("recompute_kernel");
 }

@@ -103,10 +103,12 @@ int check_launch(const char* what) {
 
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+int max_pass_ctas() { return device_info().sms * kMaxPassCtasPerSm; }
+
 size_t workspace_bytes(int ldr) {
-  const int grid = device_info().sms;
+  const int grid = max_pass_ctas();
   size_t b = 0;
-  b += align256(sizeof(float) * static_cast<size_t>(grid) * 2 * ldr);
+  b += align256(sizeof(float) * static_cast<size_t>(grid) * 4 * ldr);
   b += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
   b += align256(sizeof(double) * static_cast<size_t>(kDivGrid) * 3);
   b += align256(sizeof(unsigned) * 8);
@@ -121,10 +123,10 @@ int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws) {
     return fail(LSF_ERR_ARG, "workspace must be 256-byte aligned");
   if (bytes < need)
     return fail(LSF_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", bytes, need);
-  const int grid = device_info().sms;
+  const int grid = max_pass_ctas();
   char* p = static_cast<char*>(base);
   ws->part = reinterpret_cast<float*>(p);
-  p += align256(sizeof(float) * static_cast<size_t>(grid) * 2 * ldr);
+  p += align256(sizeof(float) * static_cast<size_t>(grid) * 4 * ldr);
   ws->rpart = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
   ws->dpart = reinterpret_cast<double*>(p);

@@ -21,13 +21,14 @@ __global__ void max_key_kernel(const float* __restrict__ x, int64_t n, unsigned*
 
 // v = 1 in shifted form: v~_j = exp(shift_j - M) with M = max shift (the global
 // factor exp(-M) cancels in P and W and is recorded in log_scale).
+// In the log domain v~ = e^shift needs no factor: log v~ = shift, and M = 0.
 __global__ void init_scaling_kernel(const float* __restrict__ shift, int64_t n,
                                     const unsigned* __restrict__ key, float* __restrict__ v,
-                                    double* log_scale_a, double* log_scale_b) {
-  const float M = key_float(*key);
+                                    double* log_scale_a, double* log_scale_b, int log_domain) {
+  const float M = log_domain ? 0.f : key_float(*key);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    v[i] = expf(shift[i] - M);
+    v[i] = log_domain ? shift[i] : expf(shift[i] - M);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (log_scale_a) *log_scale_a = static_cast<double>(M);
     if (log_scale_b) *log_scale_b = static_cast<double>(M);
@@ -51,6 +52,7 @@ struct DivSeg {
   int64_t n;
   int term;            // which result record
   double sign;         // +1: log u = log u~ - shift - M ; -1: log v = log v~ - shift + M
+  int is_log;          // the scaling array already holds log u~ (log-domain mode)
 };
 
 struct DivArgs {
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(256) divergence_kernel(const DivArgs a) {
     const int64_t hi = min(sg.n, lo + chunk);
     KahanSum part;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double lg = static_cast<double>(logf(sg.s[i])) - static_cast<double>(sg.shift[i]) - sg.sign * M;
+      const double ls = sg.is_log ? static_cast<double>(sg.s[i]) : static_cast<double>(logf(sg.s[i]));
+      const double lg = ls - static_cast<double>(sg.shift[i]) - sg.sign * M;
       part.add(static_cast<double>(sg.w[i]) * lg);
     }
     // Fold this segment's thread sum into its term in a fixed order.
@@ -144,6 +147,10 @@ int check_cloud(const lsf_cloud* c, int mode, const char* name) {
       return fail(LSF_ERR_ARG, "%s: F must be 16-byte aligned", name);
   } else if (mode == LSF_MODE_RECOMPUTE) {
     if (!c->X) return fail(LSF_ERR_ARG, "%s: recompute mode needs X", name);
+  } else if (mode == LSF_MODE_LOG) {
+    if (!c->F) return fail(LSF_ERR_ARG, "%s: log mode needs the log features in F", name);
+    if (reinterpret_cast<uintptr_t>(c->F) % 16 != 0)
+      return fail(LSF_ERR_ARG, "%s: F must be 16-byte aligned", name);
   } else {
     return fail(LSF_ERR_ARG, "unknown mode %d", mode);
   }
@@ -165,13 +172,9 @@ int check_scalings(const lsf_scalings* s, const char* name) {
   } while (0)
 
 // One fused pass on one cloud in the chosen mode.
-struct Side {
-  const lsf_cloud* cl;
-};
-
 int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int nrhs,
              const PassRhs* rhs, const Workspace& ws, int* status, cudaStream_t st) {
-  if (mode == LSF_MODE_STORED) {
+  if (mode == LSF_MODE_STORED || mode == LSF_MODE_LOG) {
     PassArgs a{};
     a.F = cl->F;
     a.n = cl->n;
@@ -181,7 +184,7 @@ int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int 
     a.rpart = ws.rpart;
     a.counter = ws.counters;
     a.status = status;
-    return launch_pass(pmode, nrhs, a, st);
+    return mode == LSF_MODE_LOG ? launch_logpass(pmode, nrhs, a, st) : launch_pass(pmode, nrhs, a, st);
   }
   RecomputeArgs a{};
   a.X = cl->X;
@@ -212,19 +215,20 @@ int start_solve(void* workspace, size_t ws_bytes, int ldr, lsf_result* result, i
   return LSF_OK;
 }
 
-int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double* ls_b,
+int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double* ls_b, int mode,
               cudaStream_t st) {
   const int grid = device_info().sms * 2;
   LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * cl->n);
   max_key_kernel<<<grid, 256, 0, st>>>(cl->shift, cl->n, key);
-  init_scaling_kernel<<<grid, 256, 0, st>>>(cl->shift, cl->n, key, v, ls_a, ls_b);
+  init_scaling_kernel<<<grid, 256, 0, st>>>(cl->shift, cl->n, key, v, ls_a, ls_b,
+                                            mode == LSF_MODE_LOG ? 1 : 0);
   return check_launch("init_scaling_kernel");
 }
 
 int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* xs,
                       const lsf_cloud* const* ys, const lsf_scalings* const* s,
                       lsf_result* const* res, const double* coef, double* combined,
-                      const Workspace& ws, cudaStream_t st) {
+                      const Workspace& ws, cudaStream_t st, int is_log) {
   DivArgs a{};
   a.nterms = nterms;
   a.eps = th->eps;
@@ -235,8 +239,8 @@ int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* x
   for (int t = 0; t < nterms; ++t) {
     a.coef[t] = coef ? coef[t] : 1.0;
     a.res[t] = res[t];
-    a.seg[a.nseg++] = DivSeg{s[t]->u, xs[t]->shift, xs[t]->w, xs[t]->n, t, +1.0};
-    a.seg[a.nseg++] = DivSeg{s[t]->v, ys[t]->shift, ys[t]->w, ys[t]->n, t, -1.0};
+    a.seg[a.nseg++] = DivSeg{s[t]->u, xs[t]->shift, xs[t]->w, xs[t]->n, t, +1.0, is_log};
+    a.seg[a.nseg++] = DivSeg{s[t]->v, ys[t]->shift, ys[t]->w, ys[t]->n, t, -1.0, is_log};
     bytes += 12.0 * (xs[t]->n + ys[t]->n);
   }
   for (int t = nterms; t < 3; ++t) a.res[t] = res[0];
@@ -265,7 +269,7 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
   LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 1, &ws, st));
   int* status = &result->status;
 
-  LSF_TRY(init_side(y, ws.keys + 0, out->v, &result->log_scale, nullptr, st));
+  LSF_TRY(init_side(y, ws.keys + 0, out->v, &result->log_scale, nullptr, mode, st));
   {
     PassRhs r{};
     r.old = out->v;
@@ -294,7 +298,7 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
 
 int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* xs,
                    const lsf_cloud* const* ys, const lsf_scalings* const* s,
-                   lsf_result* const* result, const double* coef, double* combined,
+                   lsf_result* const* result, const double* coef, double* combined, int mode,
                    void* workspace, size_t ws_bytes, void* stream) {
   LSF_TRY(check_theta(theta));
   if (nterms < 1 || nterms > 3) return fail(LSF_ERR_ARG, "nterms must be 1..3");
@@ -310,7 +314,8 @@ int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* x
   LSF_TRY(carve_workspace(workspace, ws_bytes, theta->ldr, &ws));
   if (cudaMemsetAsync(ws.counters + 1, 0, sizeof(unsigned), st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "lsf_divergence: memset failed");
-  return launch_divergence(theta, nterms, xs, ys, s, result, coef, combined, ws, st);
+  return launch_divergence(theta, nterms, xs, ys, s, result, coef, combined, ws, st,
+                           mode == LSF_MODE_LOG ? 1 : 0);
 }
 
 int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
@@ -333,11 +338,11 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
   int* status = &rxy->status;
 
   // v = 1 for all three solves: v~ = exp(shift - max shift) on the side each v lives on.
-  LSF_TRY(init_side(y, ws.keys + 0, s_xy->v, &rxy->log_scale, &ryy->log_scale, st));
+  LSF_TRY(init_side(y, ws.keys + 0, s_xy->v, &rxy->log_scale, &ryy->log_scale, mode, st));
   if (cudaMemcpyAsync(s_yy->v, s_xy->v, sizeof(float) * y->n, cudaMemcpyDeviceToDevice, st) !=
       cudaSuccess)
     return fail(LSF_ERR_CUDA, "debiased: copy of the start vector failed");
-  LSF_TRY(init_side(x, ws.keys + 1, s_xx->v, &rxx->log_scale, nullptr, st));
+  LSF_TRY(init_side(x, ws.keys + 1, s_xx->v, &rxx->log_scale, nullptr, mode, st));
   {
     PassRhs r[2] = {};
     r[0].old = s_xy->v; r[0].t_out = s_xy->t_v;
@@ -382,7 +387,8 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
     const lsf_scalings* ss[3] = {s_xy, s_xx, s_yy};
     lsf_result* rs[3] = {rxy, rxx, ryy};
     const double coef[3] = {1.0, -0.5, -0.5};
-    LSF_TRY(launch_divergence(theta, 3, xs, ys, ss, rs, coef, wbar, ws, st));
+    LSF_TRY(launch_divergence(theta, 3, xs, ys, ss, rs, coef, wbar, ws, st,
+                              mode == LSF_MODE_LOG ? 1 : 0));
   }
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
