@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched"])
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving"])
+    ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--count", type=int, default=512)
     return ap.parse_args()
 
@@ -217,7 +218,7 @@ def run_batched(args):
     groups = {}
     for p in probs:
         groups.setdefault(lsf.ldr_for(p.r), []).append(Dev(p))
-    solvers = [lsf.BatchedSolver(g, ldr=ldr) for ldr, g in sorted(groups.items())]
+    solvers = [lsf.BatchedSolver(g, ldr=ldr, mode="auto") for ldr, g in sorted(groups.items())]
     for sv in solvers:
         sv.capture(iters)
     torch.cuda.synchronize()
@@ -240,8 +241,10 @@ def run_batched(args):
     vals = [v for sv in solvers for v in sv.values()]
     nonfinite = sum(1 for v in vals if v["status"] & lsf.LSF_ERR_NONFINITE)
 
-    # plain: the same problems, one lsf_solve + Eq. (6) after another, same stream
-    singles = [lsf.SinkhornProblem(pp.X, pp.Y, pp.a, pp.b, pp.Z, pp.eps, ldr=sv.ldr)
+    routed = sum(len(idx) for sv in solvers for b, idx in sv.batches if b.mode == "log")
+    # plain: the same problems, one lsf_solve + Eq. (6) after another, same stream, in the
+    # mode the batched solver routed them to
+    singles = [lsf.SinkhornProblem(pp.X, pp.Y, pp.a, pp.b, pp.Z, pp.eps, ldr=sv.ldr, mode=pp.mode)
                for sv in solvers for pp in sv.problems]
     for sp in singles[: min(8, len(singles))]:
         sp.run(iters, debiased=False)
@@ -266,15 +269,62 @@ def run_batched(args):
                                f"r in {{128,256}}, eps log-uniform [0.05,1], mixture clouds, Dirichlet(1) "
                                f"weights, {iters} iterations, one graph-captured persistent launch per "
                                f"feature width, stored features resident",
-                   "groups": {str(sv.ldr): {"problems": len(sv.problems), "tile_bytes": sv.tile_bytes,
-                                            "tile_rows": sv.info.tile_rows, "stages": sv.info.stages}
+                   "groups": {str(sv.ldr): [{"mode": b.mode, "problems": len(idx),
+                                             "tile_bytes": b.tile_bytes, "tile_rows": b.info.tile_rows,
+                                             "stages": b.info.stages} for b, idx in sv.batches]
                               for sv in solvers}},
         "batched": {"solves_per_s": n / (ms_batched / 1e3), "ms_per_batch": ms_batched,
                     "latency_ms_p50": ms_batched, "latency_ms_p99": ms_batched,
-                    "nonfinite_problems": nonfinite},
+                    "nonfinite_problems": nonfinite, "log_domain_problems": routed},
         "plain_sequential": {"solves_per_s": n / (ms_plain / 1e3), "ms_total": ms_plain,
                              "latency_ms_p50": pct(lat_plain, 0.5), "latency_ms_p99": pct(lat_plain, 0.99)},
         "speedup_vs_plain": ms_plain / ms_batched,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Serving workload: a Poisson stream of debiased-divergence requests of uneven
+    shape served by the continuous-batching server (40 GB admission budget), against
+    the same stream served one request at a time."""
+    import torch
+    import paper_2006_07057_gb300 as lsf
+    from paper_2006_07057_gb300 import serve
+    torch.cuda.set_device(0)
+    lsf.lib()
+    iters = 100
+    count = args.count
+
+    def make():
+        out = []
+        for i, rq in enumerate(synth.serving_stream(seed=0, count=count, rate_per_s=args.rate,
+                                                    iters=iters)):
+            p = rq.problem
+            out.append(serve.Request(i, p.X, p.Y, p.a, p.b, p.Z, p.eps, iters, rq.arrival_s))
+        return out
+
+    warm = make()[: min(8, count)]
+    serve.Server(budget_bytes=40e9).serve(warm, realtime=False)
+    torch.cuda.synchronize()
+    srv = serve.Server(budget_bytes=40e9, slots=16)
+    mixed = srv.serve(make(), realtime=True)
+    st_mixed = serve.latency_stats(mixed)
+    seq = serve.serve_sequential(make(), realtime=True)
+    st_seq = serve.latency_stats(seq)
+    nonfinite = sum(1 for r in mixed if r.status & lsf.LSF_ERR_NONFINITE)
+    line = {
+        "metric": METRIC, "value": st_mixed["throughput_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * st_mixed["span_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {count} debiased-divergence requests at "
+                               f"{args.rate:g}/s, n,m log-uniform [2^8, 2^18], d in {{2,3,16}}, "
+                               f"r in {{128,512}}, eps in {{0.05,0.2,1.0}}, mixture clouds, uniform "
+                               f"weights, {iters} iterations, 40 GB admission budget, 16 slots"},
+        "served": {**st_mixed, "peak_inflight": srv.peak_inflight, "peak_bytes": srv.peak_bytes,
+                   "nonfinite_requests": nonfinite},
+        "plain_sequential": st_seq,
+        "p99_ratio_plain_over_served": st_seq["latency_ms_p99"] / st_mixed["latency_ms_p99"],
     }
     print(json.dumps(line))
     return 0
@@ -286,6 +336,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
     world, rank, local = dist_env()
     if world > 1:

@@ -260,6 +260,7 @@ typedef struct {
 typedef struct {
   int count;          /* problems                                  */
   int ldr;            /* common row stride                         */
+  int mode;           /* LSF_MODE_STORED or LSF_MODE_LOG            */
   int tile_rows;      /* rows per shared-memory tile               */
   int stages;         /* copy-ring depth                           */
   int grid;           /* CTAs of the persistent kernel (co-resident) */
@@ -272,7 +273,10 @@ typedef struct {
 } lsf_batch_info;
 
 /*
- * Plan a batch: choose the tiling (tile_bytes = 0 picks the default; the
+ * Plan a batch: mode LSF_MODE_STORED (Fx, Fy shifted features; u, v, t hold
+ * scalings) or LSF_MODE_LOG (Fx, Fy log features from lsf_log_features; u, v, t
+ * hold logs; for problems outside the FP32 range of the scaling domain). Choose
+ * the tiling (tile_bytes = 0 picks the default; the
  * autotuner passes candidates), partition the concatenated tiles of all problems
  * over the CTAs, and lay out the device plan (problem table, tile tables,
  * partial buffers, arrival counters, round flags). With plan == NULL only
@@ -280,7 +284,7 @@ typedef struct {
  * device, 256-byte aligned) is written with a copy that completes before
  * return. probs: host array of `count` records.
  */
-int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int tile_bytes,
+int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int mode, int tile_bytes,
                    lsf_batch_info* info, void* plan, size_t plan_bytes, void* stream);
 
 /*

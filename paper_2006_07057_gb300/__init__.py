@@ -484,24 +484,66 @@ class SinkhornDivergenceFn(torch.autograd.Function):
 
 # ---------------------------------------------------------------- batched solver
 
-def lsf_batch_plan(records, ldr: int, tile_bytes: int = 0, stream=None):
+def lsf_batch_plan(records, ldr: int, tile_bytes: int = 0, stream=None, mode: str = "stored"):
     """Plan a batch; returns (info, plan tensor). records: list of LsfBatchProblem."""
     arr = (LsfBatchProblem * len(records))(*records)
     info = LsfBatchInfo()
-    check(lib().lsf_batch_plan(arr, len(records), int(ldr), int(tile_bytes), ctypes.byref(info),
-                               None, 0, _stream(stream)), "lsf_batch_plan")
+    check(lib().lsf_batch_plan(arr, len(records), int(ldr), MODES[mode], int(tile_bytes),
+                               ctypes.byref(info), None, 0, _stream(stream)), "lsf_batch_plan")
     dev = torch.device("cuda", torch.cuda.current_device())
     buf = torch.empty(info.plan_bytes + 256, dtype=torch.uint8, device=dev)
     off = (-buf.data_ptr()) % 256
     plan = buf[off:off + info.plan_bytes]
-    check(lib().lsf_batch_plan(arr, len(records), int(ldr), int(tile_bytes), ctypes.byref(info),
-                               _p(plan), plan.numel(), _stream(stream)), "lsf_batch_plan")
+    check(lib().lsf_batch_plan(arr, len(records), int(ldr), MODES[mode], int(tile_bytes),
+                               ctypes.byref(info), _p(plan), plan.numel(), _stream(stream)),
+          "lsf_batch_plan")
     return info, plan
 
 
 def lsf_solve_batched(info, plan, iters: int, stream=None) -> None:
     check(lib().lsf_solve_batched(ctypes.byref(info), _p(plan), int(iters), _stream(stream)),
           "lsf_solve_batched")
+
+
+class _Batch:
+    """One planned batch: problems (SinkhornProblem without scalings) in one mode."""
+
+    def __init__(self, probs, ldr, mode, tile_bytes, stream):
+        self.probs, self.ldr, self.mode, self.stream = probs, ldr, mode, stream
+        dev = probs[0].X.device
+        self.results = alloc_results(len(probs), dev)
+        self.records = []
+        for k, prob in enumerate(probs):
+            s = Scalings.alloc(prob.x.n, prob.y.n, ldr, dev)
+            prob.s_xy = s
+            self.records.append(LsfBatchProblem(
+                _p(prob.x.F).value, _p(prob.y.F).value, _p(prob.x.shift).value,
+                _p(prob.y.shift).value, _p(prob.x.w).value, _p(prob.y.w).value, prob.x.n,
+                prob.y.n, float(prob.eps), _p(s.u).value, _p(s.v).value, _p(s.t_u).value,
+                _p(s.t_v).value, self.results.data_ptr() + k * RESULT_BYTES))
+        if tile_bytes is None:
+            from .autotune import best_batch_tile
+            tile_bytes = best_batch_tile(self)
+        self.tile_bytes = tile_bytes
+        self.info, self.plan = lsf_batch_plan(self.records, ldr, tile_bytes, stream, mode=mode)
+        self.graph = None
+
+    @property
+    def problems(self):
+        return self.probs
+
+    def run(self, iters):
+        lsf_solve_batched(self.info, self.plan, iters, self.stream)
+
+    def capture(self, iters):
+        self.run(iters)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                lsf_solve_batched(self.info, self.plan, iters, s)
+        self.graph = g
 
 
 class BatchedSolver:
@@ -511,52 +553,75 @@ class BatchedSolver:
     solves all problems with the persistent batched kernel. ``problems``: list of
     objects with X, Y, a, b, Z (CUDA float32 tensors) and eps. ``tile_bytes=None``
     asks the autotuner.
+
+    ``mode="auto"`` routes: ``route(iters)`` solves once in the scaling domain and
+    moves the problems that reported a non-finite scaling into a second batch solved
+    in the log domain; later runs solve both batches. ``mode="log"`` solves every
+    problem in the log domain.
     """
 
     def __init__(self, problems, ldr: int | None = None, tile_bytes: int | None = None,
-                 stream=None):
+                 stream=None, mode: str = "stored"):
         self.stream = stream
+        self.mode = mode
         rs = {int(p.Z.shape[0]) for p in problems}
         self.ldr = ldr if ldr is not None else ldr_for(max(rs))
-        self.problems = []
-        recs = []
-        dev = problems[0].X.device
-        self.results = alloc_results(len(problems), dev)
-        for k, p in enumerate(problems):
-            prob = SinkhornProblem(p.X, p.Y, p.a, p.b, p.Z, p.eps, mode="stored", ldr=self.ldr,
-                                   stream=stream, scalings=False)
-            s = Scalings.alloc(prob.x.n, prob.y.n, self.ldr, dev)
-            prob.s_xy = s
-            self.problems.append(prob)
-            recs.append(LsfBatchProblem(
-                _p(prob.x.F).value, _p(prob.y.F).value, _p(prob.x.shift).value,
-                _p(prob.y.shift).value, _p(prob.x.w).value, _p(prob.y.w).value, prob.x.n,
-                prob.y.n, float(p.eps), _p(s.u).value, _p(s.v).value, _p(s.t_u).value,
-                _p(s.t_v).value, self.results.data_ptr() + k * RESULT_BYTES))
-        self.records = recs
-        if tile_bytes is None:
-            from .autotune import best_batch_tile
-            tile_bytes = best_batch_tile(self)
         self.tile_bytes = tile_bytes
-        self.info, self.plan = lsf_batch_plan(recs, self.ldr, tile_bytes, stream)
-        self.graph = None
+        first = "log" if mode == "log" else "stored"
+        self.problems = [SinkhornProblem(p.X, p.Y, p.a, p.b, p.Z, p.eps, mode=first, ldr=self.ldr,
+                                         stream=stream, scalings=False) for p in problems]
+        for prob, p in zip(self.problems, problems):
+            prob.eps = float(p.eps)
+        self.batches = [(_Batch(self.problems, self.ldr, first, tile_bytes, stream),
+                         list(range(len(self.problems))))]
+        self.iters = None
+
+    @property
+    def info(self):
+        return self.batches[0][0].info
+
+    def route(self, iters: int) -> int:
+        """Solve once; move range failures to a log-domain batch. Returns their number."""
+        b0, idx0 = self.batches[0]
+        b0.run(iters)
+        bad = [k for k, v in zip(idx0, read_results(b0.results))
+               if v["status"] & LSF_ERR_NONFINITE]
+        if not bad:
+            return 0
+        good = [k for k in idx0 if k not in set(bad)]
+        for k in bad:
+            self.problems[k].switch_mode("log")
+        batches = []
+        if good:
+            batches.append((_Batch([self.problems[k] for k in good], self.ldr, "stored",
+                                   self.tile_bytes, self.stream), good))
+        batches.append((_Batch([self.problems[k] for k in bad], self.ldr, "log", self.tile_bytes,
+                               self.stream), bad))
+        self.batches = batches
+        return len(bad)
 
     def run(self, iters: int) -> None:
-        lsf_solve_batched(self.info, self.plan, iters, self.stream)
+        self.iters = iters
+        if self.mode == "auto" and len(self.batches) == 1 and self.batches[0][0].mode == "stored":
+            self.route(iters)
+        for b, _ in self.batches:
+            b.run(iters)
 
     def capture(self, iters: int) -> None:
-        """Capture one batched solve (start, persistent kernel, reduction) in a CUDA graph."""
-        self.run(iters)  # warm-up outside the capture (module loading, attributes)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                lsf_solve_batched(self.info, self.plan, iters, s)
-        self.graph = g
+        """Capture each batch's solve (start, persistent kernel, reduction) in a CUDA graph."""
+        self.run(iters)
+        for b, _ in self.batches:
+            b.capture(iters)
+        self.iters = iters
 
     def replay(self) -> None:
-        self.graph.replay()
+        for b, _ in self.batches:
+            b.graph.replay()
 
     def values(self) -> list[dict]:
-        return read_results(self.results)
+        out = [None] * len(self.problems)
+        for b, idx in self.batches:
+            for k, v in zip(idx, read_results(b.results)):
+                v["mode"] = b.mode
+                out[k] = v
+        return out

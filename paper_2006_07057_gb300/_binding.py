@@ -69,7 +69,7 @@ class LsfBatchProblem(ctypes.Structure):
 
 
 class LsfBatchInfo(ctypes.Structure):
-    _fields_ = [("count", c_int), ("ldr", c_int), ("tile_rows", c_int), ("stages", c_int),
+    _fields_ = [("count", c_int), ("ldr", c_int), ("mode", c_int), ("tile_rows", c_int), ("stages", c_int),
                 ("grid", c_int), ("tiles_x", c_int64), ("tiles_y", c_int64), ("rows_x", c_int64),
                 ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t)]
 
@@ -100,7 +100,7 @@ _SIGNATURES = {
     "lsf_gradient": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), _P(LsfScalings),
                              _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_int,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    "lsf_batch_plan": (c_int, [_P(LsfBatchProblem), c_int, c_int, c_int, _P(LsfBatchInfo),
+    "lsf_batch_plan": (c_int, [_P(LsfBatchProblem), c_int, c_int, c_int, c_int, _P(LsfBatchInfo),
                                c_void_p, c_size_t, c_void_p]),
     "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),
     "lsf_set_pass_tiling": (c_int, [c_int, c_int]),

@@ -23,9 +23,13 @@ PROBE_ITERS = 6
 
 def _key(solver) -> str:
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    rows = sum(p.x.n + p.y.n for p in solver.problems)
+    rows = sum(p.x.n + p.y.n for p in solver.probs)
     bucket = int(math.log2(max(rows, 1)))
     return f"{props.name}|{props.multi_processor_count}|ldr={solver.ldr}|rows=2^{bucket}"
+
+
+# The tuner works on one planned batch (an object with probs, records, ldr, mode
+# and stream attributes).
 
 
 def _load() -> dict:
@@ -48,14 +52,15 @@ def best_batch_tile(solver, candidates=CANDIDATES, use_cache: bool = True) -> in
     """Tile bytes with the shortest measured batched solve for this batch."""
     from . import lsf_batch_plan, lsf_solve_batched
 
-    key = _key(solver)
+    key = _key(solver) + f"|{getattr(solver, 'mode', 'stored')}"
     cache = _load() if use_cache else {}
     if key in cache:
         return int(cache[key]["tile_bytes"])
     stream = solver.stream or torch.cuda.current_stream()
     timings = {}
     for tb in candidates:
-        info, plan = lsf_batch_plan(solver.records, solver.ldr, tb, stream)
+        info, plan = lsf_batch_plan(solver.records, solver.ldr, tb, stream,
+                                    mode=getattr(solver, "mode", "stored"))
         lsf_solve_batched(info, plan, PROBE_ITERS, stream)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)

@@ -85,7 +85,7 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int C>
+template <int C, bool LOGD>
 __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArgs A) {
   constexpr int RW = 8 / C;
   constexpr int SH = RowFold<RW>::kShift;
@@ -159,19 +159,27 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
       int64_t lo, hi;
       tile_range(A.ntiles[side], &lo, &hi);
       int cur = -1;
-      float t[C][4], acc[C][4];
+      // scaling domain: t = r-vector, acc = transposed product;
+      // log domain: t = log r-vector, acc = running column max, lsum = column sums
+      float t[C][4], acc[C][4], lsum[LOGD ? C : 1][4];
       double res = 0.0;
       auto flush = [&](int p) {
         // this warp's partial r-vector (and residual) for problem p, this round
         const BProb& pb = A.probs[p];
         const int slot = static_cast<int>(blockIdx.x) - pb.first_cta[side];
-        float* dst = pb.part[side] + (static_cast<size_t>(slot) * kConsumerWarps + warp) * ldr;
+        constexpr int kVec = LOGD ? 2 : 1;  // floats per column in a partial
+        float* dst = pb.part[side] + (static_cast<size_t>(slot) * kConsumerWarps + warp) * kVec * ldr;
         if (mode != kPassDot) {
 #pragma unroll
           for (int j = 0; j < C; ++j) {
             const int col = 4 * lane + 128 * j;
-            if (col < ldr)
+            if (col < ldr) {
               *reinterpret_cast<float4*>(dst + col) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+              if (LOGD)
+                *reinterpret_cast<float4*>(dst + ldr + col) =
+                    make_float4(lsum[LOGD ? j : 0][0], lsum[LOGD ? j : 0][1], lsum[LOGD ? j : 0][2],
+                                lsum[LOGD ? j : 0][3]);
+            }
           }
         } else {
           double rr = res;
@@ -196,14 +204,31 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           for (int j = 0; j < C; ++j) {
             const int col = 4 * lane + 128 * j;
             if (col >= ldr) continue;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int q = 0; q < nparts; ++q) {
-              const float4 v = __ldcg(reinterpret_cast<const float4*>(pb.part[side] + static_cast<size_t>(q) * ldr + col));
-              s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+            if (LOGD) {
+              float m[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY}, sm[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int q = 0; q < nparts; ++q) {
+                const float* base = pb.part[side] + static_cast<size_t>(q) * 2 * ldr;
+                const float4 vm = __ldcg(reinterpret_cast<const float4*>(base + col));
+                const float4 vs = __ldcg(reinterpret_cast<const float4*>(base + ldr + col));
+                lse_merge(m[0], sm[0], vm.x, vs.x);
+                lse_merge(m[1], sm[1], vm.y, vs.y);
+                lse_merge(m[2], sm[2], vm.z, vs.z);
+                lse_merge(m[3], sm[3], vm.w, vs.w);
+              }
+              float o[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) o[e] = sm[e] > 0.f ? m[e] + logf(sm[e]) : -INFINITY;
+              *reinterpret_cast<float4*>(tout + col) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+              double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+              for (int q = 0; q < nparts; ++q) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(pb.part[side] + static_cast<size_t>(q) * ldr + col));
+                s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+              }
+              *reinterpret_cast<float4*>(tout + col) =
+                  make_float4(static_cast<float>(s0), static_cast<float>(s1), static_cast<float>(s2),
+                              static_cast<float>(s3));
             }
-            *reinterpret_cast<float4*>(tout + col) =
-                make_float4(static_cast<float>(s0), static_cast<float>(s1), static_cast<float>(s2),
-                            static_cast<float>(s3));
           }
         } else if (lane == 0) {
           double tot = 0.0;
@@ -254,11 +279,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
 #pragma unroll
           for (int j = 0; j < C; ++j) {
             const int col = 4 * lane + 128 * j;
-            float4 tv = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float z = LOGD ? -INFINITY : 0.f;
+            float4 tv = make_float4(z, z, z, z);
             if (mode != kPassAxpy && col < ldr) tv = __ldcg(reinterpret_cast<const float4*>(tin + col));
             t[j][0] = tv.x; t[j][1] = tv.y; t[j][2] = tv.z; t[j][3] = tv.w;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+            for (int e = 0; e < 4; ++e) {
+              acc[j][e] = z;
+              if (LOGD) lsum[LOGD ? j : 0][e] = 0.f;
+            }
           }
           res = 0.0;
         }
@@ -269,6 +298,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           const float* vw = ring.sV + static_cast<size_t>(s * 2) * TR;
           float* sc_out = pb.s[side];
           for (int rr = warp * RW; rr < rows; rr += RW * kConsumerWarps) {
+            const float pad = LOGD ? -INFINITY : 0.f;
             float4 f[RW][C];
 #pragma unroll
             for (int q = 0; q < RW; ++q)
@@ -277,65 +307,120 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
                 const int col = 4 * lane + 128 * j;
                 f[q][j] = (rr + q < rows && col < ldr)
                               ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(rr + q) * ldr + col)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                              : make_float4(pad, pad, pad, pad);
               }
-            float scale[RW];
+            const int row = rr + myq;
+            float scale[RW];  // scaling domain: the rows' scalings; log domain: their logs
             if (mode == kPassAxpy) {
               // the given start vector, written before this kernel
-              float g = 0.f;
-              const int row = rr + myq;
+              float g = pad;
               if (owner && row < rows) g = sc_out[tl.row0 + row];
 #pragma unroll
               for (int q = 0; q < RW; ++q) scale[q] = __shfl_sync(0xffffffffu, g, q << SH);
             } else {
               float p[RW];
+              float rowlog = 0.f;  // log of the row product (log domain)
+              float dot = 0.f;     // row product (scaling domain)
+              if (LOGD) {
 #pragma unroll
-              for (int q = 0; q < RW; ++q) {
-                float d0 = 0.f, d1 = 0.f;
+                for (int q = 0; q < RW; ++q) {
+                  float m = -INFINITY;
 #pragma unroll
-                for (int j = 0; j < C; ++j) {
-                  d0 = fmaf(f[q][j].x, t[j][0], d0);
-                  d1 = fmaf(f[q][j].y, t[j][1], d1);
-                  d0 = fmaf(f[q][j].z, t[j][2], d0);
-                  d1 = fmaf(f[q][j].w, t[j][3], d1);
+                  for (int j = 0; j < C; ++j)
+                    m = fmaxf(m, fmaxf(fmaxf(f[q][j].x + t[j][0], f[q][j].y + t[j][1]),
+                                       fmaxf(f[q][j].z + t[j][2], f[q][j].w + t[j][3])));
+                  p[q] = m;
                 }
-                p[q] = d0 + d1;
+                const float mrow = fold_rows<RW>(p, lane, OpMax());
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                  const float mq = __shfl_sync(0xffffffffu, mrow, q << SH);
+                  float sum = 0.f;
+#pragma unroll
+                  for (int j = 0; j < C; ++j)
+                    sum += ex2_approx((f[q][j].x + t[j][0] - mq) * kLog2e) +
+                           ex2_approx((f[q][j].y + t[j][1] - mq) * kLog2e) +
+                           ex2_approx((f[q][j].z + t[j][2] - mq) * kLog2e) +
+                           ex2_approx((f[q][j].w + t[j][3] - mq) * kLog2e);
+                  p[q] = sum;
+                }
+                const float srow = fold_rows<RW>(p, lane, OpAdd());
+                rowlog = mrow + logf(srow);
+              } else {
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                  float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                  for (int j = 0; j < C; ++j) {
+                    d0 = fmaf(f[q][j].x, t[j][0], d0);
+                    d1 = fmaf(f[q][j].y, t[j][1], d1);
+                    d0 = fmaf(f[q][j].z, t[j][2], d0);
+                    d1 = fmaf(f[q][j].w, t[j][3], d1);
+                  }
+                  p[q] = d0 + d1;
+                }
+                dot = fold_rows<RW>(p, lane, OpAdd());
               }
-              const float dot = fold_rows<RW>(p, lane, OpAdd());
-              const int row = rr + myq;
-              float sc = 0.f;
+              float sc = pad;
               if (row < rows) {
                 const float wi = vw[row];
                 if (mode == kPassDot) {
                   // residual: the previous scaling was written by this same lane in
                   // the last u-half (the X-side partition is the same every round)
-                  if (owner)
-                    res += fabs(static_cast<double>(sc_out[tl.row0 + row]) * static_cast<double>(dot) -
-                                static_cast<double>(wi));
+                  if (owner) {
+                    const double prev = static_cast<double>(sc_out[tl.row0 + row]);
+                    const double us = LOGD ? exp(prev + static_cast<double>(rowlog))
+                                           : prev * static_cast<double>(dot);
+                    res += fabs(us - static_cast<double>(wi));
+                  }
                 } else {
-                  sc = wi * __frcp_rn(dot);
+                  sc = LOGD ? logf(wi) - rowlog : wi * __frcp_rn(dot);
                   if (owner) {
                     sc_out[tl.row0 + row] = sc;
-                    if (!(dot > 0.f) || !isfinite(sc)) {
+                    const bool bad = LOGD ? !isfinite(sc) : (!(dot > 0.f) || !isfinite(sc));
+                    if (bad) {
                       flag |= LSF_ERR_NONFINITE;
                       atomicOr(&pb.result->status, LSF_ERR_NONFINITE);
                     }
                   }
+                  if (LOGD && !isfinite(sc)) sc = -INFINITY;
                 }
               }
 #pragma unroll
               for (int q = 0; q < RW; ++q) scale[q] = __shfl_sync(0xffffffffu, sc, q << SH);
             }
             if (mode != kPassDot) {
+              if (LOGD) {
 #pragma unroll
-              for (int q = 0; q < RW; ++q)
+                for (int j = 0; j < C; ++j)
 #pragma unroll
-                for (int j = 0; j < C; ++j) {
-                  acc[j][0] = fmaf(scale[q], f[q][j].x, acc[j][0]);
-                  acc[j][1] = fmaf(scale[q], f[q][j].y, acc[j][1]);
-                  acc[j][2] = fmaf(scale[q], f[q][j].z, acc[j][2]);
-                  acc[j][3] = fmaf(scale[q], f[q][j].w, acc[j][3]);
-                }
+                  for (int e = 0; e < 4; ++e) {
+                    float y[RW];
+                    float cm = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                      const float fv = e == 0 ? f[q][j].x : e == 1 ? f[q][j].y : e == 2 ? f[q][j].z : f[q][j].w;
+                      y[q] = fv + scale[q];
+                      cm = fmaxf(cm, y[q]);
+                    }
+                    if (cm != -INFINITY) {
+                      float cs = 0.f;
+#pragma unroll
+                      for (int q = 0; q < RW; ++q) cs += ex2_approx((y[q] - cm) * kLog2e);
+                      lse_merge(acc[j][e], lsum[LOGD ? j : 0][e], cm, cs);
+                    }
+                  }
+              } else {
+#pragma unroll
+                for (int q = 0; q < RW; ++q)
+#pragma unroll
+                  for (int j = 0; j < C; ++j) {
+                    acc[j][0] = fmaf(scale[q], f[q][j].x, acc[j][0]);
+                    acc[j][1] = fmaf(scale[q], f[q][j].y, acc[j][1]);
+                    acc[j][2] = fmaf(scale[q], f[q][j].z, acc[j][2]);
+                    acc[j][3] = fmaf(scale[q], f[q][j].w, acc[j][3]);
+                  }
+              }
             }
           }
         }
@@ -354,7 +439,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
 
 // v = 1 per problem: v~ = exp(shift_y - M_p); also resets the round state.
 __global__ void __launch_bounds__(256) batched_start_kernel(BProb* probs, unsigned* counter,
-                                                            unsigned* flag, int iters) {
+                                                            unsigned* flag, int iters, int log_domain) {
   const BProb pb = probs[blockIdx.x];
   __shared__ float s_m[8];
   float m = -INFINITY;
@@ -364,7 +449,9 @@ __global__ void __launch_bounds__(256) batched_start_kernel(BProb* probs, unsign
   __syncthreads();
   float M = s_m[0];
   for (int w = 1; w < 8; ++w) M = fmaxf(M, s_m[w]);
-  for (int64_t j = threadIdx.x; j < pb.n[1]; j += blockDim.x) pb.s[1][j] = expf(pb.shift[1][j] - M);
+  if (log_domain) M = 0.f;  // log v~ = shift exactly, no global factor needed
+  for (int64_t j = threadIdx.x; j < pb.n[1]; j += blockDim.x)
+    pb.s[1][j] = log_domain ? pb.shift[1][j] : expf(pb.shift[1][j] - M);
   if (threadIdx.x == 0) {
     pb.result->W = 0.0;
     pb.result->residual = 0.0;
@@ -377,7 +464,7 @@ __global__ void __launch_bounds__(256) batched_start_kernel(BProb* probs, unsign
 }
 
 // Eq. (6) per problem with an FP64 compensated sum (one block per problem).
-__global__ void __launch_bounds__(256) batched_divergence_kernel(const BProb* probs) {
+__global__ void __launch_bounds__(256) batched_divergence_kernel(const BProb* probs, int log_domain) {
   const BProb pb = probs[blockIdx.x];
   const double M = pb.result->log_scale;
   KahanSum acc;
@@ -385,7 +472,8 @@ __global__ void __launch_bounds__(256) batched_divergence_kernel(const BProb* pr
     const double sign = side == 0 ? 1.0 : -1.0;
     for (int64_t i = threadIdx.x; i < pb.n[side]; i += blockDim.x)
       acc.add(static_cast<double>(pb.w[side][i]) *
-              (static_cast<double>(logf(pb.s[side][i])) - pb.shift[side][i] - sign * M));
+              ((log_domain ? static_cast<double>(pb.s[side][i]) : static_cast<double>(logf(pb.s[side][i]))) -
+               pb.shift[side][i] - sign * M));
   }
   __shared__ double s_w[8];
   double v = acc.value();
@@ -402,6 +490,15 @@ __global__ void __launch_bounds__(256) batched_divergence_kernel(const BProb* pr
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+using BatchKernel = void (*)(BatchArgs);
+BatchKernel batched_kernel_for(int C, bool logd) {
+  if (logd)
+    return C == 1 ? batched_kernel<1, true> : C == 2 ? batched_kernel<2, true>
+         : C == 4 ? batched_kernel<4, true> : batched_kernel<8, true>;
+  return C == 1 ? batched_kernel<1, false> : C == 2 ? batched_kernel<2, false>
+       : C == 4 ? batched_kernel<4, false> : batched_kernel<8, false>;
+}
+
 struct PlanLayout {
   size_t probs, tiles_x, tiles_y, counter, flag, part_x, part_y, rpart, total;
 };
@@ -411,10 +508,14 @@ struct PlanLayout {
 
 using namespace lsf;
 
-extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int tile_bytes,
-                              lsf_batch_info* info, void* plan, size_t plan_bytes, void* stream) {
+extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int mode,
+                              int tile_bytes, lsf_batch_info* info, void* plan, size_t plan_bytes,
+                              void* stream) {
   if (!probs || !info) return fail(LSF_ERR_ARG, "lsf_batch_plan: NULL argument");
   if (count < 1) return fail(LSF_ERR_ARG, "lsf_batch_plan: count must be >= 1");
+  if (mode != LSF_MODE_STORED && mode != LSF_MODE_LOG)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: mode must be stored or log");
+  const bool logd = mode == LSF_MODE_LOG;
   if (ldr < 4 || ldr % 4 != 0 || ldr > 1024)
     return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: ldr must be a multiple of 4 in [4, 1024]");
   for (int p = 0; p < count; ++p) {
@@ -444,12 +545,8 @@ extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr
 
   // co-resident grid (the kernel's CTAs wait on one another)
   int per_sm = 0;
-  cudaFuncSetAttribute(batched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(batched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(batched_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  void (*kern)(BatchArgs) = C == 1 ? batched_kernel<1> : C == 2 ? batched_kernel<2>
-                          : C == 4 ? batched_kernel<4> : batched_kernel<8>;
+  void (*kern)(BatchArgs) = batched_kernel_for(C, logd);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPassThreads, smem) != cudaSuccess ||
       per_sm < 1)
     return fail(LSF_ERR_UNSUPPORTED, "lsf_batch_plan: kernel cannot be resident");
@@ -492,13 +589,15 @@ extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr
   L.tiles_y = off; off += align256(sizeof(BTile) * tiles[1].size());
   L.counter = off; off += align256(sizeof(unsigned) * count);
   L.flag = off; off += align256(sizeof(unsigned) * count);
-  L.part_x = off; off += align256(sizeof(float) * nslot_total[0] * kConsumerWarps * ldr);
-  L.part_y = off; off += align256(sizeof(float) * nslot_total[1] * kConsumerWarps * ldr);
+  const size_t vec = logd ? 2 : 1;  // (max, sum) pairs in the log domain
+  L.part_x = off; off += align256(sizeof(float) * nslot_total[0] * kConsumerWarps * ldr * vec);
+  L.part_y = off; off += align256(sizeof(float) * nslot_total[1] * kConsumerWarps * ldr * vec);
   L.rpart = off; off += align256(sizeof(double) * nslot_total[0] * kConsumerWarps);
   L.total = off;
 
   info->count = count;
   info->ldr = ldr;
+  info->mode = mode;
   info->tile_rows = static_cast<int>(tr);
   info->stages = S;
   info->grid = grid;
@@ -536,8 +635,8 @@ extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr
       b.nslots[side] = last[side][p] - first[side][p] + 1;
       b.nown[side] = nown[side][p];
     }
-    b.part[0] = reinterpret_cast<float*>(base + L.part_x) + px * kConsumerWarps * ldr;
-    b.part[1] = reinterpret_cast<float*>(base + L.part_y) + py * kConsumerWarps * ldr;
+    b.part[0] = reinterpret_cast<float*>(base + L.part_x) + px * kConsumerWarps * ldr * vec;
+    b.part[1] = reinterpret_cast<float*>(base + L.part_y) + py * kConsumerWarps * ldr * vec;
     b.rpart = reinterpret_cast<double*>(base + L.rpart) + pr * kConsumerWarps;
     px += b.nslots[0];
     py += b.nslots[1];
@@ -582,13 +681,12 @@ extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int ite
   A.rounds = 2 * iters + 2;
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
-    batched_start_kernel<<<count, 256, 0, st>>>(A.probs, A.counter, A.flag, iters);
+    batched_start_kernel<<<count, 256, 0, st>>>(A.probs, A.counter, A.flag, iters,
+                                                 info->mode == LSF_MODE_LOG ? 1 : 0);
   }
   int rc = check_launch("batched_start_kernel");
   if (rc != LSF_OK) return rc;
-  const int C = pass_columns(info->ldr);
-  void (*kern)(BatchArgs) = C == 1 ? batched_kernel<1> : C == 2 ? batched_kernel<2>
-                          : C == 4 ? batched_kernel<4> : batched_kernel<8>;
+  void (*kern)(BatchArgs) = batched_kernel_for(pass_columns(info->ldr), info->mode == LSF_MODE_LOG);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem_bytes);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(info->grid);
@@ -612,7 +710,7 @@ extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int ite
   }
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
-    batched_divergence_kernel<<<count, 256, 0, st>>>(A.probs);
+    batched_divergence_kernel<<<count, 256, 0, st>>>(A.probs, info->mode == LSF_MODE_LOG ? 1 : 0);
   }
   return check_launch("batched_divergence_kernel");
 }

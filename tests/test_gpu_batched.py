@@ -35,7 +35,7 @@ class P:
         self.eps, self.iters, self.src = p.eps, p.iters, p
 
 
-def make_batch(seed, count, n_lo, n_hi, r, iters, eps_lo=0.2):
+def make_batch(seed, count, n_lo, n_hi, r, iters, eps_lo=0.5):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -95,9 +95,37 @@ def test_batched_graph_replay_and_determinism(lsf):
         assert x["W"] == y["W"] and x["residual"] == y["residual"]
 
 
+def test_range_failures_are_resolved_in_the_log_domain(lsf):
+    # small eps with d = 16: some problems leave the FP32 range of the scaling domain
+    probs = []
+    for i, (d, eps) in enumerate([(16, 0.05), (3, 0.5), (16, 0.1), (2, 0.3), (16, 0.05)]):
+        probs.append(synth.small_problem(300 + i, 300 + 50 * i, 250 + 40 * i, d, 128, eps, 30,
+                                         weights="dirichlet", shift=2.0))
+    solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=32 * 1024, mode="auto")
+    solver.run(30)
+    vals = solver.values()
+    for v, p in zip(vals, probs):
+        ref = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=False)
+        assert v["status"] == 0, v
+        assert abs(v["W"] - ref["W_xy"]) <= 1e-4 * abs(ref["W_xy"]), (v["W"], ref["W_xy"])
+
+
+def test_log_domain_batch_matches_oracle(lsf):
+    probs = make_batch(8, 20, 100, 3000, 256, 25, eps_lo=0.05)
+    solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=32 * 1024, mode="log")
+    solver.run(25)
+    for v, p in zip(solver.values(), probs):
+        ref = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=False)
+        th = ref["theta"]
+        spread = max(float(np.ptp(o.log_features(Q, th.U, p.eps, th.q), axis=1).max()) for Q in (p.X, p.Y))
+        assert v["status"] == 0 and v["mode"] == "log"
+        assert abs(v["W"] - ref["W_xy"]) <= 1e-4 * abs(ref["W_xy"]), (v["W"], ref["W_xy"])
+        assert abs(v["residual"] - ref["res_xy"]) <= 1e-5 + 2 * spread * 2.0 ** -23 * ref["res_xy"]
+
+
 def test_autotuner_picks_a_candidate(lsf):
     from paper_2006_07057_gb300 import autotune
     probs = make_batch(7, 10, 500, 3000, 128, 10)
     solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=32 * 1024)
-    tb = autotune.best_batch_tile(solver, use_cache=False)
+    tb = autotune.best_batch_tile(solver.batches[0][0], use_cache=False)
     assert tb in autotune.CANDIDATES
