@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batched", "serving", "diff", "tiny"])
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--count", type=int, default=512)
     return ap.parse_args()
@@ -330,6 +331,151 @@ def run_serving(args):
     return 0
 
 
+def _profile_roofline(lsf, cls, kernel, peak, peak_kind, ms_total):
+    """Roofline entry for one kernel class from the library's CUDA-event records."""
+    k_ms, k_n, k_bytes = lsf.lsf_profile_read(cls)
+    achieved = (k_bytes / 1e9) / (k_ms / 1e3) if k_ms > 0 else None
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+            "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / max(k_n, 1),
+            "bytes_per_launch": k_bytes / max(k_n, 1),
+            "share_of_step": k_ms / ms_total if ms_total > 0 else None}
+
+
+def _timed(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_diff(args):
+    """Differentiation workload: features, the debiased forward solve and the adjoint
+    w.r.t. X, Y, a, b (and the anchors) for n = m = 8192 points in R^128."""
+    import torch
+    import paper_2006_07057_gb300 as lsf
+    torch.cuda.set_device(0)
+    lsf.lib()
+    p = synth.diff_problem(seed=0)
+    dev = torch.device("cuda", 0)
+    t = {k: torch.from_numpy(getattr(p, k)).to(dev) for k in ("X", "Y", "a", "b", "Z")}
+    stream = torch.cuda.current_stream()
+    holder = {}
+
+    def forward():
+        prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps)
+        prob.run(p.iters, debiased=True)
+        holder["prob"] = prob
+
+    def step():
+        forward()
+        holder["g"] = holder["prob"].gradient()
+        holder["gU"] = holder["prob"].anchor_gradient()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    vals = holder["prob"].values()
+    ms_fwd = _timed(forward, args.steps, stream)
+    prob = holder["prob"]
+    ms_adj = _timed(lambda: (prob.gradient(), prob.anchor_gradient()), args.steps, stream)
+    lsf.lsf_profile_enable(True)
+    lsf.lsf_launch_count_reset()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = _timed(step, args.steps, stream)
+    clocks = sampler.stop()
+    launches = lsf.lsf_launch_count()
+    peak, peak_kind = load_peaks()
+    roof = _profile_roofline(lsf, lsf.LSF_KERNEL_PASS, "pass_kernel (32 MiB features: L2-resident)",
+                             peak, peak_kind, ms * args.steps)
+    adj_ms, adj_n, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_ADJOINT)
+    feat_ms, feat_n, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
+    lsf.lsf_profile_enable(False)
+    updates = p.iters * 3 * (p.n + p.m) * p.r
+    line = {
+        "metric": METRIC, "value": updates / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"differentiation: n=m={p.n} points in R^{p.d} (N(0,I) vs N(mu,I), "
+                               f"|mu|=1), uniform weights, eps={p.eps}, r={p.r}, {p.iters} iterations, "
+                               f"debiased forward + adjoint w.r.t. X, Y, a, b and the anchors",
+                   "l2": "features (2 x 32 MiB) stay L2-resident; step counted with features rebuilt"},
+        "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
+        "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
+        "adjoint_kernels_ms_per_step": adj_ms / args.steps, "adjoint_launches": adj_n,
+        "features_ms_per_step": feat_ms / args.steps,
+        "result": {"W_bar": vals["W_bar"], "status": vals["status"]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_tiny(args):
+    """Tiny workload: latency of one whole solve (parameters, features, 100 iterations,
+    Eq. (6)) for n = m = 1000 points in R^2, r = 100: launch-bound, reported per solve,
+    plain stream launches and one CUDA-graph replay of the same solve."""
+    import torch
+    import paper_2006_07057_gb300 as lsf
+    torch.cuda.set_device(0)
+    lsf.lib()
+    p = synth.tiny_problem()
+    dev = torch.device("cuda", 0)
+    t = {k: torch.from_numpy(getattr(p, k)).to(dev) for k in ("X", "Y", "a", "b", "Z")}
+    stream = torch.cuda.current_stream()
+    steps = max(args.steps, 20)
+
+    def solve():
+        prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps)
+        prob.run(p.iters, debiased=False)
+        return prob
+
+    for _ in range(args.warmup):
+        prob = solve()
+    torch.cuda.synchronize()
+    vals = prob.values()
+    lsf.lsf_launch_count_reset()
+    ms_full = _timed(solve, steps, stream)
+    launches = lsf.lsf_launch_count() / steps
+    # the iterations alone, resident problem, captured once in a CUDA graph
+    prob = solve()
+    torch.cuda.synchronize()
+    ms_solve = _timed(lambda: prob.run(p.iters, debiased=False), steps, stream)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        prob.stream = s
+        prob.run(p.iters, debiased=False)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            prob.run(p.iters, debiased=False)
+    prob.stream = None
+    torch.cuda.synchronize()
+    ms_graph = _timed(g.replay, steps, stream)
+    updates = p.iters * (p.n + p.m) * p.r
+    line = {
+        "metric": METRIC, "value": updates / (ms_full / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"tiny: n=m={p.n} points in R^2 (3-component mixture vs the same "
+                               f"mixture + 1), uniform weights, eps={p.eps}, r={p.r}, {p.iters} "
+                               f"iterations, W(a,b) (Eq. 6)",
+                   "l2": "inputs L2-resident (latency-bound workload)"},
+        "gpu_launches_per_solve": launches,
+        "latency_us": {"whole_path": 1e3 * ms_full, "iterations_resident": 1e3 * ms_solve,
+                       "iterations_graph_replay": 1e3 * ms_graph},
+        "result": {"W": vals["W_xy"], "res": vals["res_xy"], "status": vals["status"]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -338,6 +484,10 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "diff":
+        return run_diff(args)
+    if args.workload == "tiny":
+        return run_tiny(args)
     import torch
     world, rank, local = dist_env()
     if world > 1:

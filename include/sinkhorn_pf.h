@@ -317,6 +317,32 @@ int lsf_gradient(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  const lsf_scalings* s_yy, const lsf_result* result, int debiased, int mode,
                  float* gX, float* gY, float* ga, float* gb, void* stream);
 
+/*
+ * Envelope gradient w.r.t. the anchors U (r x d), with q held fixed: the
+ * gradient a learned feature map needs (Sec. 3.3 learns the features through
+ * the same envelope gradient, Prop. 3.3). Every feature of both clouds depends
+ * on u_k through ||p - u_k||^2 and the weight ||u_k||^2/(eps q) of Lemma 1:
+ *   grad u_k = -sum_i A_ik (4 (x_i - u_k) + 2 u_k/q) - sum_j B_jk (4 (y_j - u_k) + 2 u_k/q),
+ *   A_ik = u~_i t_v[k] F_ik (the mass of gradient x_i), B_jk = v~_j t_u[k] G_jk,
+ * with the self terms of Eq. (2) at weight -1/2 when debiased != 0 (s_xx,
+ * s_yy). q is the Lemma 1 parameter the features were built with. mode:
+ * LSF_MODE_STORED or LSF_MODE_LOG, as in lsf_gradient. The device output gU
+ * (r x d) is overwritten with scale * grad U (scale = sigma gives the gradient
+ * w.r.t. the normal draws Z of U = sigma Z). x->X, x->F, y->X, y->F and the
+ * r-vectors of the scalings are required (the r-vectors 16-byte aligned).
+ * workspace: the solve's workspace (lsf_workspace_bytes(ldr) bytes); its
+ * partial region is overwritten, so no solve may use it concurrently.
+ * Summation order is fixed: the result is deterministic.
+ * Errors: LSF_ERR_ARG (NULL or misaligned pointers, bad sizes),
+ * LSF_ERR_UNSUPPORTED (recompute mode, or d so large that the partials do
+ * not fit the workspace: d above 8 * floor(8 * SMs / 9), 1080 on 152 SMs),
+ * LSF_ERR_WORKSPACE.
+ */
+int lsf_anchor_gradient(const lsf_theta* theta, double q, const lsf_cloud* x, const lsf_cloud* y,
+                        const lsf_scalings* s_xy, const lsf_scalings* s_xx,
+                        const lsf_scalings* s_yy, int debiased, int mode, double scale, float* gU,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- tuning */
 
 /*
@@ -337,9 +363,10 @@ typedef enum {
   LSF_KERNEL_PASS = 0,       /* fused Sinkhorn passes (stored features)   */
   LSF_KERNEL_PASS_RECOMPUTE, /* fused Sinkhorn passes (recompute)         */
   LSF_KERNEL_FEATURES,       /* feature build and row shifts              */
-  LSF_KERNEL_OTHER,          /* small kernels: init, reductions, adjoint  */
+  LSF_KERNEL_OTHER,          /* small kernels: init, reductions           */
   LSF_KERNEL_PASS_LOG,       /* fused Sinkhorn passes (log domain)        */
   LSF_KERNEL_BATCHED,        /* batched persistent solver                 */
+  LSF_KERNEL_ADJOINT,        /* gradient kernels (points, weights, anchors) */
   LSF_KERNEL_NCLASSES
 } lsf_kernel_class;
 

@@ -24,7 +24,9 @@ What it computes, in the paper's order and notation (Scetbon & Cuturi,
 * Eq. (6): W_hat = eps (a^T log u + b^T log v).
 * Eq. (2): debiased W_bar = W(a,b) - (W(a,a) + W(b,b))/2 with one shared theta.
 * Prop. 3.3 and the formula after it (Sec. 3.3): dW/dK = -eps u v^T at the
-  optimum, chained through xi(X) with theta held fixed.
+  optimum, chained through xi(X) with theta held fixed; the same chain taken
+  through the anchors U (q held fixed) gives the gradient a learned feature map
+  needs (Sec. 3.3, learning the features).
 
 The primary solver works in the log domain (always representable in FP64).
 ``sinkhorn_scaled`` runs the same iterates in the scaling domain with per-row
@@ -60,6 +62,7 @@ __all__ = [
     "solve",
     "divergence",
     "gradient",
+    "anchor_gradient",
     "deviation",
 ]
 
@@ -394,6 +397,44 @@ def _grad_self(P, U, L, s, eps):
     lt_u = lse(L + s["logu"][:, None], axis=0)
     g = _grad_points(P, U, L, s["logu"], lt_v) + _grad_points(P, U, L, s["logv"], lt_u)
     return g, eps * (s["logu"] + s["logv"])
+
+
+def _grad_anchors(P, U, L, logw, lt, q):
+    """-sum_i exp(log w_i + L_ik + lt_k) * (4 (p_i - u_k) + 2 u_k / q), for every anchor u_k.
+
+    This is -eps sum_i w_i t_k d xi_ik / d u_k with
+    log xi_ik = (d/4) log 2q - (1/2) log r - (2/eps)||p_i - u_k||^2 + ||u_k||^2/(eps q)
+    (Lemma 1, proof form), so d xi_ik / d u_k = xi_ik ((4/eps)(p_i - u_k) + 2 u_k/(eps q)).
+    """
+    Mass = np.exp(logw[:, None] + L + lt[None, :])
+    return -4.0 * (Mass.T @ P) + (4.0 - 2.0 / q) * Mass.sum(axis=0)[:, None] * U
+
+
+def anchor_gradient(X, Y, theta: Theta, state: dict, debiased: bool = True) -> np.ndarray:
+    """Envelope gradient of W (or W_bar) w.r.t. the anchors U (r x d), q held fixed.
+
+    Same chain as ``gradient`` (dW/dK = -eps u v^T at the optimum, Prop. 3.3),
+    taken through the anchors instead of the points: every feature of both
+    clouds depends on u_k, through ||p - u_k||^2 and the weight ||u_k||^2/(eps q).
+    For W(a,a) both factors of xi xi^T depend on U.  Learning U (a learned
+    feature map, Sec. 3.3) needs exactly this block.
+    """
+    eps, U, q = theta.eps, theta.U, theta.q
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    Lx = log_features(X, U, eps, q)
+    Ly = log_features(Y, U, eps, q)
+    s = state["xy"]
+    lt_v = lse(Ly + s["logv"][:, None], axis=0)
+    lt_u = lse(Lx + s["logu"][:, None], axis=0)
+    g = _grad_anchors(X, U, Lx, s["logu"], lt_v, q) + _grad_anchors(Y, U, Ly, s["logv"], lt_u, q)
+    if debiased:
+        for P, L, key in ((X, Lx, "xx"), (Y, Ly, "yy")):
+            t = state[key]
+            g_self = (_grad_anchors(P, U, L, t["logu"], lse(L + t["logv"][:, None], axis=0), q)
+                      + _grad_anchors(P, U, L, t["logv"], lse(L + t["logu"][:, None], axis=0), q))
+            g = g - 0.5 * g_self
+    return g
 
 
 def deviation(rot: float, rot_hat: float) -> float:

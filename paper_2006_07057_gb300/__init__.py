@@ -20,7 +20,8 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_BATCHED,  # noqa: F401
+from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,  # noqa: F401
+                       LSF_KERNEL_BATCHED,
                        LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
                        LsfBatchInfo, LsfBatchProblem,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
@@ -268,6 +269,21 @@ def lsf_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: Scaling
           "lsf_gradient")
 
 
+def lsf_anchor_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: Scalings | None,
+                        s_yy: Scalings | None, debiased: bool, gU, workspace, scale: float = 1.0,
+                        stream=None, mode: str = "stored"):
+    th, cx, cy = theta.as_c(), x.as_c(), y.as_c()
+    a = s_xy.as_c()
+    b = s_xx.as_c() if s_xx is not None else None
+    c = s_yy.as_c() if s_yy is not None else None
+    check(lib().lsf_anchor_gradient(ctypes.byref(th), float(theta.q), ctypes.byref(cx),
+                                    ctypes.byref(cy), ctypes.byref(a),
+                                    ctypes.byref(b) if b else None, ctypes.byref(c) if c else None,
+                                    int(bool(debiased)), MODES[mode], float(scale), _p(gU),
+                                    _p(workspace), workspace.numel(), _stream(stream)),
+          "lsf_anchor_gradient")
+
+
 def lsf_set_pass_tiling(tile_bytes: int, max_stages: int) -> None:
     check(lib().lsf_set_pass_tiling(int(tile_bytes), int(max_stages)), "lsf_set_pass_tiling")
 
@@ -451,6 +467,28 @@ class SinkhornProblem:
         return gX, gY, ga, gb
 
 
+    def anchor_gradient(self, debiased: bool | None = None, wrt: str = "U"):
+        """Envelope gradient of the last run w.r.t. the anchors (q fixed).
+
+        ``wrt="U"`` gives dW/dU (r x d); ``wrt="Z"`` gives dW/dZ = sigma dW/dU for
+        the normal draws of U = sigma Z.
+        """
+        deb = self.debiased if debiased is None else bool(debiased)
+        if deb and not self.debiased:
+            raise ValueError("the debiased gradient needs a debiased run")
+        if self.mode == "recompute":
+            raise NotImplementedError("the adjoint reads stored features")
+        if wrt not in ("U", "Z"):
+            raise ValueError("wrt must be 'U' or 'Z'")
+        th = self.theta
+        gU = torch.empty((th.r, th.d), dtype=torch.float32, device=self.X.device)
+        lsf_anchor_gradient(th, self.x, self.y, self.s_xy, self.s_xx if deb else None,
+                            self.s_yy if deb else None, deb, gU, self.workspace,
+                            scale=th.sigma if wrt == "Z" else 1.0, stream=self.stream,
+                            mode=self.mode)
+        return gU
+
+
 def sinkhorn_divergence(X, Y, a, b, Z, eps: float, iters: int, debiased: bool = True,
                         mode: str = "stored") -> dict:
     """Solve once and return host scalars (W_xy, and W_xx, W_yy, W_bar if debiased)."""
@@ -460,11 +498,13 @@ def sinkhorn_divergence(X, Y, a, b, Z, eps: float, iters: int, debiased: bool = 
 
 
 class SinkhornDivergenceFn(torch.autograd.Function):
-    """W (or the debiased W_bar) as a differentiable function of X, Y, a, b.
+    """W (or the debiased W_bar) as a differentiable function of X, Y, a, b and Z.
 
     theta (R, q, U) is computed from the inputs and then held fixed, as in the
-    gradient formula after Prop. 3.3. The backward pass uses the envelope
-    gradient of the final iterate; no iteration is replayed.
+    gradient formula after Prop. 3.3; the gradient w.r.t. Z (anchors U = sigma Z)
+    moves the anchors with q fixed, as a learned feature map does. The backward
+    pass uses the envelope gradient of the final iterate; no iteration is
+    replayed.
     """
 
     @staticmethod
@@ -479,7 +519,8 @@ class SinkhornDivergenceFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         gX, gY, ga, gb = ctx.prob.gradient()
-        return gX * g, gY * g, ga * g, gb * g, None, None, None, None
+        gZ = ctx.prob.anchor_gradient(wrt="Z") * g if ctx.needs_input_grad[4] else None
+        return gX * g, gY * g, ga * g, gb * g, gZ, None, None, None
 
 
 # ---------------------------------------------------------------- batched solver

@@ -37,6 +37,7 @@ LSF_KERNEL_FEATURES = 2
 LSF_KERNEL_OTHER = 3
 LSF_KERNEL_PASS_LOG = 4
 LSF_KERNEL_BATCHED = 5
+LSF_KERNEL_ADJOINT = 6
 
 
 class LsfTheta(ctypes.Structure):
@@ -100,6 +101,9 @@ _SIGNATURES = {
     "lsf_gradient": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), _P(LsfScalings),
                              _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_int,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lsf_anchor_gradient": (c_int, [_P(LsfTheta), c_double, _P(LsfCloud), _P(LsfCloud),
+                                    _P(LsfScalings), _P(LsfScalings), _P(LsfScalings), c_int,
+                                    c_int, c_double, c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_batch_plan": (c_int, [_P(LsfBatchProblem), c_int, c_int, c_int, c_int, _P(LsfBatchInfo),
                                c_void_p, c_size_t, c_void_p]),
     "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
       const int side = round_side(r, A.rounds);
       const bool copy_w = round_mode(r, A.rounds) != kPassAxpy;
       int64_t lo, hi;
-      tile_range(A.ntiles[side], &lo, &hi);
+      tile_range(side ? A.ntiles[1] : A.ntiles[0], &lo, &hi);
       for (int64_t ti = lo; ti < hi; ++ti, ++it) {
         const int s = it % S;
         const uint32_t ph = static_cast<uint32_t>(it / S) & 1u;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           dead = true;
           break;
         }
-        const BTile tl = A.tiles[side][ti];
+        const BTile tl = (side ? A.tiles[1] : A.tiles[0])[ti];
         const BProb& pb = A.probs[tl.p];
         if (lane == 0) {
           const uint32_t bytes = static_cast<uint32_t>(tl.rows) * static_cast<uint32_t>(ldr) * 4u;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
       const int side = round_side(r, A.rounds);
       const int mode = round_mode(r, A.rounds);
       int64_t lo, hi;
-      tile_range(A.ntiles[side], &lo, &hi);
+      tile_range(side ? A.ntiles[1] : A.ntiles[0], &lo, &hi);
       int cur = -1;
       // scaling domain: t = r-vector, acc = transposed product;
       // log domain: t = log r-vector, acc = running column max, lsum = column sums
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           dead = true;
           break;
         }
-        const BTile tl = A.tiles[side][ti];
+        const BTile tl = (side ? A.tiles[1] : A.tiles[0])[ti];
         if (tl.p != cur) {
           if (cur >= 0) flush(cur);
           cur = tl.p;

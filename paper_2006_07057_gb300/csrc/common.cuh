@@ -42,9 +42,10 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Workspace layout shared by the solver entry points (all offsets 256-aligned).
 struct Workspace {
   float* part;          // [grid][2][2][ldr] per-CTA partial r-vectors (log passes: max and sum)
+  float* gpart;         // [groups][2][2][ldr] per-group partials of the two-level reduction
   double* rpart;        // [grid][2] per-CTA partial residuals
   double* dpart;        // [div_grid][3] per-block partial divergences
-  unsigned* counters;   // [8] arrival counters of the last-CTA reductions
+  unsigned* counters;   // arrival counters: [1] divergence, [kPassCounter ...] passes
   unsigned* keys;       // [8] order-preserving float keys of running maxima
   size_t bytes;
 };
@@ -55,6 +56,14 @@ int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws);
 // CTA, so every pass launcher clamps its grid to this.
 int max_pass_ctas();
 constexpr int kMaxPassCtasPerSm = 2;
+
+// Two-level pass reduction: CTAs are summed in groups of kReduceGroup, then the
+// groups. The pass counters start at counters[kPassCounter]: one for the groups,
+// then one per group.
+constexpr int kReduceGroup = 16;
+constexpr int kPassCounter = 8;
+inline int reduce_groups(int grid) { return (grid + kReduceGroup - 1) / kReduceGroup; }
+int workspace_counters();  // unsigned counters in the workspace
 
 constexpr int kDivGrid = 64;
 

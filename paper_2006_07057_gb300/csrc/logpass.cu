@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
   }
   if (flag) atomicOr(&s_flag, flag);
   __syncthreads();
-  finish_pass_log<NRHS, kAcc>(red, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.rpart,
+  finish_pass_log<NRHS, kAcc>(red, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.gpart, a.rpart,
                               a.counter, a.status, s_flag, &s_last);
 }
 

@@ -19,8 +19,9 @@
 // For r > 512 a warp takes one row from each of two consecutive ring stages, so
 // it still has two independent rows in flight with tiles of modest size.
 // Every wait is bounded and reports LSF_ERR_TIMEOUT. At the end each CTA writes
-// its partial r-vector; the last CTA to arrive sums the partials in CTA order
-// (FP64), so results do not depend on timing.
+// its partial r-vector; the partials are summed in two fixed-order levels
+// (groups of CTAs, then groups; compensated FP32), so results do not depend on
+// timing.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -144,10 +145,22 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
                       ? *reinterpret_cast<const float4*>(tF_u[u] + static_cast<size_t>(rr + q) * ldr + col)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        // this lane's owned row: tile mu, row rr + mq
+        // this lane's owned row: tile mu, row rr + mq. The per-tile values are
+        // picked by compile-time indices (a runtime index would put the arrays in
+        // local memory).
         const int mu = myq / RW, mq = myq - (myq / RW) * RW;
         const int mrow = rr + mq;
-        const bool mvalid = mrow < rows_u[mu];
+        int rows_m = rows_u[0];
+        int64_t row0_m = row0_u[0];
+        const float* vbase_m = vbase_u[0];
+#pragma unroll
+        for (int u = 1; u < TP; ++u)
+          if (mu == u) {
+            rows_m = rows_u[u];
+            row0_m = row0_u[u];
+            vbase_m = vbase_u[u];
+          }
+        const bool mvalid = mrow < rows_m;
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
           float scale[RT];
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
             const float dot = fold_rows<RT>(p, lane, OpAdd());
             float sc = 0.f;
             if (mvalid) {
-              const float* vw = vbase_u[mu] + static_cast<size_t>(k * 2) * TR;
+              const float* vw = vbase_m + static_cast<size_t>(k * 2) * TR;
               const float* vold = vw + TR;
               const float wi = vw[mrow];
               if (has_old[k] && owner)
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
               if (MODE == kPassUpdate) {
                 sc = wi * __frcp_rn(dot);
                 if (owner) {
-                  a.rhs[k].out[row0_u[mu] + mrow] = sc;
+                  a.rhs[k].out[row0_m + mrow] = sc;
                   if (!(dot > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
                 }
               }
@@ -246,7 +259,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
   }
   if (flag) atomicOr(&s_flag, flag);
   __syncthreads();
-  finish_pass<NRHS, kAcc>(red, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.rpart,
+  finish_pass<NRHS, kAcc>(red, kConsumerWarps, &s_res[0][0], ldr, a.rhs, a.part, a.gpart, a.rpart,
                           a.counter, a.status, s_flag, &s_last);
 }
 

@@ -30,8 +30,9 @@ struct PassArgs {
   int nstages;
   PassRhs rhs[2];
   float* part;        // workspace partial r-vectors
+  float* gpart;       // workspace per-group partials of the two-level reduction
   double* rpart;      // workspace partial residuals
-  unsigned* counter;  // workspace arrival counter (zero between launches)
+  unsigned* counter;  // workspace arrival counters [1 + groups] (zero between launches)
   int* status;        // device status word (lsf_result.status)
 };
 

@@ -233,10 +233,10 @@ __global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeAr
   }
   __syncthreads();
   if (kDt)
-    finish_pass<NRHS, false>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.rpart, a.counter,
+    finish_pass<NRHS, false>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.gpart, a.rpart, a.counter,
                              a.status, s_flag, &s_last);
   else
-    finish_pass<NRHS, true>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.rpart, a.counter,
+    finish_pass<NRHS, true>(s_part, NG, &s_res[0][0], ldr, a.rhs, a.part, a.gpart, a.rpart, a.counter,
                             a.status, s_flag, &s_last);
 }
 

@@ -15,6 +15,7 @@ struct RecomputeArgs {
   float two_over_eps;
   PassRhs rhs[2];
   float* part;
+  float* gpart;
   double* rpart;
   unsigned* counter;
   int* status;

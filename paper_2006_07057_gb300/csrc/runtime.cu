@@ -105,13 +105,16 @@ static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255);
 
 int max_pass_ctas() { return device_info().sms * kMaxPassCtasPerSm; }
 
+int workspace_counters() { return kPassCounter + 1 + reduce_groups(max_pass_ctas()); }
+
 size_t workspace_bytes(int ldr) {
   const int grid = max_pass_ctas();
   size_t b = 0;
   b += align256(sizeof(float) * static_cast<size_t>(grid) * 4 * ldr);
+  b += align256(sizeof(float) * static_cast<size_t>(reduce_groups(grid)) * 4 * ldr);
   b += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
   b += align256(sizeof(double) * static_cast<size_t>(kDivGrid) * 3);
-  b += align256(sizeof(unsigned) * 8);
+  b += align256(sizeof(unsigned) * workspace_counters());
   b += align256(sizeof(unsigned) * 8);
   return b;
 }
@@ -127,12 +130,14 @@ int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws) {
   char* p = static_cast<char*>(base);
   ws->part = reinterpret_cast<float*>(p);
   p += align256(sizeof(float) * static_cast<size_t>(grid) * 4 * ldr);
+  ws->gpart = reinterpret_cast<float*>(p);
+  p += align256(sizeof(float) * static_cast<size_t>(reduce_groups(grid)) * 4 * ldr);
   ws->rpart = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
   ws->dpart = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * static_cast<size_t>(kDivGrid) * 3);
   ws->counters = reinterpret_cast<unsigned*>(p);
-  p += align256(sizeof(unsigned) * 8);
+  p += align256(sizeof(unsigned) * workspace_counters());
   ws->keys = reinterpret_cast<unsigned*>(p);
   p += align256(sizeof(unsigned) * 8);
   ws->bytes = need;

@@ -181,8 +181,9 @@ int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int 
     a.ldr = th->ldr;
     for (int k = 0; k < nrhs; ++k) a.rhs[k] = rhs[k];
     a.part = ws.part;
+    a.gpart = ws.gpart;
     a.rpart = ws.rpart;
-    a.counter = ws.counters;
+    a.counter = ws.counters + kPassCounter;
     a.status = status;
     return mode == LSF_MODE_LOG ? launch_logpass(pmode, nrhs, a, st) : launch_pass(pmode, nrhs, a, st);
   }
@@ -198,8 +199,9 @@ int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int 
   a.two_over_eps = static_cast<float>(2.0 / th->eps);
   for (int k = 0; k < nrhs; ++k) a.rhs[k] = rhs[k];
   a.part = ws.part;
+  a.gpart = ws.gpart;
   a.rpart = ws.rpart;
-  a.counter = ws.counters;
+  a.counter = ws.counters + kPassCounter;
   a.status = status;
   return launch_recompute_pass(pmode, nrhs, a, st);
 }
@@ -209,7 +211,7 @@ int start_solve(void* workspace, size_t ws_bytes, int ldr, lsf_result* result, i
   LSF_TRY(carve_workspace(workspace, ws_bytes, ldr, ws));
   if (!result) return fail(LSF_ERR_ARG, "result is NULL");
   if (cudaMemsetAsync(result, 0, sizeof(lsf_result) * nres, st) != cudaSuccess ||
-      cudaMemsetAsync(ws->counters, 0, sizeof(unsigned) * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(ws->counters, 0, sizeof(unsigned) * workspace_counters(), st) != cudaSuccess ||
       cudaMemsetAsync(ws->keys, 0, sizeof(unsigned) * 8, st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "solve: memset failed");
   return LSF_OK;

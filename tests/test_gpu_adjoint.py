@@ -79,3 +79,51 @@ def test_autograd_function_matches_direct_gradient(lsf):
     torch.testing.assert_close(Y.grad, 2.0 * gY)
     torch.testing.assert_close(a.grad, 2.0 * ga)
     torch.testing.assert_close(b.grad, 2.0 * gb)
+
+
+# ---------------------------------------------------------------- anchors (theta gradient)
+
+@pytest.mark.parametrize("debiased", [False, True])
+@pytest.mark.parametrize("n,m,d,r,eps,iters,mode", [
+    (1000, 1000, 2, 100, 0.5, 100, "stored"),   # tiny workload shape
+    (700, 900, 3, 250, 0.2, 60, "stored"),      # ragged r (ldr 252), ragged rows
+    (300, 257, 16, 1024, 1.0, 40, "stored"),    # two coordinate chunks of 8
+    (200, 190, 48, 512, 1.0, 30, "stored"),
+    (1024, 1024, 128, 1024, 1.0, 50, "stored"),  # differentiation workload shape at reduced n
+    (600, 500, 3, 128, 0.3, 40, "log"),          # log-domain features and scalings
+])
+def test_anchor_gradient_matches_oracle(lsf, n, m, d, r, eps, iters, mode, debiased):
+    if d == 128:
+        p = synth.diff_problem(seed=0, n=n, iters=iters)
+    else:
+        p = synth.small_problem(51 + d, n, m, d, r, eps, iters, weights="dirichlet")
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k))).cuda() for k in "XYabZ"}
+    prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps, mode=mode)
+    prob.run(p.iters, debiased=debiased)
+    assert prob.values()["status"] == 0
+    gU = prob.anchor_gradient().double().cpu().numpy()
+    st = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=debiased)
+    ref = o.anchor_gradient(p.X, p.Y, st["theta"], st, debiased=debiased)
+    assert gU.shape == ref.shape
+    assert rel_l2(gU, ref) <= 1e-4, rel_l2(gU, ref)
+    # deterministic: a second call gives the same bits
+    gU2 = prob.anchor_gradient().double().cpu().numpy()
+    assert np.array_equal(gU, gU2)
+
+
+def test_anchor_gradient_wrt_draws_and_autograd(lsf):
+    p = synth.small_problem(43, 500, 400, 3, 128, 0.3, 40, weights="dirichlet")
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k))).cuda() for k in "XYabZ"}
+    Z = t["Z"].clone().requires_grad_(True)
+    W = lsf.SinkhornDivergenceFn.apply(t["X"], t["Y"], t["a"], t["b"], Z, p.eps, p.iters, True)
+    (3.0 * W).backward()
+    prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps)
+    prob.run(p.iters, debiased=True)
+    gU = prob.anchor_gradient(wrt="U")
+    gZ = prob.anchor_gradient(wrt="Z")
+    sigma = prob.theta.sigma
+    torch.testing.assert_close(gZ, sigma * gU, rtol=1e-6, atol=1e-7)
+    torch.testing.assert_close(Z.grad, 3.0 * gZ)
+    st = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=True)
+    ref = sigma * o.anchor_gradient(p.X, p.Y, st["theta"], st, debiased=True)
+    assert rel_l2(gZ.double().cpu().numpy(), ref) <= 1e-4

@@ -342,3 +342,47 @@ def test_envelope_gradient_matches_central_differences(debiased):
             else:
                 fd = (W(X, Y, a, b + e) - W(X, Y, a, b - e)) / (2 * h)
             assert abs((g[name][i] - g[name][j]) - fd) < 1e-8 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("debiased", [False, True])
+def test_anchor_gradient_matches_central_differences(debiased):
+    # q (and R) stay frozen; only the anchors move, as when U is learned.
+    X, Y, a, b, th = _fd_problem()
+    iters = 1500
+    key = "W_bar" if debiased else "W_xy"
+    st = o.divergence(X, Y, a, b, theta=th, iters=iters, debiased=debiased)
+    g = o.anchor_gradient(X, Y, th, st, debiased=debiased)
+    assert g.shape == th.U.shape
+
+    def W(U_):
+        t = o.Theta(th.q, th.sigma, U_, th.eps, th.R)
+        return o.divergence(X, Y, a, b, theta=t, iters=iters, debiased=debiased)[key]
+
+    h = 1e-5
+    fd = np.zeros_like(th.U)
+    for idx in np.ndindex(th.U.shape):
+        e = np.zeros_like(th.U); e[idx] = h
+        fd[idx] = (W(th.U + e) - W(th.U - e)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_joint_translation_gradient_is_the_anchor_weight_term():
+    # Moving X, Y and U together by delta changes only ||u_k||^2/(eps q) (see the
+    # translation pin above), so the directional derivative of W along a common
+    # translation is the derivative of that term alone, computed here by central
+    # differences of W with the points and anchors all moved.
+    X, Y, a, b, th = _fd_problem()
+    iters = 1500
+    st = o.divergence(X, Y, a, b, theta=th, iters=iters, debiased=True)
+    gp = o.gradient(X, Y, a, b, th, st, debiased=True)["W_bar"]
+    gU = o.anchor_gradient(X, Y, th, st, debiased=True)
+    total = gp["X"].sum(0) + gp["Y"].sum(0) + gU.sum(0)
+    h = 1e-5
+    for c in range(X.shape[1]):
+        e = np.zeros(X.shape[1]); e[c] = h
+
+        def W(s):
+            t = o.Theta(th.q, th.sigma, th.U + s * e, th.eps, th.R)
+            return o.divergence(X + s * e, Y + s * e, a, b, theta=t, iters=iters)["W_bar"]
+        fd = (W(1.0) - W(-1.0)) / (2 * h)
+        assert abs(total[c] - fd) < 1e-6 * max(1.0, abs(fd)), (c, total[c], fd)
