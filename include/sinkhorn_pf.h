@@ -356,6 +356,19 @@ int lsf_anchor_gradient(const lsf_theta* theta, double q, const lsf_cloud* x, co
 int lsf_set_pass_tiling(int tile_bytes, int max_stages);
 int lsf_get_pass_tiling(int* tile_bytes, int* max_stages);
 
+/*
+ * Solver choice for stored-feature problems whose features stay in L2 (not a
+ * paper quantity; the iterates are the same). Small problems spend most of a
+ * multi-launch solve in launch and grid-reduction latency, so lsf_solve and
+ * lsf_debiased run them instead in one launch of a cluster-persistent kernel
+ * (one thread-block cluster per solve, the r-vector reduced across the cluster
+ * in distributed shared memory every half iteration). policy: 0 never, 1 when
+ * (n + m) * ldr <= max_entries for every solve of the call (default, with
+ * max_entries = 2^24), 2 always. Process-wide; set it before launching.
+ * Errors: LSF_ERR_ARG for a policy outside 0..2 or max_entries < 0.
+ */
+int lsf_set_small_solver(int policy, int64_t max_entries);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Kernel classes timed by the optional event recorder. */
@@ -367,6 +380,7 @@ typedef enum {
   LSF_KERNEL_PASS_LOG,       /* fused Sinkhorn passes (log domain)        */
   LSF_KERNEL_BATCHED,        /* batched persistent solver                 */
   LSF_KERNEL_ADJOINT,        /* gradient kernels (points, weights, anchors) */
+  LSF_KERNEL_SMALL,          /* cluster-persistent small-problem solver   */
   LSF_KERNEL_NCLASSES
 } lsf_kernel_class;
 

@@ -21,7 +21,7 @@ import numpy as np
 import torch
 
 from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,  # noqa: F401
-                       LSF_KERNEL_BATCHED,
+                       LSF_KERNEL_BATCHED, LSF_KERNEL_SMALL,
                        LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
                        LsfBatchInfo, LsfBatchProblem,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
@@ -282,6 +282,11 @@ def lsf_anchor_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: 
                                     int(bool(debiased)), MODES[mode], float(scale), _p(gU),
                                     _p(workspace), workspace.numel(), _stream(stream)),
           "lsf_anchor_gradient")
+
+
+def lsf_set_small_solver(policy: int, max_entries: int = 1 << 24) -> None:
+    """0: never use the cluster small-problem solver, 1: by size (default), 2: always."""
+    check(lib().lsf_set_small_solver(int(policy), int(max_entries)), "lsf_set_small_solver")
 
 
 def lsf_set_pass_tiling(tile_bytes: int, max_stages: int) -> None:

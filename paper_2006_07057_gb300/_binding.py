@@ -38,6 +38,7 @@ LSF_KERNEL_OTHER = 3
 LSF_KERNEL_PASS_LOG = 4
 LSF_KERNEL_BATCHED = 5
 LSF_KERNEL_ADJOINT = 6
+LSF_KERNEL_SMALL = 7
 
 
 class LsfTheta(ctypes.Structure):
@@ -108,6 +109,7 @@ _SIGNATURES = {
                                c_void_p, c_size_t, c_void_p]),
     "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),
     "lsf_set_pass_tiling": (c_int, [c_int, c_int]),
+    "lsf_set_small_solver": (c_int, [c_int, ctypes.c_int64]),
     "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),
     "lsf_profile_enable": (c_int, [c_int]),
     "lsf_profile_read": (c_int, [c_int, _P(c_double), _P(c_int64), _P(c_double)]),

@@ -44,7 +44,7 @@ struct Workspace {
   float* part;          // [grid][2][2][ldr] per-CTA partial r-vectors (log passes: max and sum)
   float* gpart;         // [groups][2][2][ldr] per-group partials of the two-level reduction
   double* rpart;        // [grid][2] per-CTA partial residuals
-  double* dpart;        // [div_grid][3] per-block partial divergences
+  double* dpart;        // [grid][3] per-block partial divergences
   unsigned* counters;   // arrival counters: [1] divergence, [kPassCounter ...] passes
   unsigned* keys;       // [8] order-preserving float keys of running maxima
   size_t bytes;
@@ -65,7 +65,7 @@ constexpr int kPassCounter = 8;
 inline int reduce_groups(int grid) { return (grid + kReduceGroup - 1) / kReduceGroup; }
 int workspace_counters();  // unsigned counters in the workspace
 
-constexpr int kDivGrid = 64;
+// The divergence reduction runs one block per partial slot, at most max_pass_ctas().
 
 // ---------------------------------------------------------------- device side
 

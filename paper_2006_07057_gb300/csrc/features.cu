@@ -173,6 +173,156 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
     atomicMax(spread_key, __float_as_uint(local_spread));
 }
 
+
+// ---------------------------------------------------------------- large d
+//
+// For d > kFeatDChunk the warp-per-row kernel would restage U for every block
+// of rows. There the distances are a register-tiled contraction instead: a CTA
+// computes a 128-row x 128-anchor tile of D_ik = sum_d (x_id - u_kd)^2 (the same
+// direct differences, accumulated over d in the same order), stages 16 dims of
+// X and U at a time in shared memory, writes L_ik = c_k - (2/eps) D_ik to the
+// output and folds the row maxima into order-preserving keys (a maximum does
+// not depend on the order of the atomics). A warp-per-row pass then turns each
+// row into its shifted form (exp or log) and records the spread.
+constexpr int kTM = 128, kTN = 128, kTK = 16;
+
+__global__ void __launch_bounds__(256)
+    features_tile_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ U,
+                         const float* __restrict__ c, int r, int ldr, float two_over_eps,
+                         float* __restrict__ L, unsigned* __restrict__ row_key) {
+  // rows padded by 4 floats: the transposing stores hit 2 banks at most
+  __shared__ __align__(16) float sX[kTK][kTM + 4];
+  __shared__ __align__(16) float sU[kTK][kTN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kTM;
+  const int k0 = blockIdx.y * kTN;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  // loader roles: dim kk = tid % 16, rows/anchors tid / 16 + 16 s
+  const int lk = tid & 15, lr = tid >> 4;
+  for (int d0 = 0; d0 < d; d0 += kTK) {
+    const int dd = d0 + lk;
+#pragma unroll
+    for (int s8 = 0; s8 < 8; ++s8) {
+      const int rr = lr + 16 * s8;
+      const int64_t i = i0 + rr;
+      sX[lk][rr] = (i < n && dd < d) ? __ldg(X + i * d + dd) : 0.f;
+      const int k = k0 + rr;
+      sU[lk][rr] = (k < r && dd < d) ? __ldg(U + static_cast<int64_t>(k) * d + dd) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTK; ++kk) {
+      const float4 xa = *reinterpret_cast<const float4*>(&sX[kk][4 * ty]);
+      const float4 xb = *reinterpret_cast<const float4*>(&sX[kk][64 + 4 * ty]);
+      const float4 ua = *reinterpret_cast<const float4*>(&sU[kk][4 * tx]);
+      const float4 ub = *reinterpret_cast<const float4*>(&sU[kk][64 + 4 * tx]);
+      const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+      const float uv[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float t = xv[a] - uv[b];
+          acc[a][b] = fmaf(t, t, acc[a][b]);
+        }
+    }
+    __syncthreads();
+  }
+  // epilogue: rows 4ty + a (a < 4) and 64 + 4ty + a - 4 (a >= 4); anchors likewise
+  float cv[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int k = k0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + b - 4);
+    cv[b] = (k < r) ? __ldg(c + k) : 0.f;
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + (a < 4 ? 4 * ty + a : 64 + 4 * ty + a - 4);
+    float mx = -INFINITY;
+    float Lv[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int k = k0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + b - 4);
+      Lv[b] = cv[b] - two_over_eps * acc[a][b];
+      if (k < r) mx = fmaxf(mx, Lv[b]);
+    }
+    // the 16 threads of a half-warp hold the same rows
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (i < n) {
+      float* Li = L + i * ldr;
+      const int ka = k0 + 4 * tx, kb = k0 + 64 + 4 * tx;
+      if (ka < ldr) *reinterpret_cast<float4*>(Li + ka) = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
+      if (kb < ldr) *reinterpret_cast<float4*>(Li + kb) = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
+      if (tx == 0 && mx != -INFINITY) atomicMax(row_key + i, float_key(mx));
+    }
+  }
+}
+
+// Warp per row: shift = the row's maximum (decoded from its key, in place),
+// F_ik = exp(L_ik - shift) (KIND 1, padding 0) or L_ik - shift (KIND 2,
+// padding -inf), and the row's spread max - min.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+    features_shift_kernel(int64_t n, int r, int ldr, float* __restrict__ F, float* shift,
+                          unsigned* spread_key) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  float local_spread = 0.f;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+       i += warps) {
+    const float mx = key_float(reinterpret_cast<const unsigned*>(shift)[i]);
+    __syncwarp();
+    float* Fi = F + i * ldr;
+    float mn = INFINITY;
+    for (int col = 4 * lane; col < ldr; col += 128) {
+      float4 v = *reinterpret_cast<float4*>(Fi + col);
+      float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (col + q < r) {
+          mn = fminf(mn, e[q]);
+          e[q] = KIND == 1 ? expf(e[q] - mx) : e[q] - mx;
+        } else {
+          e[q] = KIND == 1 ? 0.f : -INFINITY;
+        }
+      }
+      *reinterpret_cast<float4*>(Fi + col) = make_float4(e[0], e[1], e[2], e[3]);
+    }
+    mn = warp_min(mn);
+    if (lane == 0) shift[i] = mx;
+    local_spread = fmaxf(local_spread, mx - mn);
+  }
+  if (spread_key && lane == 0 && local_spread > 0.f)
+    atomicMax(spread_key, __float_as_uint(local_spread));
+}
+
+template <int KIND>
+int launch_features_tiled(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
+                          unsigned* skey, float toe, cudaStream_t st) {
+  if (cudaMemsetAsync(shift, 0, sizeof(float) * static_cast<size_t>(n), st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "features: memset failed");
+  {
+    LaunchScope ls(st, LSF_KERNEL_FEATURES, 4.0 * n * th->d + 4.0 * n * th->ldr);
+    dim3 grid(static_cast<unsigned>((n + kTM - 1) / kTM), static_cast<unsigned>((th->ldr + kTN - 1) / kTN));
+    features_tile_kernel<<<grid, 256, 0, st>>>(X, n, th->d, th->U, th->c, th->r, th->ldr, toe, F,
+                                               reinterpret_cast<unsigned*>(shift));
+    int rc = check_launch("features_tile_kernel");
+    if (rc != LSF_OK) return rc;
+  }
+  LaunchScope ls(st, LSF_KERNEL_FEATURES, 8.0 * n * th->ldr + 4.0 * n);
+  int64_t grid = (n + 7) / 8;
+  const int64_t cap = static_cast<int64_t>(device_info().sms) * 8;
+  if (grid > cap) grid = cap;
+  features_shift_kernel<KIND><<<static_cast<unsigned>(grid), 256, 0, st>>>(n, th->r, th->ldr, F, shift, skey);
+  return check_launch("features_shift_kernel");
+}
+
 template <int KIND>
 int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
                     float* spread, cudaStream_t st) {
@@ -197,6 +347,7 @@ int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, fl
   if (grid > cap) grid = cap;
   const float toe = static_cast<float>(2.0 / th->eps);
   unsigned* skey = reinterpret_cast<unsigned*>(spread);
+  if (STORE && th->d > kFeatDChunk) return launch_features_tiled<KIND>(X, n, th, F, shift, skey, toe, st);
   double bytes = 4.0 * n * th->d + 4.0 * n + (STORE ? 4.0 * n * ldr : 0.0);
   LaunchScope ls(st, LSF_KERNEL_FEATURES, bytes);
 #define LSF_FEAT_CASE(CC)                                                                  \

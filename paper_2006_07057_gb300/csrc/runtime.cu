@@ -113,7 +113,7 @@ size_t workspace_bytes(int ldr) {
   b += align256(sizeof(float) * static_cast<size_t>(grid) * 4 * ldr);
   b += align256(sizeof(float) * static_cast<size_t>(reduce_groups(grid)) * 4 * ldr);
   b += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
-  b += align256(sizeof(double) * static_cast<size_t>(kDivGrid) * 3);
+  b += align256(sizeof(double) * static_cast<size_t>(grid) * 3);
   b += align256(sizeof(unsigned) * workspace_counters());
   b += align256(sizeof(unsigned) * 8);
   return b;
@@ -135,7 +135,7 @@ int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws) {
   ws->rpart = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * static_cast<size_t>(grid) * 2);
   ws->dpart = reinterpret_cast<double*>(p);
-  p += align256(sizeof(double) * static_cast<size_t>(kDivGrid) * 3);
+  p += align256(sizeof(double) * static_cast<size_t>(grid) * 3);
   ws->counters = reinterpret_cast<unsigned*>(p);
   p += align256(sizeof(unsigned) * workspace_counters());
   ws->keys = reinterpret_cast<unsigned*>(p);

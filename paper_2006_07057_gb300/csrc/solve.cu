@@ -3,8 +3,11 @@
 // divergence reduction).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pass.cuh"
 #include "recompute.cuh"
+#include "small.cuh"
 
 namespace lsf {
 namespace {
@@ -43,6 +46,29 @@ __global__ void set_iters_kernel(lsf_result* r0, lsf_result* r1, lsf_result* r2,
   }
 }
 
+// The three solves of Eq. (2) report their status bits jointly (as the lock-step
+// schedule does, where they share passes): OR them and mirror.
+__global__ void merge_status_kernel(lsf_result* r0, lsf_result* r1, lsf_result* r2) {
+  if (threadIdx.x == 0) {
+    const int32_t s = r0->status | r1->status | r2->status;
+    r0->status = s;
+    r1->status = s;
+    r2->status = s;
+  }
+}
+
+SProb small_problem(const lsf_cloud* x, const lsf_cloud* y, const lsf_scalings* s, lsf_result* r) {
+  SProb p{};
+  p.F[0] = x->F; p.F[1] = y->F;
+  p.w[0] = x->w; p.w[1] = y->w;
+  p.shift[0] = x->shift; p.shift[1] = y->shift;
+  p.s[0] = s->u; p.s[1] = s->v;
+  p.t[0] = s->t_u; p.t[1] = s->t_v;
+  p.result = r;
+  p.n[0] = x->n; p.n[1] = y->n;
+  return p;
+}
+
 // ---------------------------------------------------------------- Eq. (6) reduction
 
 struct DivSeg {
@@ -73,50 +99,61 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Eq. (6) for up to three solves, W_t = eps sum over the segments of term t of
+// w_i (log s_i - shift_i -+ M_t). Each thread sums its elements in FP64 (a few
+// dozen terms); the cross-thread and cross-block folds are fixed-order, and the
+// final fold over the blocks is compensated (Neumaier, FP64).
 __global__ void __launch_bounds__(256) divergence_kernel(const DivArgs a) {
   __shared__ double s_w[8][3];
+  __shared__ double s_lane[32][3];
   __shared__ int s_last;
-  KahanSum acc[3];
+  double acc[3] = {0.0, 0.0, 0.0};
   for (int sgi = 0; sgi < a.nseg; ++sgi) {
     const DivSeg sg = a.seg[sgi];
-    const double M = a.res[sg.term]->log_scale;
+    const double off = static_cast<double>(sg.sign) * a.res[sg.term]->log_scale;
     const int64_t chunk = (sg.n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = chunk * blockIdx.x;
     const int64_t hi = min(sg.n, lo + chunk);
-    KahanSum part;
+    double part = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const double ls = sg.is_log ? static_cast<double>(sg.s[i]) : static_cast<double>(logf(sg.s[i]));
-      const double lg = ls - static_cast<double>(sg.shift[i]) - sg.sign * M;
-      part.add(static_cast<double>(sg.w[i]) * lg);
+      part = fma(static_cast<double>(sg.w[i]), ls - static_cast<double>(sg.shift[i]) - off, part);
     }
-    // Fold this segment's thread sum into its term in a fixed order.
-    if (sg.term == 0) acc[0].add(part.value());
-    else if (sg.term == 1) acc[1].add(part.value());
-    else acc[2].add(part.value());
+    if (sg.term == 0) acc[0] += part;
+    else if (sg.term == 1) acc[1] += part;
+    else acc[2] += part;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    const double v = warp_sum_d(acc[t].value());
+    const double v = warp_sum_d(acc[t]);
     if (lane == 0) s_w[warp][t] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int t = 0; t < 3; ++t) {
-      KahanSum b;
-      for (int w = 0; w < 8; ++w) b.add(s_w[w][t]);
-      a.dpart[blockIdx.x * 3 + t] = b.value();
+      double b = 0.0;
+      for (int w = 0; w < 8; ++w) b += s_w[w][t];
+      a.dpart[blockIdx.x * 3 + t] = b;
     }
     __threadfence();
     s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1u) ? 1 : 0;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last || warp != 0) return;
   __threadfence();
+  // lane l folds blocks l, l + 32, ... (compensated), then lane 0 folds the lanes in order
+  for (int t = 0; t < a.nterms; ++t) {
+    KahanSum k;
+    for (unsigned g = lane; g < gridDim.x; g += 32) k.add(__ldcg(a.dpart + g * 3 + t));
+    s_lane[lane][t] = k.value();
+  }
+  __syncwarp();
+  if (lane != 0) return;
   double comb = 0.0;
   for (int t = 0; t < a.nterms; ++t) {
     KahanSum tot;
-    for (unsigned g = 0; g < gridDim.x; ++g) tot.add(__ldcg(a.dpart + g * 3 + t));
+    for (int l = 0; l < 32; ++l) tot.add(s_lane[l][t]);
     const double W = a.eps * tot.value();
     a.res[t]->W = W;
     comb += a.coef[t] * W;
@@ -247,7 +284,10 @@ int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* x
   }
   for (int t = nterms; t < 3; ++t) a.res[t] = res[0];
   LaunchScope ls(st, LSF_KERNEL_OTHER, bytes);
-  divergence_kernel<<<kDivGrid, 256, 0, st>>>(a);
+  int64_t most = 1;
+  for (int t = 0; t < a.nseg; ++t) most = std::max<int64_t>(most, a.seg[t].n);
+  const int grid = static_cast<int>(std::min<int64_t>(max_pass_ctas(), (most + 255) / 256));
+  divergence_kernel<<<grid, 256, 0, st>>>(a);
   return check_launch("divergence_kernel");
 }
 
@@ -270,6 +310,10 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
   Workspace ws{};
   LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 1, &ws, st));
   int* status = &result->status;
+  if (mode == LSF_MODE_STORED && small_solver_takes(x->n, y->n, theta->ldr)) {
+    const SProb p = small_problem(x, y, out, result);
+    return small_solve(&p, 1, theta->ldr, iters, st);
+  }
 
   LSF_TRY(init_side(y, ws.keys + 0, out->v, &result->log_scale, nullptr, mode, st));
   {
@@ -338,6 +382,24 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
   lsf_result* rxx = result + 1;
   lsf_result* ryy = result + 2;
   int* status = &rxy->status;
+  if (mode == LSF_MODE_STORED && small_solver_takes(x->n, y->n, theta->ldr) &&
+      small_solver_takes(x->n, x->n, theta->ldr) && small_solver_takes(y->n, y->n, theta->ldr)) {
+    // one cluster per solve of Eq. (2), all in one launch
+    const SProb p[3] = {small_problem(x, y, s_xy, rxy), small_problem(x, x, s_xx, rxx),
+                        small_problem(y, y, s_yy, ryy)};
+    LSF_TRY(small_solve(p, 3, theta->ldr, iters, st));
+    {
+      LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+      merge_status_kernel<<<1, 32, 0, st>>>(rxy, rxx, ryy);
+      LSF_TRY(check_launch("merge_status_kernel"));
+    }
+    const lsf_cloud* xs[3] = {x, x, y};
+    const lsf_cloud* ys[3] = {y, x, y};
+    const lsf_scalings* ss[3] = {s_xy, s_xx, s_yy};
+    lsf_result* rs[3] = {rxy, rxx, ryy};
+    const double coef[3] = {1.0, -0.5, -0.5};
+    return launch_divergence(theta, 3, xs, ys, ss, rs, coef, wbar, ws, st, 0);
+  }
 
   // v = 1 for all three solves: v~ = exp(shift - max shift) on the side each v lives on.
   LSF_TRY(init_side(y, ws.keys + 0, s_xy->v, &rxy->log_scale, &ryy->log_scale, mode, st));

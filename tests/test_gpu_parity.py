@@ -102,7 +102,9 @@ def test_tiny_golden_values(lsf):
 # ---------------------------------------------------------------- features
 
 @pytest.mark.parametrize("n,d,r,eps", [(1000, 2, 100, 0.5), (300, 16, 256, 0.2),
-                                       (257, 128, 1024, 1.0), (33, 3, 1, 0.1), (5, 3, 7, 0.3)])
+                                       (257, 128, 1024, 1.0), (33, 3, 1, 0.1), (5, 3, 7, 0.3),
+                                       # d > 32: tiled distance kernel, ragged d, r and rows
+                                       (300, 33, 250, 0.7), (129, 64, 100, 1.0), (1, 40, 3, 1.0)])
 def test_features_match_oracle(lsf, n, d, r, eps):
     p = synth.small_problem(1, n, n + 3, d, r, eps, 1)
     X, Y, a, b, Z = dev(p)
@@ -127,6 +129,24 @@ def test_features_match_oracle(lsf, n, d, r, eps):
     Ly = o.log_features(p.Y, th.U, eps, th.q)
     sp = max((L.max(1) - L.min(1)).max(), (Ly.max(1) - Ly.min(1)).max())
     assert abs(spread - sp) <= 1e-4 * sp + 1e-4
+
+
+@pytest.mark.parametrize("n,d,r,eps", [(300, 16, 256, 0.2), (300, 33, 250, 0.7), (257, 128, 1024, 1.0)])
+def test_log_features_match_oracle(lsf, n, d, r, eps):
+    # the log-domain mode stores L - shift (padding -inf)
+    p = synth.small_problem(2, n, n + 3, d, r, eps, 1)
+    X, Y, a, b, Z = dev(p)
+    prob = lsf.SinkhornProblem(X, Y, a, b, Z, eps, mode="log")
+    th = o.make_theta(p.X, p.Y, p.Z, eps)
+    L = o.log_features(p.X, th.U, eps, th.q)
+    shift = L.max(axis=1)
+    c = (d / 4) * math.log(2 * th.q) - 0.5 * math.log(r) + (th.U ** 2).sum(1) / (eps * th.q)
+    tolL = (2 * math.sqrt(d) + 4) * (np.abs(L) + np.abs(c)[None, :]) * 2.0 ** -24
+    G = prob.x.F.double().cpu().numpy()
+    assert np.all(np.isneginf(G[:, r:]))
+    ref = L - shift[:, None]
+    assert np.all(np.abs(G[:, :r] - ref) <= 2 * (tolL + tolL.max(axis=1)[:, None]) + 1e-6)
+    assert np.all(np.abs(prob.x.shift.double().cpu().numpy() - shift) <= tolL.max(axis=1) + 1e-6)
 
 
 # ---------------------------------------------------------------- ragged shapes and tails
