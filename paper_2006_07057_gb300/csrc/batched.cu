@@ -391,24 +391,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
             }
             if (mode != kPassDot) {
               if (LOGD) {
+                // online (max, sum) per column, one ex2 per entry
 #pragma unroll
                 for (int j = 0; j < C; ++j)
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    float y[RW];
-                    float cm = -INFINITY;
-#pragma unroll
-                    for (int q = 0; q < RW; ++q) {
-                      const float fv = e == 0 ? f[q][j].x : e == 1 ? f[q][j].y : e == 2 ? f[q][j].z : f[q][j].w;
-                      y[q] = fv + scale[q];
-                      cm = fmaxf(cm, y[q]);
-                    }
-                    if (cm != -INFINITY) {
-                      float cs = 0.f;
-#pragma unroll
-                      for (int q = 0; q < RW; ++q) cs += ex2_approx((y[q] - cm) * kLog2e);
-                      lse_merge(acc[j][e], lsum[LOGD ? j : 0][e], cm, cs);
-                    }
+                  for (int q = 0; q < RW; ++q) {
+                    lse_push(acc[j][0], lsum[LOGD ? j : 0][0], f[q][j].x + scale[q]);
+                    lse_push(acc[j][1], lsum[LOGD ? j : 0][1], f[q][j].y + scale[q]);
+                    lse_push(acc[j][2], lsum[LOGD ? j : 0][2], f[q][j].z + scale[q]);
+                    lse_push(acc[j][3], lsum[LOGD ? j : 0][3], f[q][j].w + scale[q]);
                   }
               } else {
 #pragma unroll

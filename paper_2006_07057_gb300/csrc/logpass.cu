@@ -13,8 +13,10 @@
 // Layout is that of the stored pass (same copy ring; a warp takes RW = 8/C rows at
 // full width): the RW row maxima and then the shifted row sums are folded across
 // the warp by the multi-row butterfly; the column side keeps a running (max, sum)
-// pair per column, merged once per RW rows, and warps then CTAs are merged in a
-// fixed order at the end.
+// pair per column, updated online with one ex2 per entry, and warps then CTAs are
+// merged in a fixed order at the end. A two right-hand-side pass at C >= 4 runs as
+// two one-RHS launches: two (max, sum) states per column would not fit in
+// registers, and the pass is bound by ex2, not by the second read of F.
 #include <cuda_runtime.h>
 
 #include "reduce.cuh"
@@ -156,25 +158,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
             for (int q = 0; q < RW; ++q) fq[q] = __shfl_sync(0xffffffffu, fi, q << SH);
           }
           if (kAcc) {
-            // column side: fold the RW rows into one (max, sum) per column
+            // column side: online (max, sum) per column, one ex2 per entry
 #pragma unroll
             for (int j = 0; j < C; ++j)
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                float y[RW];
-                float cm = -INFINITY;
-#pragma unroll
-                for (int q = 0; q < RW; ++q) {
-                  const float fv = e == 0 ? f[q][j].x : e == 1 ? f[q][j].y : e == 2 ? f[q][j].z : f[q][j].w;
-                  y[q] = fv + fq[q];
-                  cm = fmaxf(cm, y[q]);
-                }
-                if (cm != -INFINITY) {
-                  float cs = 0.f;
-#pragma unroll
-                  for (int q = 0; q < RW; ++q) cs += ex2_approx((y[q] - cm) * kLog2e);
-                  lse_merge(lm[k][j][e], ls[k][j][e], cm, cs);
-                }
+              for (int q = 0; q < RW; ++q) {
+                lse_push(lm[k][j][0], ls[k][j][0], f[q][j].x + fq[q]);
+                lse_push(lm[k][j][1], ls[k][j][1], f[q][j].y + fq[q]);
+                lse_push(lm[k][j][2], ls[k][j][2], f[q][j].z + fq[q]);
+                lse_push(lm[k][j][3], ls[k][j][3], f[q][j].w + fq[q]);
               }
           }
         }
@@ -233,11 +225,14 @@ int launch_log_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, c
 
 template <int NRHS>
 int launch_log_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {
-  switch (pass_columns(a.ldr)) {
-    case 1: return launch_log_c_nrhs<1, NRHS>(mode, a, grid, smem, st);
-    case 2: return launch_log_c_nrhs<2, NRHS>(mode, a, grid, smem, st);
-    case 4: return launch_log_c_nrhs<4, NRHS>(mode, a, grid, smem, st);
-    default: return launch_log_c_nrhs<8, NRHS>(mode, a, grid, smem, st);
+  const int c = pass_columns(a.ldr);
+  if (c == 1) return launch_log_c_nrhs<1, NRHS>(mode, a, grid, smem, st);
+  if (c == 2) return launch_log_c_nrhs<2, NRHS>(mode, a, grid, smem, st);
+  if constexpr (NRHS == 1) {
+    if (c == 4) return launch_log_c_nrhs<4, 1>(mode, a, grid, smem, st);
+    return launch_log_c_nrhs<8, 1>(mode, a, grid, smem, st);
+  } else {
+    return fail(LSF_ERR_UNSUPPORTED, "logpass: two right-hand sides need ldr <= 256");
   }
 }
 
@@ -252,6 +247,20 @@ int launch_logpass(int mode, int nrhs, PassArgs a, cudaStream_t st) {
   for (int k = 0; k < nrhs; ++k) with_old |= a.rhs[k].old != nullptr;
   LaunchScope ls(st, LSF_KERNEL_PASS_LOG, pass_bytes(mode, nrhs, a.n, a.ldr, with_old));
   if (nrhs == 1) return launch_log_nrhs<1>(mode, a, grid, smem, st);
+  if (pass_columns(a.ldr) >= 4) {
+    for (int k = 0; k < 2; ++k) {
+      PassArgs one = a;
+      one.rhs[0] = a.rhs[k];
+      one.rhs[1] = PassRhs{};
+      size_t smem1 = 0;
+      unsigned grid1 = 0;
+      int rc1 = plan_pass(one, 1, 2 * a.ldr, &smem1, &grid1);
+      if (rc1 != LSF_OK) return rc1;
+      rc1 = launch_log_nrhs<1>(mode, one, grid1, smem1, st);
+      if (rc1 != LSF_OK) return rc1;
+    }
+    return LSF_OK;
+  }
   return launch_log_nrhs<2>(mode, a, grid, smem, st);
 }
 

@@ -10,18 +10,22 @@
 // accumulation of the same pass. HBM traffic drops to the points and vectors;
 // the bound becomes the FMA and MUFU pipes.
 //
-// Layout: 256 threads; a row group of GW warps owns one row at a time with each
-// thread holding four consecutive feature columns (their A_k and W_kd stay in
-// registers for the whole launch). A batch gives every group 8 rows; row data
-// (x, B, weights, previous scalings) for the next batch is loaded into registers
-// while the current batch computes, then parked in the other shared buffer.
-// Cross-warp row sums go through shared memory in a fixed order.
+// Layout: 256 threads; a row group of GW warps covers a row, each thread holding
+// four consecutive feature columns (their A_k and W_kd stay in registers for the
+// whole launch). A batch gives every group 8 rows; the rows' records (x, B,
+// weights, previous scalings; float4-packed) for the next batch are loaded into
+// registers while the current batch computes, then parked in the other shared
+// buffer. A warp folds its 8 row products with the multi-row butterfly (9
+// shuffles); one thread per row then sums the group's warps in a fixed order,
+// forms the new scaling (division, residual term, status) and shares it through
+// shared memory, so the division and the residual are done once per row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "recompute.cuh"
 #include "reduce.cuh"
+#include "ring.cuh"
 
 namespace lsf {
 namespace {
@@ -30,20 +34,25 @@ constexpr int kRcThreads = 256;
 constexpr int kRcWarps = kRcThreads / 32;
 constexpr int kRcRB = 8;  // rows per group per batch
 
-// Row data slots per row in shared memory: x[D], B, then per rhs (w, old).
-template <int D, int NRHS>
-struct RowSlots {
-  static constexpr int kStride = D + 1 + 2 * NRHS;
+// Row record in shared memory, in float4s: x_0 .. x_{D-1}, B (padded to a float4
+// boundary), then (w, old) of each right-hand side.
+template <int D>
+struct RowPack {
+  static constexpr int kXV = (D + 1 + 3) / 4;  // float4s of x and B
+  static constexpr int kSV = kXV + 1;          // + (w0, old0, w1, old1)
 };
 
 template <int GW, int D, int NRHS>
-__global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeArgs a, const int mode) {
+__global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
+    recompute_kernel(const RecomputeArgs a, const int mode) {
   constexpr int NG = kRcWarps / GW;         // row groups per CTA
   constexpr int RPB = NG * kRcRB;           // rows per batch
   constexpr int TPG = GW * 32;              // threads per group
-  constexpr int SR = RowSlots<D, NRHS>::kStride;
-  __shared__ float s_rows[2][RPB * SR];
-  __shared__ float s_red[NRHS * kRcRB * kRcWarps];  // per-warp partial row products
+  constexpr int XV = RowPack<D>::kXV;
+  constexpr int SV = RowPack<D>::kSV;
+  __shared__ __align__(16) float4 s_rows[2][RPB * SV];
+  __shared__ float s_red[NRHS][kRcRB][kRcWarps];     // per-warp partial row products
+  __shared__ __align__(16) float s_sc[NRHS][NG][kRcRB];  // the rows' new scalings
   __shared__ double s_res[kRcWarps][2];
   __shared__ int s_flag, s_last;
   extern __shared__ __align__(16) float s_part[];  // [NG][NRHS * ldr] at the end
@@ -52,7 +61,6 @@ __global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeAr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp / GW;                  // my group
   const int tg = tid - g * TPG;             // my thread index inside the group
-  const int wg = warp - g * GW;             // my warp index inside the group
   const int ldr = a.ldr, d = a.d;
   const int col0 = 4 * tg;                  // my four columns
 
@@ -94,35 +102,48 @@ __global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeAr
   int flag = 0;
 
   const int64_t nbatch = (a.n + RPB - 1) / RPB;
-  // register prefetch of one row's data by threads tid < RPB
-  float pre[SR];
+  // register prefetch of one row's record by threads tid < RPB
+  float4 pre[SV];
   auto load_rows = [&](int64_t b) {
     if (tid >= RPB) return;
     const int64_t i = b * RPB + tid;
-    if (b >= nbatch || i >= a.n) {
+    float rec[4 * SV];
 #pragma unroll
-      for (int q = 0; q < SR; ++q) pre[q] = 0.f;
-      pre[D] = -INFINITY;
-      return;
-    }
-    float nrm = 0.f;
+    for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
+    if (b < nbatch && i < a.n) {
+      float nrm = 0.f;
 #pragma unroll
-    for (int dd = 0; dd < D; ++dd) {
-      const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
-      pre[dd] = x;
-      nrm = fmaf(x, x, nrm);
-    }
-    pre[D] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
+      for (int dd = 0; dd < D; ++dd) {
+        const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
+        rec[dd] = x;
+        nrm = fmaf(x, x, nrm);
+      }
+      rec[D] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) {
-      pre[D + 1 + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
-      pre[D + 2 + 2 * k] = has_old[k] ? a.rhs[k].old[i] : 0.f;
+      for (int k = 0; k < NRHS; ++k) {
+        rec[4 * XV + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
+        rec[4 * XV + 2 * k + 1] = has_old[k] ? a.rhs[k].old[i] : 0.f;
+      }
+    } else {
+      rec[D] = -INFINITY;  // rows past the end carry no mass
     }
+#pragma unroll
+    for (int v = 0; v < SV; ++v) pre[v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
   };
-  auto park_rows = [&](int buf) {
+  auto park_rows = [&](int bf) {
     if (tid >= RPB) return;
 #pragma unroll
-    for (int q = 0; q < SR; ++q) s_rows[buf][tid * SR + q] = pre[q];
+    for (int v = 0; v < SV; ++v) s_rows[bf][tid * SV + v] = pre[v];
+  };
+  // the new scaling of one row (Update), its residual term, status and output
+  auto finish_row = [&](int k, int64_t i, float s, float wi, float oi) -> float {
+    if (has_old[k])
+      res[k] += fabs(static_cast<double>(oi) * static_cast<double>(s) - static_cast<double>(wi));
+    if (!kUpd) return 0.f;
+    const float sc = wi * __frcp_rn(s);
+    a.rhs[k].out[i] = sc;
+    if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
+    return sc;
   };
 
   int buf = 0;
@@ -131,80 +152,110 @@ __global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeAr
   __syncthreads();
   for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
     load_rows(b + gridDim.x);  // in flight while this batch computes
-    const float* rows = s_rows[buf];
+    const float4* rows = s_rows[buf];
+    const int64_t row0 = b * RPB;
     float F[kRcRB][4];
     float dots[NRHS][kRcRB];
 #pragma unroll
     for (int q = 0; q < kRcRB; ++q) {
-      const float* rw = rows + (g * kRcRB + q) * SR;
-      const float B = rw[D];
+      const float4* rw = rows + (g * kRcRB + q) * SV;
+      float xb[4 * XV];
+#pragma unroll
+      for (int v = 0; v < XV; ++v) {
+        const float4 f4 = rw[v];
+        xb[4 * v] = f4.x; xb[4 * v + 1] = f4.y; xb[4 * v + 2] = f4.z; xb[4 * v + 3] = f4.w;
+      }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        float E = Ap[e] + B;
+        float E = Ap[e] + xb[D];
 #pragma unroll
-        for (int dd = 0; dd < D; ++dd) E = fmaf(rw[dd], Wp[e][dd], E);
+        for (int dd = 0; dd < D; ++dd) E = fmaf(xb[dd], Wp[e][dd], E);
         F[q][e] = ex2_approx(E);
       }
 #pragma unroll
       for (int k = 0; k < NRHS; ++k)
         dots[k][q] = fmaf(F[q][0], t[k][0], fmaf(F[q][1], t[k][1], fmaf(F[q][2], t[k][2], F[q][3] * t[k][3])));
     }
-    if (!kAx) {
+    float sc[NRHS][kRcRB];
+    bool parked = false;
+    if (kAx) {
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k)
+      for (int q = 0; q < kRcRB; ++q) {
+        const float4 wo = rows[(g * kRcRB + q) * SV + XV];
+        sc[0][q] = wo.y;
+        if (NRHS > 1) sc[NRHS - 1][q] = wo.w;
+      }
+    } else {
+      // warp partials of the 8 rows: lanes 4q .. 4q + 3 hold row q
+      float v[NRHS];
 #pragma unroll
-        for (int q = 0; q < kRcRB; ++q) dots[k][q] = warp_sum(dots[k][q]);
-      if (GW > 1) {
-        if (lane == 0) {
+      for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
+      const int q = lane >> 2;
+      const bool lead = (lane & 3) == 0;
+      if (GW == 1) {
+        // a group is one warp: the quad leader of row q finishes it
+        const int64_t i = row0 + g * kRcRB + q;
+        const float4 wo = rows[(g * kRcRB + q) * SV + XV];
+        float mine[NRHS];
 #pragma unroll
-          for (int k = 0; k < NRHS; ++k)
-#pragma unroll
-            for (int q = 0; q < kRcRB; ++q) s_red[(k * kRcRB + q) * kRcWarps + warp] = dots[k][q];
+        for (int k = 0; k < NRHS; ++k) {
+          mine[k] = 0.f;
+          if (lead && i < a.n)
+            mine[k] = finish_row(k, i, v[k], k == 0 ? wo.x : wo.z, k == 0 ? wo.y : wo.w);
         }
-        __syncthreads();
 #pragma unroll
         for (int k = 0; k < NRHS; ++k)
 #pragma unroll
-          for (int q = 0; q < kRcRB; ++q) {
-            const float* pr = s_red + (k * kRcRB + q) * kRcWarps + g * GW;
-            float s = 0.f;
+          for (int qq = 0; qq < kRcRB; ++qq) sc[k][qq] = __shfl_sync(0xffffffffu, mine[k], qq << 2);
+      } else {
+        if (lead)
 #pragma unroll
-            for (int w = 0; w < GW; ++w) s += pr[w];
-            dots[k][q] = s;
+          for (int k = 0; k < NRHS; ++k) s_red[k][q][warp] = v[k];
+        __syncthreads();
+        park_rows(buf ^ 1);
+        parked = true;
+        // one thread per (rhs, group, row): warps of the group in a fixed order
+        if (tid < NRHS * NG * kRcRB) {
+          const int k = tid / (NG * kRcRB);
+          const int gg = (tid / kRcRB) % NG;
+          const int qq = tid % kRcRB;
+          float s = 0.f;
+#pragma unroll
+          for (int w = 0; w < GW; ++w) s += s_red[k][qq][gg * GW + w];
+          const int64_t i = row0 + gg * kRcRB + qq;
+          const float4 wo = rows[(gg * kRcRB + qq) * SV + XV];
+          float scv = 0.f;
+          if (i < a.n) {
+            // compile-time rhs index (a runtime one would move res[] to local memory)
+            if (NRHS == 1 || k == 0) scv = finish_row(0, i, s, wo.x, wo.y);
+            else scv = finish_row(NRHS - 1, i, s, wo.z, wo.w);
           }
-      }
-    }
-    const int64_t row0 = b * RPB + g * kRcRB;
-#pragma unroll
-    for (int q = 0; q < kRcRB; ++q) {
-      const int64_t i = row0 + q;
-      if (i >= a.n) break;
-      const float* rw = rows + (g * kRcRB + q) * SR;
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) {
-        const float wi = rw[D + 1 + 2 * k];
-        const float oi = rw[D + 2 + 2 * k];
-        float scale;
-        if (kAx) {
-          scale = oi;
-        } else {
-          const float s = dots[k][q];
-          if (has_old[k] && tg == 0)
-            res[k] += fabs(static_cast<double>(oi) * static_cast<double>(s) - static_cast<double>(wi));
-          scale = kUpd ? wi / s : 0.f;
-          if (kUpd && tg == 0) {
-            a.rhs[k].out[i] = scale;
-            if (!(s > 0.f) || !isfinite(scale)) flag |= LSF_ERR_NONFINITE;
-          }
+          s_sc[k][gg][qq] = scv;
         }
-        if (!kDt) {
+        __syncthreads();
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(scale, F[q][e], acc[k][e]);
+        for (int k = 0; k < NRHS; ++k) {
+          const float4 s0 = *reinterpret_cast<const float4*>(&s_sc[k][g][0]);
+          const float4 s1 = *reinterpret_cast<const float4*>(&s_sc[k][g][4]);
+          sc[k][0] = s0.x; sc[k][1] = s0.y; sc[k][2] = s0.z; sc[k][3] = s0.w;
+          sc[k][4] = s1.x; sc[k][5] = s1.y; sc[k][6] = s1.z; sc[k][7] = s1.w;
         }
       }
     }
-    park_rows(buf ^ 1);
-    __syncthreads();
+    if (!kDt) {
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+        for (int q = 0; q < kRcRB; ++q)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(sc[k][q], F[q][e], acc[k][e]);
+    }
+    if (!parked) {
+      // buffer buf ^ 1 was last read in the previous batch, before its barrier
+      // (with the cross-warp exchange the swap rides on the exchange's barriers)
+      park_rows(buf ^ 1);
+      __syncthreads();
+    }
   }
 
   // partials: group g writes its columns into s_part[g][k][col]
@@ -217,19 +268,24 @@ __global__ void __launch_bounds__(kRcThreads) recompute_kernel(const RecomputeAr
         if (col < ldr) s_part[static_cast<size_t>(g) * NRHS * ldr + k * ldr + col] = acc[k][e];
       }
   }
-  if (lane == 0)
+  // residual terms live in the threads that finished rows: per-warp sums, then
+  // all warps into slot 0 in order (the other slots zero)
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) s_res[warp][k] = (wg == 0) ? res[k] : 0.0;
+  for (int k = 0; k < NRHS; ++k) {
+    double r = res[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) s_res[warp][k] = r;
+  }
   if (flag) atomicOr(&s_flag, flag);
   __syncthreads();
-  // residual sums are per warp; fold each group's warps into slot g (in order)
   if (tid == 0) {
-    for (int gg = 0; gg < NG; ++gg)
-      for (int k = 0; k < NRHS; ++k) {
-        double r = 0.0;
-        for (int w = 0; w < GW; ++w) r += s_res[gg * GW + w][k];
-        s_res[gg][k] = r;
-      }
+    for (int k = 0; k < NRHS; ++k) {
+      double r = 0.0;
+      for (int w = 0; w < kRcWarps; ++w) r += s_res[w][k];
+      s_res[0][k] = r;
+      for (int w = 1; w < kRcWarps; ++w) s_res[w][k] = 0.0;
+    }
   }
   __syncthreads();
   if (kDt)

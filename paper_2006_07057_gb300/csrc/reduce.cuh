@@ -134,6 +134,17 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   m = M;
 }
 
+// Online log-sum-exp: (m, s) represents log(s e^m); adding one term y gives
+// (max(m, y), s e^(m - max) + e^(y - max)). One of the two exponentials is
+// e^0 = 1, so one ex2 per term suffices. m = -inf, s = 0 is the empty sum.
+__device__ __forceinline__ void lse_push(float& m, float& s, float y) {
+  if (y == -INFINITY) return;
+  const float d = y - m;  // +inf while the sum is empty
+  const float e = ex2_approx(-fabsf(d) * kLog2e);
+  s = (d > 0.f) ? fmaf(s, e, 1.f) : s + e;
+  m = fmaxf(m, y);
+}
+
 // As finish_pass for the log-domain passes: red holds [ngroups][NRHS][2][ldr]
 // (per-group maxima then sums per column); the r-vector written is
 // t_out[k] = m + log(s) (-inf where no mass). The same two fixed-order levels
