@@ -156,6 +156,50 @@ int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta,
 int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta,
                   float* shift, float* spread, void* stream);
 
+/*
+ * Arc-cosine positive features (Sec. 3.2, "Arc-cosine kernels", and the lemma
+ * in the appendix): the perturbed kernel k_s(x,y) + kappa, where
+ *   k_s(x,y) = int Theta_s(u.x) Theta_s(u.y) dN(0,I)(u),  Theta_s(w) = sqrt(2) max(0,w)^s,
+ * has the features phi(x,u) = (sigma^{d/2} sqrt(2) max(0,u.x)^s
+ * exp(-||u||^2 (1 - 1/sigma^2)/4), sqrt(kappa)) for u ~ N(0, sigma^2 I),
+ * sigma > 1. With r anchors the r constant entries only enter K through their
+ * sum, so they are merged into one last feature: r + 1 features per point,
+ *   L_ik = c_k + s log(u_k.x_i)  (u_k.x_i > 0; -inf, i.e. an exact zero, else),
+ *   L_ir = log sqrt(kappa),
+ * c_k = (d/2) log sigma + (1/2) log 2 - (1/2) log r - ||u_k||^2 (1 - 1/sigma^2)/4.
+ * The kernel has no bandwidth: Sinkhorn runs on K = xi zeta^T as it is, and eps
+ * (lsf_theta.eps of the solve) only scales the divergence, W = eps (a.log u + b.log v).
+ * The stored solve, the log-domain solve and the batched solver take these
+ * features unchanged (an lsf_theta with r + 1 features and the solve's eps).
+ * The recompute mode and lsf_gradient / lsf_anchor_gradient evaluate the
+ * Gaussian map and its derivatives; they must not be given arc-cosine
+ * features (the library cannot tell the maps apart from F).
+ */
+typedef struct {
+  const float* U;   /* r x d anchors (lsf_arccos_anchors)                          */
+  const float* c;   /* r log-constants c_k                                          */
+  int r;            /* anchors, >= 1                                                */
+  int ldr;          /* row stride: multiple of 4, >= r + 1, <= 1024                */
+  int d;            /* dimension, >= 1                                              */
+  int s;            /* exponent 0, 1 or 2 (max(0,w)^0 is taken as 0 for w <= 0)     */
+  double kappa;     /* perturbation > 0 (k >= kappa keeps every entry of K positive) */
+} lsf_arccos;
+
+/* U = sigma * Z (Z: r x d standard normal draws, device) and the constants c_k
+ * above. sigma > 1. Outputs U (r x d) and c (r), device. */
+int lsf_arccos_anchors(const float* Z, int r, int d, double sigma, float* U, float* c,
+                       void* stream);
+
+/* Stored shifted arc-cosine features: shift[i] = max_{k<=r} L_ik,
+ * F[i*ldr + k] = exp(L_ik - shift[i]) for k <= r, 0 beyond. Arguments, layout
+ * and the spread output as lsf_features (the spread ignores exact zeros). */
+int lsf_arccos_features(const float* X, int64_t n, const lsf_arccos* params,
+                        float* F, float* shift, float* spread, void* stream);
+
+/* Log form for LSF_MODE_LOG: L[i*ldr + k] = L_ik - shift[i], -inf beyond r. */
+int lsf_arccos_log_features(const float* X, int64_t n, const lsf_arccos* params,
+                            float* L, float* shift, float* spread, void* stream);
+
 /* ---------------------------------------------------------------- solver */
 
 /*

@@ -23,6 +23,9 @@ What it computes, in the paper's order and notation (Scetbon & Cuturi,
   reported residual is ||u o (K v) - a||_1 after the last v-half.
 * Eq. (6): W_hat = eps (a^T log u + b^T log v).
 * Eq. (2): debiased W_bar = W(a,b) - (W(a,a) + W(b,b))/2 with one shared theta.
+* Sec. 3.2 and its appendix lemma: the perturbed arc-cosine kernel k_s + kappa
+  with features (sigma^{d/2} sqrt(2) max(0, u.x)^s exp(-||u||^2 (1 - 1/sigma^2)/4),
+  sqrt(kappa)), u ~ N(0, sigma^2 I), sigma > 1.
 * Prop. 3.3 and the formula after it (Sec. 3.3): dW/dK = -eps u v^T at the
   optimum, chained through xi(X) with theta held fixed; the same chain taken
   through the anchors U (q held fixed) gives the gradient a learned feature map
@@ -63,6 +66,9 @@ __all__ = [
     "divergence",
     "gradient",
     "anchor_gradient",
+    "arccos_kernel",
+    "arccos_log_features",
+    "arccos_divergence",
     "deviation",
 ]
 
@@ -171,7 +177,8 @@ def lse(A: np.ndarray, axis: int) -> np.ndarray:
     """log sum exp along an axis, shifted by the maximum so nothing overflows."""
     mx = A.max(axis=axis, keepdims=True)
     mx = np.where(np.isfinite(mx), mx, 0.0)
-    out = np.log(np.exp(A - mx).sum(axis=axis, keepdims=True)) + mx
+    with np.errstate(divide="ignore"):  # an empty sum (all -inf) is log 0 = -inf
+        out = np.log(np.exp(A - mx).sum(axis=axis, keepdims=True)) + mx
     return np.squeeze(out, axis=axis)
 
 
@@ -435,6 +442,81 @@ def anchor_gradient(X, Y, theta: Theta, state: dict, debiased: bool = True) -> n
                       + _grad_anchors(P, U, L, t["logv"], lse(L + t["logu"][:, None], axis=0), q))
             g = g - 0.5 * g_self
     return g
+
+
+# --------------------------------------------------------------------------
+# Arc-cosine positive features (Sec. 3.2 "Arc-cosine kernels"; lemma in App. A)
+# --------------------------------------------------------------------------
+
+def arccos_kernel(X, Y, s: int) -> np.ndarray:
+    """k_s(x, y) = int Theta_s(u.x) Theta_s(u.y) dN(0, I)(u), Theta_s(w) = sqrt(2) max(0, w)^s.
+
+    Closed form for s = 0, 1, 2 (Cho and Saul's arc-cosine kernels, the source the
+    paper cites): k_s = ||x||^s ||y||^s J_s(angle) / pi with J_0 = pi - t,
+    J_1 = sin t + (pi - t) cos t, J_2 = 3 sin t cos t + (pi - t)(1 + 2 cos^2 t).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    nx = np.sqrt((X * X).sum(axis=1))
+    ny = np.sqrt((Y * Y).sum(axis=1))
+    cos = np.clip((X @ Y.T) / (nx[:, None] * ny[None, :]), -1.0, 1.0)
+    t = np.arccos(cos)
+    if s == 0:
+        J = np.pi - t
+    elif s == 1:
+        J = np.sin(t) + (np.pi - t) * cos
+    elif s == 2:
+        J = 3.0 * np.sin(t) * cos + (np.pi - t) * (1.0 + 2.0 * cos * cos)
+    else:
+        raise ValueError("closed form for s = 0, 1, 2 only")
+    return (nx[:, None] ** s) * (ny[None, :] ** s) * J / np.pi
+
+
+def arccos_log_features(P: np.ndarray, U: np.ndarray, s: int, sigma: float,
+                        kappa: float) -> np.ndarray:
+    """log phi_theta(p) for the perturbed arc-cosine kernel k_s + kappa.
+
+    Per anchor u_k ~ N(0, sigma^2 I) (sigma > 1) the lemma's map has two entries,
+    sigma^{d/2} sqrt(2) max(0, u.p)^s exp(-||u||^2 (1 - 1/sigma^2) / 4) and
+    sqrt(kappa); phi_theta scales both by r^{-1/2}. The r constant entries only
+    ever enter K through their sum kappa, so they are merged into one last
+    feature sqrt(kappa): r + 1 features. Entries with u.p <= 0 are 0 (log -inf;
+    max(0, w)^0 is taken as 0 for w <= 0). Returns n x (r + 1) in FP64.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    r, d = U.shape
+    unorm2 = (U * U).sum(axis=1)
+    const = (0.5 * d) * math.log(sigma) + 0.5 * math.log(2.0) - 0.5 * math.log(r) \
+        - 0.25 * unorm2 * (1.0 - 1.0 / sigma ** 2)
+    W = P @ U.T
+    out = np.full((P.shape[0], r + 1), -np.inf)
+    pos = W > 0
+    logw = np.log(np.where(pos, W, 1.0))  # only read where u.p > 0
+    out[:, :r] = np.where(pos, const[None, :] + s * logw, -np.inf)
+    out[:, r] = 0.5 * math.log(kappa)
+    return out
+
+
+def arccos_divergence(X, Y, a, b, U, s: int, sigma: float, kappa: float, eps: float = 1.0,
+                      iters: int = 100, debiased: bool = True, mode: str = "log") -> dict:
+    """Alg. 1 and Eq. (6)/(2) on K = xi zeta^T with arc-cosine features; eps scales W
+    (the kernel has no bandwidth: the cost is -eps log k)."""
+    Lx = arccos_log_features(X, U, s, sigma, kappa)
+    Ly = arccos_log_features(Y, U, s, sigma, kappa)
+    out = {}
+    sxy = solve(Lx, Ly, a, b, iters, mode)
+    out["xy"] = sxy
+    out["W_xy"] = dual_estimate(a, b, sxy["logu"], sxy["logv"], eps)
+    out["res_xy"] = sxy["residual"]
+    if debiased:
+        sxx = solve(Lx, Lx, a, a, iters, mode)
+        syy = solve(Ly, Ly, b, b, iters, mode)
+        out["W_xx"] = dual_estimate(a, a, sxx["logu"], sxx["logv"], eps)
+        out["W_yy"] = dual_estimate(b, b, syy["logu"], syy["logv"], eps)
+        out["res_xx"], out["res_yy"] = sxx["residual"], syy["residual"]
+        out["W_bar"] = out["W_xy"] - 0.5 * (out["W_xx"] + out["W_yy"])
+    return out
 
 
 def deviation(rot: float, rot_hat: float) -> float:

@@ -26,7 +26,7 @@ from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,  
                        LsfBatchInfo, LsfBatchProblem,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
-                       LsfTheta, check, header_symbols, lib)
+                       LsfArccos, LsfTheta, check, header_symbols, lib)
 
 MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG}
 
@@ -80,6 +80,24 @@ class Theta:
 
     def as_c(self) -> LsfTheta:
         return LsfTheta(_p(self.U), _p(self.c), self.r, self.ldr, self.d, float(self.eps))
+
+
+@dataclass
+class Arccos:
+    """Arc-cosine feature parameters: anchors U = sigma Z, constants c, exponent s, kappa."""
+
+    U: torch.Tensor
+    c: torch.Tensor
+    r: int
+    ldr: int
+    d: int
+    s: int
+    sigma: float
+    kappa: float
+
+    def as_c(self) -> LsfArccos:
+        return LsfArccos(_p(self.U), _p(self.c), self.r, self.ldr, self.d, int(self.s),
+                         float(self.kappa))
 
 
 @dataclass
@@ -188,6 +206,44 @@ def lsf_row_shift(X, theta: Theta, shift=None, spread=None, stream=None):
     check(lib().lsf_row_shift(_p(X), n, ctypes.byref(th), _p(shift), _p(spread),
                               _stream(stream)), "lsf_row_shift")
     return shift
+
+
+def lsf_arccos_anchors(Z, sigma: float, U=None, c=None, stream=None):
+    _f32(Z)
+    r, d = Z.shape
+    if U is None:
+        U = torch.empty(r, d, dtype=torch.float32, device=Z.device)
+    if c is None:
+        c = torch.empty(r, dtype=torch.float32, device=Z.device)
+    check(lib().lsf_arccos_anchors(_p(Z), r, d, float(sigma), _p(U), _p(c), _stream(stream)),
+          "lsf_arccos_anchors")
+    return U, c
+
+
+def lsf_arccos_features(X, params: Arccos, F=None, shift=None, spread=None, stream=None):
+    _f32(X)
+    n = X.shape[0]
+    if F is None:
+        F = torch.empty(n, params.ldr, dtype=torch.float32, device=X.device)
+    if shift is None:
+        shift = torch.empty(n, dtype=torch.float32, device=X.device)
+    pa = params.as_c()
+    check(lib().lsf_arccos_features(_p(X), n, ctypes.byref(pa), _p(F), _p(shift), _p(spread),
+                                    _stream(stream)), "lsf_arccos_features")
+    return F, shift
+
+
+def lsf_arccos_log_features(X, params: Arccos, L=None, shift=None, spread=None, stream=None):
+    _f32(X)
+    n = X.shape[0]
+    if L is None:
+        L = torch.empty(n, params.ldr, dtype=torch.float32, device=X.device)
+    if shift is None:
+        shift = torch.empty(n, dtype=torch.float32, device=X.device)
+    pa = params.as_c()
+    check(lib().lsf_arccos_log_features(_p(X), n, ctypes.byref(pa), _p(L), _p(shift), _p(spread),
+                                        _stream(stream)), "lsf_arccos_log_features")
+    return L, shift
 
 
 def lsf_workspace_bytes(ldr: int) -> int:
@@ -346,9 +402,16 @@ class SinkhornProblem:
     """
 
     def __init__(self, X, Y, a, b, Z, eps: float, mode: str = "stored", ldr: int | None = None,
-                 theta: Theta | None = None, stream=None, scalings: bool = True):
+                 theta: Theta | None = None, stream=None, scalings: bool = True,
+                 kernel: str = "gaussian", s: int = 1, sigma: float = 1.5, kappa: float = 0.1):
         if mode not in MODES and mode != "auto":
             raise ValueError(f"mode must be one of {sorted(MODES) + ['auto']}")
+        if kernel not in ("gaussian", "arccos"):
+            raise ValueError("kernel must be 'gaussian' or 'arccos'")
+        if kernel == "arccos" and mode == "recompute":
+            raise ValueError("the recompute mode evaluates the Gaussian map only")
+        self.kernel = kernel
+        self.arccos = None
         for t in (X, Y, a, b, Z):
             _f32(t)
         self.X, self.Y, self.a, self.b, self.Z = X, Y, a, b, Z
@@ -359,12 +422,19 @@ class SinkhornProblem:
         n, d = X.shape
         m = Y.shape[0]
         r = Z.shape[0]
-        if theta is None:
+        if kernel == "arccos":
+            # r anchors give r + 1 features (the merged constant feature sqrt(kappa))
+            ldr = ldr if ldr is not None else ldr_for(r + 1)
+            U, c = lsf_arccos_anchors(Z, sigma, stream=stream)
+            self.arccos = Arccos(U, c, r, ldr, d, s, float(sigma), float(kappa))
+            # the solver reads only ldr and eps; no Gaussian kernel may see these anchors
+            theta = Theta(None, None, r + 1, ldr, d, self.eps, 0.0, 0.0, float(sigma))
+        elif theta is None:
             R = float(lsf_radius(X, Y, stream=stream).item())
-            q, sigma = lsf_gaussian_params(R, eps, d)
+            q, sig = lsf_gaussian_params(R, eps, d)
             ldr = ldr if ldr is not None else ldr_for(r)
-            U, c = lsf_anchors(Z, q, sigma, eps, stream=stream)
-            theta = Theta(U, c, r, ldr, d, self.eps, R, q, sigma)
+            U, c = lsf_anchors(Z, q, sig, eps, stream=stream)
+            theta = Theta(U, c, r, ldr, d, self.eps, R, q, sig)
         self.theta = theta
         ldr = theta.ldr
         self.spread = torch.zeros(1, dtype=torch.float32, device=dev)
@@ -385,6 +455,13 @@ class SinkhornProblem:
 
     def _build_features(self):
         X, Y, th, st = self.X, self.Y, self.theta, self.stream
+        if self.arccos is not None:
+            build = lsf_arccos_features if self.mode == "stored" else lsf_arccos_log_features
+            Fx, sx = build(X, self.arccos, spread=self.spread, stream=st)
+            Fy, sy = build(Y, self.arccos, spread=self.spread, stream=st)
+            self.x = Cloud(X, Fx, sx, self.a)
+            self.y = Cloud(Y, Fy, sy, self.b)
+            return
         if self.mode == "stored":
             Fx, sx = lsf_features(X, th, spread=self.spread, stream=st)
             Fy, sy = lsf_features(Y, th, spread=self.spread, stream=st)
@@ -461,6 +538,8 @@ class SinkhornProblem:
             raise ValueError("the debiased gradient needs a debiased run")
         if self.mode == "recompute":
             raise NotImplementedError("the adjoint reads stored features")
+        if self.arccos is not None:
+            raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
         dev = self.X.device
         gX = torch.empty_like(self.X)
         gY = torch.empty_like(self.Y)
@@ -483,6 +562,8 @@ class SinkhornProblem:
             raise ValueError("the debiased gradient needs a debiased run")
         if self.mode == "recompute":
             raise NotImplementedError("the adjoint reads stored features")
+        if self.arccos is not None:
+            raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
         if wrt not in ("U", "Z"):
             raise ValueError("wrt must be 'U' or 'Z'")
         th = self.theta

@@ -46,6 +46,11 @@ class LsfTheta(ctypes.Structure):
                 ("eps", c_double)]
 
 
+class LsfArccos(ctypes.Structure):
+    _fields_ = [("U", c_void_p), ("c", c_void_p), ("r", c_int), ("ldr", c_int), ("d", c_int),
+                ("s", c_int), ("kappa", c_double)]
+
+
 class LsfCloud(ctypes.Structure):
     _fields_ = [("X", c_void_p), ("F", c_void_p), ("shift", c_void_p), ("w", c_void_p),
                 ("n", c_int64)]
@@ -83,6 +88,11 @@ _SIGNATURES = {
     "lsf_radius": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_void_p]),
     "lsf_anchors": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
                             c_void_p, c_void_p]),
+    "lsf_arccos_anchors": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, c_void_p]),
+    "lsf_arccos_features": (c_int, [c_void_p, c_int64, _P(LsfArccos), c_void_p, c_void_p, c_void_p,
+                                    c_void_p]),
+    "lsf_arccos_log_features": (c_int, [c_void_p, c_int64, _P(LsfArccos), c_void_p, c_void_p,
+                                        c_void_p, c_void_p]),
     "lsf_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
                              c_void_p]),
     "lsf_row_shift": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p]),

@@ -45,20 +45,55 @@ __global__ void anchors_kernel(const float* __restrict__ Z, int r, int d, double
                             nrm / (eps * q));
 }
 
+// Which feature map a kernel evaluates, with its constants. Gaussian (Lemma 1):
+// L_ik = c_k - (2/eps) ||x_i - u_k||^2 for k < r. Arc-cosine (Sec. 3.2 lemma):
+// L_ik = c_k + s log(u_k . x_i) for u_k . x_i > 0 (else -inf, an exact zero
+// feature) and k < r, and L_ir = log sqrt(kappa) (the merged constant feature).
+// rf is the number of feature columns: r, or r + 1 for the arc-cosine map.
+struct MapArgs {
+  int r;
+  int rf;
+  float two_over_eps;  // Gaussian
+  float s;             // arc-cosine exponent
+  float lk;            // arc-cosine log sqrt(kappa)
+};
+enum FeatureMap : int { kMapGauss = 0, kMapArccos = 1 };
+
+// accumulate one coordinate of the distance (Gaussian) or projection (arc-cosine)
+template <int MAP>
+__device__ __forceinline__ float map_acc(float x, float u, float acc) {
+  if (MAP == kMapGauss) {
+    const float t = x - u;
+    return fmaf(t, t, acc);
+  }
+  return fmaf(x, u, acc);
+}
+
+// the log-feature of column k from its accumulated distance / projection
+template <int MAP>
+__device__ __forceinline__ float map_log(float acc, float ck, int k, const MapArgs& m) {
+  if (MAP == kMapGauss) return ck - m.two_over_eps * acc;
+  if (k == m.r) return m.lk;
+  if (!(acc > 0.f)) return -INFINITY;
+  return m.s == 0.f ? ck : ck + m.s * logf(acc);
+}
+
 // Warp-per-row feature kernel. Lane l owns columns 4l + 128j + e (j < C, e < 4).
 // U is staged transposed in shared memory (d-chunk x ldr) so that lanes read
 // consecutive columns. KIND 0 computes only the row shifts, KIND 1 stores
 // F = exp(L - shift) (padding 0), KIND 2 stores the log form L - shift
-// (padding -inf) for the log-domain passes.
-template <int C, int KIND>
+// (padding -inf) for the log-domain passes. The spread is max - min over the
+// finite log-features of a row (an exact zero feature has no range to lose).
+template <int C, int KIND, int MAP>
 __global__ void __launch_bounds__(kFeatWarps * 32)
     features_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ U,
-                    const float* __restrict__ c, int r, int ldr, float two_over_eps,
+                    const float* __restrict__ c, int ldr, const MapArgs m,
                     float* __restrict__ F, float* __restrict__ shift, unsigned* spread_key) {
   extern __shared__ __align__(16) float sU[];  // [min(d, kFeatDChunk)][ldr] then c[ldr]
   float* sc = sU + static_cast<size_t>(min(d, kFeatDChunk)) * ldr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (d + kFeatDChunk - 1) / kFeatDChunk;
+  const int r = m.r;
 
   for (int k = threadIdx.x; k < ldr; k += blockDim.x) sc[k] = (k < r) ? c[k] : 0.f;
   auto load_chunk = [&](int ch) {
@@ -104,11 +139,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
             const int col = 4 * lane + 128 * j;
             if (col < ldr) {
               const float4 u4 = *reinterpret_cast<const float4*>(urow + col);
-              float t;
-              t = xv - u4.x; acc[q][j][0] = fmaf(t, t, acc[q][j][0]);
-              t = xv - u4.y; acc[q][j][1] = fmaf(t, t, acc[q][j][1]);
-              t = xv - u4.z; acc[q][j][2] = fmaf(t, t, acc[q][j][2]);
-              t = xv - u4.w; acc[q][j][3] = fmaf(t, t, acc[q][j][3]);
+              acc[q][j][0] = map_acc<MAP>(xv, u4.x, acc[q][j][0]);
+              acc[q][j][1] = map_acc<MAP>(xv, u4.y, acc[q][j][1]);
+              acc[q][j][2] = map_acc<MAP>(xv, u4.z, acc[q][j][2]);
+              acc[q][j][3] = map_acc<MAP>(xv, u4.w, acc[q][j][3]);
             }
           }
         }
@@ -125,11 +159,11 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int k = 4 * lane + 128 * j + e;
-          if (k < r) {
-            const float L = sc[k] - two_over_eps * acc[q][j][e];
+          if (k < m.rf) {
+            const float L = map_log<MAP>(acc[q][j][e], sc[k < r ? k : 0], k, m);
             acc[q][j][e] = L;
             mx = fmaxf(mx, L);
-            mn = fminf(mn, L);
+            if (L != -INFINITY) mn = fminf(mn, L);
           }
         }
       }
@@ -144,10 +178,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
           const int col = 4 * lane + 128 * j;
           if (col < ldr) {
             float4 o;
-            o.x = (col + 0 < r) ? expf(acc[q][j][0] - mx) : 0.f;
-            o.y = (col + 1 < r) ? expf(acc[q][j][1] - mx) : 0.f;
-            o.z = (col + 2 < r) ? expf(acc[q][j][2] - mx) : 0.f;
-            o.w = (col + 3 < r) ? expf(acc[q][j][3] - mx) : 0.f;
+            o.x = (col + 0 < m.rf) ? expf(acc[q][j][0] - mx) : 0.f;
+            o.y = (col + 1 < m.rf) ? expf(acc[q][j][1] - mx) : 0.f;
+            o.z = (col + 2 < m.rf) ? expf(acc[q][j][2] - mx) : 0.f;
+            o.w = (col + 3 < m.rf) ? expf(acc[q][j][3] - mx) : 0.f;
             *reinterpret_cast<float4*>(Fi + col) = o;
           }
         }
@@ -158,10 +192,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
           const int col = 4 * lane + 128 * j;
           if (col < ldr) {
             float4 o;
-            o.x = (col + 0 < r) ? acc[q][j][0] - mx : -INFINITY;
-            o.y = (col + 1 < r) ? acc[q][j][1] - mx : -INFINITY;
-            o.z = (col + 2 < r) ? acc[q][j][2] - mx : -INFINITY;
-            o.w = (col + 3 < r) ? acc[q][j][3] - mx : -INFINITY;
+            o.x = (col + 0 < m.rf) ? acc[q][j][0] - mx : -INFINITY;
+            o.y = (col + 1 < m.rf) ? acc[q][j][1] - mx : -INFINITY;
+            o.z = (col + 2 < m.rf) ? acc[q][j][2] - mx : -INFINITY;
+            o.w = (col + 3 < m.rf) ? acc[q][j][3] - mx : -INFINITY;
             *reinterpret_cast<float4*>(Fi + col) = o;
           }
         }
@@ -172,7 +206,6 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
   if (spread_key && lane == 0 && local_spread > 0.f)
     atomicMax(spread_key, __float_as_uint(local_spread));
 }
-
 
 // ---------------------------------------------------------------- large d
 //
@@ -186,10 +219,12 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
 // row into its shifted form (exp or log) and records the spread.
 constexpr int kTM = 128, kTN = 128, kTK = 16;
 
+template <int MAP>
 __global__ void __launch_bounds__(256)
     features_tile_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ U,
-                         const float* __restrict__ c, int r, int ldr, float two_over_eps,
+                         const float* __restrict__ c, int ldr, const MapArgs m,
                          float* __restrict__ L, unsigned* __restrict__ row_key) {
+  const int r = m.r;
   // rows padded by 4 floats: the transposing stores hit 2 banks at most
   __shared__ __align__(16) float sX[kTK][kTM + 4];
   __shared__ __align__(16) float sU[kTK][kTN + 4];
@@ -227,8 +262,7 @@ __global__ void __launch_bounds__(256)
       for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          const float t = xv[a] - uv[b];
-          acc[a][b] = fmaf(t, t, acc[a][b]);
+          acc[a][b] = map_acc<MAP>(xv[a], uv[b], acc[a][b]);
         }
     }
     __syncthreads();
@@ -248,8 +282,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int k = k0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + b - 4);
-      Lv[b] = cv[b] - two_over_eps * acc[a][b];
-      if (k < r) mx = fmaxf(mx, Lv[b]);
+      Lv[b] = map_log<MAP>(acc[a][b], cv[b], k, m);
+      if (k < m.rf) mx = fmaxf(mx, Lv[b]);
     }
     // the 16 threads of a half-warp hold the same rows
 #pragma unroll
@@ -269,7 +303,7 @@ __global__ void __launch_bounds__(256)
 // padding -inf), and the row's spread max - min.
 template <int KIND>
 __global__ void __launch_bounds__(256)
-    features_shift_kernel(int64_t n, int r, int ldr, float* __restrict__ F, float* shift,
+    features_shift_kernel(int64_t n, int rf, int ldr, float* __restrict__ F, float* shift,
                           unsigned* spread_key) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
@@ -285,8 +319,8 @@ __global__ void __launch_bounds__(256)
       float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (col + q < r) {
-          mn = fminf(mn, e[q]);
+        if (col + q < rf) {
+          if (e[q] != -INFINITY) mn = fminf(mn, e[q]);
           e[q] = KIND == 1 ? expf(e[q] - mx) : e[q] - mx;
         } else {
           e[q] = KIND == 1 ? 0.f : -INFINITY;
@@ -302,60 +336,56 @@ __global__ void __launch_bounds__(256)
     atomicMax(spread_key, __float_as_uint(local_spread));
 }
 
-template <int KIND>
-int launch_features_tiled(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
-                          unsigned* skey, float toe, cudaStream_t st) {
+template <int KIND, int MAP>
+int launch_features_tiled(const float* X, int64_t n, int d, const float* U, const float* c, int ldr,
+                          const MapArgs& m, float* F, float* shift, unsigned* skey, cudaStream_t st) {
   if (cudaMemsetAsync(shift, 0, sizeof(float) * static_cast<size_t>(n), st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "features: memset failed");
   {
-    LaunchScope ls(st, LSF_KERNEL_FEATURES, 4.0 * n * th->d + 4.0 * n * th->ldr);
-    dim3 grid(static_cast<unsigned>((n + kTM - 1) / kTM), static_cast<unsigned>((th->ldr + kTN - 1) / kTN));
-    features_tile_kernel<<<grid, 256, 0, st>>>(X, n, th->d, th->U, th->c, th->r, th->ldr, toe, F,
-                                               reinterpret_cast<unsigned*>(shift));
+    LaunchScope ls(st, LSF_KERNEL_FEATURES, 4.0 * n * d + 4.0 * n * ldr);
+    dim3 grid(static_cast<unsigned>((n + kTM - 1) / kTM), static_cast<unsigned>((ldr + kTN - 1) / kTN));
+    features_tile_kernel<MAP><<<grid, 256, 0, st>>>(X, n, d, U, c, ldr, m, F,
+                                                    reinterpret_cast<unsigned*>(shift));
     int rc = check_launch("features_tile_kernel");
     if (rc != LSF_OK) return rc;
   }
-  LaunchScope ls(st, LSF_KERNEL_FEATURES, 8.0 * n * th->ldr + 4.0 * n);
+  LaunchScope ls(st, LSF_KERNEL_FEATURES, 8.0 * n * ldr + 4.0 * n);
   int64_t grid = (n + 7) / 8;
   const int64_t cap = static_cast<int64_t>(device_info().sms) * 8;
   if (grid > cap) grid = cap;
-  features_shift_kernel<KIND><<<static_cast<unsigned>(grid), 256, 0, st>>>(n, th->r, th->ldr, F, shift, skey);
+  features_shift_kernel<KIND><<<static_cast<unsigned>(grid), 256, 0, st>>>(n, m.rf, ldr, F, shift, skey);
   return check_launch("features_shift_kernel");
 }
 
-template <int KIND>
-int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
-                    float* spread, cudaStream_t st) {
+// Shared front end of the feature entry points (both maps, all three kinds).
+template <int KIND, int MAP>
+int launch_map(const float* X, int64_t n, int d, const float* U, const float* c, int ldr,
+               const MapArgs& m, float* F, float* shift, float* spread, cudaStream_t st) {
   constexpr bool STORE = KIND != 0;
-  if (!X || !th || !shift || (STORE && !F)) return fail(LSF_ERR_ARG, "features: NULL argument");
-  if (!th->U || !th->c) return fail(LSF_ERR_ARG, "features: theta has NULL U or c");
+  if (!X || !shift || (STORE && !F)) return fail(LSF_ERR_ARG, "features: NULL argument");
+  if (!U || !c) return fail(LSF_ERR_ARG, "features: NULL anchors or constants");
   if (n < 1) return fail(LSF_ERR_ARG, "features: n must be >= 1");
-  if (th->d < 1 || th->r < 1 || th->r > th->ldr)
-    return fail(LSF_ERR_ARG, "features: need d >= 1 and 1 <= r <= ldr");
-  if (th->ldr % 4 != 0 || th->ldr > 1024)
+  if (d < 1 || m.r < 1 || m.rf > ldr) return fail(LSF_ERR_ARG, "features: need d >= 1, r >= 1 and room in ldr");
+  if (ldr % 4 != 0 || ldr > 1024)
     return fail(LSF_ERR_UNSUPPORTED, "features: ldr must be a multiple of 4, <= 1024");
-  if (!(th->eps > 0.0)) return fail(LSF_ERR_ARG, "features: eps must be > 0");
   if (STORE && reinterpret_cast<uintptr_t>(F) % 16 != 0)
     return fail(LSF_ERR_ARG, "features: F must be 16-byte aligned");
-  const int ldr = th->ldr;
+  unsigned* skey = reinterpret_cast<unsigned*>(spread);
+  if (STORE && d > kFeatDChunk) return launch_features_tiled<KIND, MAP>(X, n, d, U, c, ldr, m, F, shift, skey, st);
   const int C = (ldr + 127) / 128;
-  const int dchunk = th->d < kFeatDChunk ? th->d : kFeatDChunk;
+  const int dchunk = d < kFeatDChunk ? d : kFeatDChunk;
   const size_t smem = sizeof(float) * (static_cast<size_t>(dchunk) * ldr + ldr);
   const int64_t rows_per_cta = kFeatWarps * kFeatRowsPerWarp;
   int64_t grid = (n + rows_per_cta - 1) / rows_per_cta;
   const int64_t cap = static_cast<int64_t>(device_info().sms) * 8;
   if (grid > cap) grid = cap;
-  const float toe = static_cast<float>(2.0 / th->eps);
-  unsigned* skey = reinterpret_cast<unsigned*>(spread);
-  if (STORE && th->d > kFeatDChunk) return launch_features_tiled<KIND>(X, n, th, F, shift, skey, toe, st);
-  double bytes = 4.0 * n * th->d + 4.0 * n + (STORE ? 4.0 * n * ldr : 0.0);
+  double bytes = 4.0 * n * d + 4.0 * n + (STORE ? 4.0 * n * ldr : 0.0);
   LaunchScope ls(st, LSF_KERNEL_FEATURES, bytes);
-#define LSF_FEAT_CASE(CC)                                                                  \
-  case CC: {                                                                               \
-    auto kern = features_kernel<CC, KIND>;                                                \
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-    kern<<<(unsigned)grid, kFeatWarps * 32, smem, st>>>(X, n, th->d, th->U, th->c, th->r,  \
-                                                        ldr, toe, F, shift, skey);         \
+#define LSF_FEAT_CASE(CC)                                                                   \
+  case CC: {                                                                                \
+    auto kern = features_kernel<CC, KIND, MAP>;                                            \
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    kern<<<(unsigned)grid, kFeatWarps * 32, smem, st>>>(X, n, d, U, c, ldr, m, F, shift, skey); \
   } break;
   switch (C <= 1 ? 1 : C <= 2 ? 2 : C <= 4 ? 4 : 8) {
     LSF_FEAT_CASE(1)
@@ -365,6 +395,48 @@ int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, fl
   }
 #undef LSF_FEAT_CASE
   return check_launch("features_kernel");
+}
+
+template <int KIND>
+int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
+                    float* spread, cudaStream_t st) {
+  if (!th) return fail(LSF_ERR_ARG, "features: NULL theta");
+  if (th->r > th->ldr) return fail(LSF_ERR_ARG, "features: need r <= ldr");
+  if (!(th->eps > 0.0)) return fail(LSF_ERR_ARG, "features: eps must be > 0");
+  MapArgs m{};
+  m.r = th->r;
+  m.rf = th->r;
+  m.two_over_eps = static_cast<float>(2.0 / th->eps);
+  return launch_map<KIND, kMapGauss>(X, n, th->d, th->U, th->c, th->ldr, m, F, shift, spread, st);
+}
+
+template <int KIND>
+int launch_arccos(const float* X, int64_t n, const lsf_arccos* th, float* F, float* shift,
+                  float* spread, cudaStream_t st) {
+  if (!th) return fail(LSF_ERR_ARG, "arc-cosine features: NULL parameters");
+  if (th->s < 0 || th->s > 2) return fail(LSF_ERR_UNSUPPORTED, "arc-cosine features: s must be 0, 1 or 2");
+  if (!(th->kappa > 0.0)) return fail(LSF_ERR_ARG, "arc-cosine features: kappa must be > 0");
+  if (th->r + 1 > th->ldr) return fail(LSF_ERR_ARG, "arc-cosine features: need r + 1 <= ldr");
+  MapArgs m{};
+  m.r = th->r;
+  m.rf = th->r + 1;
+  m.s = static_cast<float>(th->s);
+  m.lk = static_cast<float>(0.5 * log(th->kappa));
+  return launch_map<KIND, kMapArccos>(X, n, th->d, th->U, th->c, th->ldr, m, F, shift, spread, st);
+}
+
+__global__ void arccos_anchors_kernel(const float* __restrict__ Z, int r, int d, double sigma,
+                                      float* __restrict__ U, float* __restrict__ c) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= r) return;
+  double nrm = 0.0;
+  for (int j = 0; j < d; ++j) {
+    const float u = static_cast<float>(sigma * static_cast<double>(Z[static_cast<int64_t>(k) * d + j]));
+    U[static_cast<int64_t>(k) * d + j] = u;
+    nrm += static_cast<double>(u) * u;
+  }
+  c[k] = static_cast<float>(0.5 * d * log(sigma) + 0.5 * log(2.0) - 0.5 * log(static_cast<double>(r)) -
+                            0.25 * nrm * (1.0 - 1.0 / (sigma * sigma)));
 }
 
 }  // namespace
@@ -418,6 +490,26 @@ int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta, float* L
 int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta, float* shift,
                   float* spread, void* stream) {
   return launch_features<0>(X, n, theta, nullptr, shift, spread, as_stream(stream));
+}
+
+int lsf_arccos_anchors(const float* Z, int r, int d, double sigma, float* U, float* c, void* stream) {
+  if (!Z || !U || !c) return fail(LSF_ERR_ARG, "lsf_arccos_anchors: NULL argument");
+  if (r < 1 || d < 1) return fail(LSF_ERR_ARG, "lsf_arccos_anchors: need r, d >= 1");
+  if (!(sigma > 1.0)) return fail(LSF_ERR_ARG, "lsf_arccos_anchors: sigma must be > 1");
+  cudaStream_t st = as_stream(stream);
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * r * d + 4.0 * r);
+  arccos_anchors_kernel<<<(r + 127) / 128, 128, 0, st>>>(Z, r, d, sigma, U, c);
+  return check_launch("arccos_anchors_kernel");
+}
+
+int lsf_arccos_features(const float* X, int64_t n, const lsf_arccos* th, float* F, float* shift,
+                        float* spread, void* stream) {
+  return launch_arccos<1>(X, n, th, F, shift, spread, as_stream(stream));
+}
+
+int lsf_arccos_log_features(const float* X, int64_t n, const lsf_arccos* th, float* L, float* shift,
+                            float* spread, void* stream) {
+  return launch_arccos<2>(X, n, th, L, shift, spread, as_stream(stream));
 }
 
 }  // extern "C"

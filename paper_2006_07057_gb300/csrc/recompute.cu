@@ -12,13 +12,15 @@
 //
 // Layout: 256 threads; a row group of GW warps covers a row, each thread holding
 // four consecutive feature columns (their A_k and W_kd stay in registers for the
-// whole launch). A batch gives every group 8 rows; the rows' records (x, B,
-// weights, previous scalings; float4-packed) for the next batch are loaded into
-// registers while the current batch computes, then parked in the other shared
-// buffer. A warp folds its 8 row products with the multi-row butterfly (9
-// shuffles); one thread per row then sums the group's warps in a fixed order,
-// forms the new scaling (division, residual term, status) and shares it through
-// shared memory, so the division and the residual are done once per row.
+// whole launch). A batch gives every group 8 rows. A warp folds its 8 row
+// products with the multi-row butterfly (9 shuffles) and writes them to shared
+// memory; after one barrier every warp of the group sums the group's partials
+// for the 8 rows in the same fixed order and forms the new scalings itself (the
+// first warp of the group also writes them, with the residual terms and the
+// status), so no warp waits for another to finish a row. One barrier per batch
+// suffices: the partials are double-buffered, and the rows' records (x, B,
+// weights, previous scalings; float4-packed) go through a three-deep ring,
+// loaded two batches ahead and parked after the barrier.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,9 +52,8 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   constexpr int TPG = GW * 32;              // threads per group
   constexpr int XV = RowPack<D>::kXV;
   constexpr int SV = RowPack<D>::kSV;
-  __shared__ __align__(16) float4 s_rows[2][RPB * SV];
-  __shared__ float s_red[NRHS][kRcRB][kRcWarps];     // per-warp partial row products
-  __shared__ __align__(16) float s_sc[NRHS][NG][kRcRB];  // the rows' new scalings
+  __shared__ __align__(16) float4 s_rows[3][RPB * SV];
+  __shared__ __align__(16) float s_red[2][NRHS][kRcRB][kRcWarps];  // per-warp partial row products
   __shared__ double s_res[kRcWarps][2];
   __shared__ int s_flag, s_last;
   extern __shared__ __align__(16) float s_part[];  // [NG][NRHS * ldr] at the end
@@ -146,13 +147,16 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     return sc;
   };
 
-  int buf = 0;
+  // prime the ring with the first two batches
   load_rows(blockIdx.x);
   park_rows(0);
+  load_rows(static_cast<int64_t>(blockIdx.x) + gridDim.x);
+  park_rows(1);
   __syncthreads();
-  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
-    load_rows(b + gridDim.x);  // in flight while this batch computes
-    const float4* rows = s_rows[buf];
+  int it = 0;
+  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+    load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight while this batch computes
+    const float4* rows = s_rows[it % 3];
     const int64_t row0 = b * RPB;
     float F[kRcRB][4];
     float dots[NRHS][kRcRB];
@@ -177,84 +181,80 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
         dots[k][q] = fmaf(F[q][0], t[k][0], fmaf(F[q][1], t[k][1], fmaf(F[q][2], t[k][2], F[q][3] * t[k][3])));
     }
     float sc[NRHS][kRcRB];
-    bool parked = false;
+    const int q = lane >> 2;
+    const bool lead = (lane & 3) == 0;
     if (kAx) {
 #pragma unroll
-      for (int q = 0; q < kRcRB; ++q) {
-        const float4 wo = rows[(g * kRcRB + q) * SV + XV];
-        sc[0][q] = wo.y;
-        if (NRHS > 1) sc[NRHS - 1][q] = wo.w;
+      for (int qq = 0; qq < kRcRB; ++qq) {
+        const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
+        sc[0][qq] = wo.y;
+        if (NRHS > 1) sc[NRHS - 1][qq] = wo.w;
       }
-    } else {
-      // warp partials of the 8 rows: lanes 4q .. 4q + 3 hold row q
+      __syncthreads();
+    } else if (GW == 1) {
+      // warp partials of the 8 rows: lanes 4q .. 4q + 3 hold row q; a group is one
+      // warp, so its quad leaders finish the rows
       float v[NRHS];
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
-      const int q = lane >> 2;
-      const bool lead = (lane & 3) == 0;
-      if (GW == 1) {
-        // a group is one warp: the quad leader of row q finishes it
-        const int64_t i = row0 + g * kRcRB + q;
-        const float4 wo = rows[(g * kRcRB + q) * SV + XV];
-        float mine[NRHS];
+      const int64_t i = row0 + g * kRcRB + q;
+      const float4 wo = rows[(g * kRcRB + q) * SV + XV];
+      float mine[NRHS];
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-          mine[k] = 0.f;
-          if (lead && i < a.n)
-            mine[k] = finish_row(k, i, v[k], k == 0 ? wo.x : wo.z, k == 0 ? wo.y : wo.w);
-        }
+      for (int k = 0; k < NRHS; ++k) {
+        mine[k] = 0.f;
+        if (lead && i < a.n) mine[k] = finish_row(k, i, v[k], k == 0 ? wo.x : wo.z, k == 0 ? wo.y : wo.w);
+      }
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k)
+      for (int k = 0; k < NRHS; ++k)
 #pragma unroll
-          for (int qq = 0; qq < kRcRB; ++qq) sc[k][qq] = __shfl_sync(0xffffffffu, mine[k], qq << 2);
-      } else {
-        if (lead)
+        for (int qq = 0; qq < kRcRB; ++qq) sc[k][qq] = __shfl_sync(0xffffffffu, mine[k], qq << 2);
+      __syncthreads();
+    } else {
+      float v[NRHS];
 #pragma unroll
-          for (int k = 0; k < NRHS; ++k) s_red[k][q][warp] = v[k];
-        __syncthreads();
-        park_rows(buf ^ 1);
-        parked = true;
-        // one thread per (rhs, group, row): warps of the group in a fixed order
-        if (tid < NRHS * NG * kRcRB) {
-          const int k = tid / (NG * kRcRB);
-          const int gg = (tid / kRcRB) % NG;
-          const int qq = tid % kRcRB;
-          float s = 0.f;
+      for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
+      if (lead)
 #pragma unroll
-          for (int w = 0; w < GW; ++w) s += s_red[k][qq][gg * GW + w];
-          const int64_t i = row0 + gg * kRcRB + qq;
-          const float4 wo = rows[(gg * kRcRB + qq) * SV + XV];
-          float scv = 0.f;
-          if (i < a.n) {
-            // compile-time rhs index (a runtime one would move res[] to local memory)
-            if (NRHS == 1 || k == 0) scv = finish_row(0, i, s, wo.x, wo.y);
-            else scv = finish_row(NRHS - 1, i, s, wo.z, wo.w);
+        for (int k = 0; k < NRHS; ++k) s_red[it & 1][k][q][warp] = v[k];
+      __syncthreads();
+      // every warp of the group: lane (k, qq) sums the group's warps for row qq, in order
+      const int kq = lane >> 3, qq = lane & 7;
+      float scl = 0.f;
+      if (kq < NRHS) {
+        const float* pr = &s_red[it & 1][kq][qq][g * GW];
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < GW; ++w) s += pr[w];
+        const int64_t i = row0 + g * kRcRB + qq;
+        if (i < a.n) {
+          const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
+          const float wi = (NRHS == 1 || kq == 0) ? wo.x : wo.z;
+          const float oi = (NRHS == 1 || kq == 0) ? wo.y : wo.w;
+          if (warp == g * GW) {
+            // the group's first warp records the row (compile-time rhs index)
+            if (NRHS == 1 || kq == 0) scl = finish_row(0, i, s, wi, oi);
+            else scl = finish_row(NRHS - 1, i, s, wi, oi);
+          } else if (kUpd) {
+            scl = wi * __frcp_rn(s);
           }
-          s_sc[k][gg][qq] = scv;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-          const float4 s0 = *reinterpret_cast<const float4*>(&s_sc[k][g][0]);
-          const float4 s1 = *reinterpret_cast<const float4*>(&s_sc[k][g][4]);
-          sc[k][0] = s0.x; sc[k][1] = s0.y; sc[k][2] = s0.z; sc[k][3] = s0.w;
-          sc[k][4] = s1.x; sc[k][5] = s1.y; sc[k][6] = s1.z; sc[k][7] = s1.w;
         }
       }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+        for (int r8 = 0; r8 < kRcRB; ++r8) sc[k][r8] = __shfl_sync(0xffffffffu, scl, k * 8 + r8);
     }
+    // after this batch's barrier: park the batch two ahead (its ring slot was last
+    // read in the previous batch, before that barrier)
+    park_rows((it + 2) % 3);
     if (!kDt) {
 #pragma unroll
       for (int k = 0; k < NRHS; ++k)
 #pragma unroll
-        for (int q = 0; q < kRcRB; ++q)
+        for (int qq = 0; qq < kRcRB; ++qq)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(sc[k][q], F[q][e], acc[k][e]);
-    }
-    if (!parked) {
-      // buffer buf ^ 1 was last read in the previous batch, before its barrier
-      // (with the cross-warp exchange the swap rides on the exchange's barriers)
-      park_rows(buf ^ 1);
-      __syncthreads();
+          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(sc[k][qq], F[qq][e], acc[k][e]);
     }
   }
 

@@ -386,3 +386,72 @@ def test_joint_translation_gradient_is_the_anchor_weight_term():
             return o.divergence(X + s * e, Y + s * e, a, b, theta=t, iters=iters)["W_bar"]
         fd = (W(1.0) - W(-1.0)) / (2 * h)
         assert abs(total[c] - fd) < 1e-6 * max(1.0, abs(fd)), (c, total[c], fd)
+
+
+# ---------------------------------------------------------------- arc-cosine features
+
+@pytest.mark.parametrize("s", [0, 1, 2])
+def test_arccos_closed_form_matches_monte_carlo(s):
+    # k_s(x,y) = E_{u ~ N(0,I)} 2 max(0,u.x)^s max(0,u.y)^s, checked against the closed form
+    rng = np.random.default_rng(20 + s)
+    d = 3
+    X = rng.standard_normal((4, d))
+    Y = rng.standard_normal((3, d))
+    Uz = rng.standard_normal((1_000_000, d))
+    wx = np.maximum(Uz @ X.T, 0.0)
+    wy = np.maximum(Uz @ Y.T, 0.0)
+    if s == 0:
+        wx, wy = (wx > 0).astype(float), (wy > 0).astype(float)
+    else:
+        wx, wy = wx ** s, wy ** s
+    mc = 2.0 * (wx.T @ wy) / Uz.shape[0]
+    np.testing.assert_allclose(mc, o.arccos_kernel(X, Y, s), rtol=0.03, atol=3e-3)
+
+
+def test_arccos_special_values():
+    x = np.array([[0.6, -0.8, 0.0]])
+    assert abs(o.arccos_kernel(x, x, 0)[0, 0] - 1.0) < 1e-12          # angle 0: J_0 = pi
+    assert abs(o.arccos_kernel(x, -x, 0)[0, 0]) < 1e-12               # angle pi
+    assert abs(o.arccos_kernel(2 * x, x, 1)[0, 0] - 2.0) < 1e-12      # ||x|| ||y|| at angle 0
+    y = np.array([[0.8, 0.6, 0.0]])                                    # orthogonal unit vectors
+    assert abs(o.arccos_kernel(x, y, 1)[0, 0] - 1.0 / math.pi) < 1e-12
+    assert abs(o.arccos_kernel(x, y, 0)[0, 0] - 0.5) < 1e-12
+
+
+@pytest.mark.parametrize("s", [0, 1, 2])
+def test_arccos_features_are_unbiased(s):
+    # sum_k phi(x,u_k) phi(y,u_k) over r anchors u_k ~ N(0, sigma^2 I) -> k_s(x,y) + kappa
+    rng = np.random.default_rng(30 + s)
+    d, r, sigma, kappa = 2, 400_000, 1.5, 0.3
+    X = rng.standard_normal((3, d)) * 0.7
+    Y = rng.standard_normal((2, d)) * 0.7
+    U = sigma * rng.standard_normal((r, d))
+    Lx = o.arccos_log_features(X, U, s, sigma, kappa)
+    Ly = o.arccos_log_features(Y, U, s, sigma, kappa)
+    K = np.exp(Lx) @ np.exp(Ly).T
+    np.testing.assert_allclose(K, o.arccos_kernel(X, Y, s) + kappa, rtol=0.03)
+
+
+def test_arccos_kernel_is_bounded_below_by_kappa():
+    rng = np.random.default_rng(40)
+    U = 1.3 * rng.standard_normal((50, 4))
+    X = rng.standard_normal((30, 4))
+    Y = -X  # every projection changes sign: only the constant feature is shared
+    K = np.exp(o.arccos_log_features(X, U, 1, 1.3, 0.2)) @ np.exp(o.arccos_log_features(Y, U, 1, 1.3, 0.2)).T
+    assert np.all(K >= 0.2 * (1 - 1e-12))
+    np.testing.assert_allclose(np.diag(K), 0.2, rtol=1e-12)
+
+
+def test_arccos_factored_sinkhorn_matches_dense_textbook():
+    rng = np.random.default_rng(41)
+    n, m, d, r = 9, 7, 3, 20
+    X = rng.standard_normal((n, d))
+    Y = rng.standard_normal((m, d)) + 0.5
+    a = rng.exponential(size=n); a /= a.sum()
+    b = rng.exponential(size=m); b /= b.sum()
+    U = 1.4 * rng.standard_normal((r, d))
+    out = o.arccos_divergence(X, Y, a, b, U, 1, 1.4, 0.1, eps=1.0, iters=60, debiased=False)
+    K = np.exp(o.arccos_log_features(X, U, 1, 1.4, 0.1)) @ np.exp(o.arccos_log_features(Y, U, 1, 1.4, 0.1)).T
+    dense = o.sinkhorn_dense(K, a, b, 60)
+    np.testing.assert_allclose(out["xy"]["logu"], dense["logu"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(out["W_xy"], o.dual_estimate(a, b, dense["logu"], dense["logv"], 1.0), rtol=1e-12)
