@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="both", choices=["both", "stored", "recompute"])
+    ap.add_argument("--mode", default="both", choices=["both", "stored", "recompute", "log"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
@@ -624,15 +624,18 @@ def main():
         launches = lsf.lsf_launch_count()
         clocks = sampler.stop()
         ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        cls = lsf.LSF_KERNEL_PASS if mode == "stored" else lsf.LSF_KERNEL_PASS_RECOMPUTE
+        cls = {"stored": lsf.LSF_KERNEL_PASS, "recompute": lsf.LSF_KERNEL_PASS_RECOMPUTE,
+               "log": lsf.LSF_KERNEL_PASS_LOG}[mode]
         k_ms, k_n, k_bytes = lsf.lsf_profile_read(cls)
         feat_ms, _, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
         lsf.lsf_profile_enable(False)
         vals = prob.values()
         share = k_ms / (ms * args.steps) if ms > 0 else None
-        if mode == "stored":
+        if mode in ("stored", "log"):
             achieved = (k_bytes / 1e9) / (k_ms / 1e3) if k_ms > 0 else None
-            roof = {"bound": "hbm", "kernel": "pass_kernel (fused Sinkhorn half-iteration)",
+            kname = ("pass_kernel (fused Sinkhorn half-iteration)" if mode == "stored" else
+                     "logpass_kernel (log-domain fused half-iteration; ex2-bound)")
+            roof = {"bound": "hbm", "kernel": kname,
                     "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                     "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / max(k_n, 1),
