@@ -6,20 +6,21 @@
 // thousand points. Here one thread-block cluster (16 CTAs, or 8 where 16 cannot
 // be scheduled) runs the whole solve in one launch: the start v~ = exp(shift_y -
 // M), every half iteration, and the residual pass. Each CTA owns a contiguous
-// slice of the rows of both clouds (kept in shared memory when they fit, read
-// from L2 otherwise); a half iteration is
+// slice of the rows of both clouds (kept in shared memory with their weights and
+// scalings when they fit, read from L2 otherwise); a half iteration is
 //   row products s_i = F_i . t, new_i = w_i / s_i, t'_k += new_i F_ik
 // with warp-per-row dot products (two rows in flight per warp) and the
-// transposed product in registers; the warps' partials are folded in shared
-// memory, and after one cluster barrier every CTA sums the CTAs' partials of
-// the cluster in rank order from distributed shared memory, so all CTAs hold the
-// same t' for the next half. The CTA partials are double-buffered: a CTA
-// rewrites a buffer only two barriers after its peers finished reading it.
+// transposed product in registers. The warps' partials are folded in shared
+// memory and each CTA pushes its partial r-vector into every CTA of the cluster
+// (asynchronous distributed-shared-memory stores that complete transaction
+// bytes on the receiver's mbarrier); a CTA then waits on its own barrier only,
+// and sums the CTAs' partials in rank order, so all CTAs hold the same t'. Two
+// gather buffers alternate: a CTA pushes into buffer b for half h + 2 only after
+// every peer has pushed half h + 1, which each peer does after it consumed
+// buffer b of half h.
 //
-// Every CTA executes the same sequence of cluster barriers whatever its data
-// (no early exit), so the barriers cannot wait for a CTA that left. Sums are in
-// a fixed order (rows within a warp, warps, then ranks), so results are
-// deterministic.
+// Waits are bounded (status LSF_ERR_TIMEOUT). Sums are in a fixed order (rows
+// within a warp, warps, then ranks), so results are deterministic.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -87,12 +88,22 @@ __device__ __forceinline__ void small_axpy(float (&acc)[C][4], float sc, const f
 // kHalfDot (residual |old (F t) - w| only). For Init and Update the cluster's
 // transposed product ends up in tb (every CTA) and, from rank 0, in t_out.
 // Returns this thread's residual sum (Dot).
+// Exchange state of one cluster: gather buffers [2][kMaxCluster][ldr], their
+// mbarriers, and which buffer / phase the next half uses.
+constexpr int kMaxCluster = 16;
+struct Exchange {
+  float* gbuf;
+  uint64_t* gbar;
+  unsigned rank, CL;
+  int h;  // halves exchanged so far
+};
+
+// w and s are indexed by i - off (off = lo for rows held in shared memory)
 template <int C, bool RES, int KIND>
 __device__ __forceinline__ double small_half(const float* F, const float* w, const float* shift,
-                                             float* s, float* t_out, const float* rows, int64_t lo,
-                                             int64_t hi, float M, float* tb, float* pbuf,
-                                             float* red, int ldr, int& flag) {
-  cg::cluster_group cluster = cg::this_cluster();
+                                             float* s, int64_t off, float* t_out, const float* rows,
+                                             int64_t lo, int64_t hi, float M, float* tb,
+                                             float* red, int ldr, Exchange& ex, int& flag) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float acc[C][4];
 #pragma unroll
@@ -123,8 +134,8 @@ __device__ __forceinline__ double small_half(const float* F, const float* w, con
       sa = expf(shift[i] - M);
       if (has2) sb = expf(shift[i2] - M);
       if (lane == 0) {
-        s[i] = sa;
-        if (has2) s[i2] = sb;
+        s[i - off] = sa;
+        if (has2) s[i2 - off] = sb;
       }
     } else {
       float da = small_dot<C>(fa, tv), db = small_dot<C>(fb, tv);
@@ -133,23 +144,23 @@ __device__ __forceinline__ double small_half(const float* F, const float* w, con
         da += __shfl_xor_sync(0xffffffffu, da, o);
         db += __shfl_xor_sync(0xffffffffu, db, o);
       }
-      const float wa = w[i], wb = has2 ? w[i2] : 0.f;
+      const float wa = w[i - off], wb = has2 ? w[i2 - off] : 0.f;
       if (KIND == kHalfDot) {
         // the previous scalings were written by this same lane in the last update
         if (lane == 0) {
-          res += fabs(static_cast<double>(s[i]) * static_cast<double>(da) - static_cast<double>(wa));
+          res += fabs(static_cast<double>(s[i - off]) * static_cast<double>(da) - static_cast<double>(wa));
           if (has2)
-            res += fabs(static_cast<double>(s[i2]) * static_cast<double>(db) - static_cast<double>(wb));
+            res += fabs(static_cast<double>(s[i2 - off]) * static_cast<double>(db) - static_cast<double>(wb));
         }
         continue;
       }
       sa = wa * __frcp_rn(da);
       sb = has2 ? wb * __frcp_rn(db) : 0.f;
       if (lane == 0) {
-        s[i] = sa;
+        s[i - off] = sa;
         if (!(da > 0.f) || !isfinite(sa)) flag |= LSF_ERR_NONFINITE;
         if (has2) {
-          s[i2] = sb;
+          s[i2 - off] = sb;
           if (!(db > 0.f) || !isfinite(sb)) flag |= LSF_ERR_NONFINITE;
         }
       }
@@ -169,27 +180,44 @@ __device__ __forceinline__ double small_half(const float* F, const float* w, con
             make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ldr; idx += blockDim.x) {
-      float sum = 0.f;
-#pragma unroll
-      for (int wq = 0; wq < kSmallWarps; ++wq) sum += red[static_cast<size_t>(wq) * ldr + idx];
-      pbuf[idx] = sum;
-    }
-    cluster.sync();
-    const unsigned CL = cluster.num_blocks();
     const int nv4 = ldr >> 2;
+    const int b = ex.h & 1;
+    const uint32_t parity = static_cast<uint32_t>(ex.h >> 1) & 1u;
+    // fold the warps and push this CTA's partial into slot `rank` of every CTA's buffer b
+    const uint32_t slot = smem_u32(ex.gbuf + (static_cast<size_t>(b) * kMaxCluster + ex.rank) * ldr);
+    const uint32_t bar = smem_u32(ex.gbar + b);
+    for (int i4 = threadIdx.x; i4 < nv4; i4 += blockDim.x) {
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int wq = 0; wq < kSmallWarps; ++wq) {
+        const float4 v = *reinterpret_cast<const float4*>(red + static_cast<size_t>(wq) * ldr + 4 * i4);
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+      }
+      for (unsigned rk = 0; rk < ex.CL; ++rk) {
+        uint32_t rdst, rbar;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rdst) : "r"(slot + 16u * i4), "r"(rk));
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(bar), "r"(rk));
+        asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                     :: "r"(rdst), "f"(sum.x), "f"(sum.y), "f"(sum.z), "f"(sum.w), "r"(rbar) : "memory");
+      }
+    }
+    // every CTA's partial of this half has landed in buffer b
+    if (!mbar_wait_bounded(ex.gbar + b, parity)) flag |= LSF_ERR_TIMEOUT;
+    const float* g = ex.gbuf + static_cast<size_t>(b) * kMaxCluster * ldr;
     for (int i4 = threadIdx.x; i4 < nv4; i4 += blockDim.x) {
       CompSum a0, a1, a2, a3;
-      for (unsigned rk = 0; rk < CL; ++rk) {
-        const float* peer = cluster.map_shared_rank(pbuf, rk);
-        const float4 v = *reinterpret_cast<const float4*>(peer + 4 * i4);
+      for (unsigned rk = 0; rk < ex.CL; ++rk) {
+        const float4 v = *reinterpret_cast<const float4*>(g + static_cast<size_t>(rk) * ldr + 4 * i4);
         a0.add(v.x); a1.add(v.y); a2.add(v.z); a3.add(v.w);
       }
       const float4 tot = make_float4(a0.value(), a1.value(), a2.value(), a3.value());
       *reinterpret_cast<float4*>(tb + 4 * i4) = tot;
-      if (cluster.block_rank() == 0) *reinterpret_cast<float4*>(t_out + 4 * i4) = tot;
+      if (ex.rank == 0) *reinterpret_cast<float4*>(t_out + 4 * i4) = tot;
     }
     __syncthreads();
+    // buffer b is consumed: arm its barrier for its next use (half h + 2)
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(ex.gbar + b, ex.CL * ldr * 4u);
+    ++ex.h;
     return 0.0;
   }
 }
@@ -207,10 +235,11 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     if (pid == static_cast<unsigned>(q)) P = A.probs[q];
   const int ldr = A.ldr;
   extern __shared__ __align__(16) float sm[];
-  float* tb = sm;                         // [ldr] current r-vector
-  float* pb = tb + ldr;                   // [2][ldr] CTA partials, read by the peers
-  float* red = pb + 2 * ldr;              // [kSmallWarps][ldr]
-  float* rows = red + kSmallWarps * ldr;  // resident rows (RES)
+  float* tb = sm;                                   // [ldr] current r-vector
+  float* red = tb + ldr;                            // [kSmallWarps][ldr]
+  float* gbuf = red + kSmallWarps * ldr;            // [2][kMaxCluster][ldr] gathered partials
+  float* rows = gbuf + 2 * kMaxCluster * ldr;       // resident rows (RES), then w and s
+  __shared__ __align__(8) uint64_t s_gbar[2];
   __shared__ double s_dred[kSmallWarps];
   __shared__ double s_dpart;
   __shared__ float s_fred[kSmallWarps];
@@ -219,14 +248,30 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
 
   const int64_t lo0 = P.n[0] * rank / CL, hi0 = P.n[0] * (rank + 1) / CL;
   const int64_t lo1 = P.n[1] * rank / CL, hi1 = P.n[1] * (rank + 1) / CL;
+  const int64_t nr0 = hi0 - lo0, nr1 = hi1 - lo1;
   float* rows0 = rows;
-  float* rows1 = rows + (hi0 - lo0) * ldr;
+  float* rows1 = rows + nr0 * ldr;
+  // resident weights and scalings (RES): w0, w1, s0, s1 after the rows
+  float* rw0 = rows1 + nr1 * ldr;
+  float* rw1 = rw0 + nr0;
+  float* rs0 = rw1 + nr1;
+  float* rs1 = rs0 + nr0;
   if (RES) {
-    const int64_t c0 = (hi0 - lo0) * ldr / 4, c1 = (hi1 - lo1) * ldr / 4;
+    const int64_t c0 = nr0 * ldr / 4, c1 = nr1 * ldr / 4;
     const float4* g0 = reinterpret_cast<const float4*>(P.F[0] + lo0 * ldr);
     const float4* g1 = reinterpret_cast<const float4*>(P.F[1] + lo1 * ldr);
     for (int64_t q = threadIdx.x; q < c0; q += blockDim.x) reinterpret_cast<float4*>(rows0)[q] = __ldg(g0 + q);
     for (int64_t q = threadIdx.x; q < c1; q += blockDim.x) reinterpret_cast<float4*>(rows1)[q] = __ldg(g1 + q);
+    for (int64_t q = threadIdx.x; q < nr0; q += blockDim.x) rw0[q] = __ldg(P.w[0] + lo0 + q);
+    for (int64_t q = threadIdx.x; q < nr1; q += blockDim.x) rw1[q] = __ldg(P.w[1] + lo1 + q);
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(s_gbar + 0, 1);
+    mbar_init(s_gbar + 1, 1);
+    fence_mbarrier_init();
+    // first use of each gather buffer: every CTA of the cluster pushes ldr floats
+    mbar_arrive_expect_tx(s_gbar + 0, CL * ldr * 4u);
+    mbar_arrive_expect_tx(s_gbar + 1, CL * ldr * 4u);
   }
   // M = max_j shift_y(j) over the whole cloud (the start v = 1 as v~ = exp(shift - M))
   float m = -INFINITY;
@@ -239,6 +284,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     for (int wq = 1; wq < kSmallWarps; ++wq) mm = fmaxf(mm, s_fred[wq]);
     s_fpart = mm;
   }
+  // also orders every CTA's barrier setup before any push
   cluster.sync();
   float M = -INFINITY;
   for (unsigned rk = 0; rk < CL; ++rk) M = fmaxf(M, *cluster.map_shared_rank(&s_fpart, rk));
@@ -247,21 +293,28 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     P.result->iters = A.iters;
   }
 
+  Exchange ex{gbuf, s_gbar, rank, CL, 0};
+  const float* w0 = RES ? rw0 : P.w[0];
+  const float* w1 = RES ? rw1 : P.w[1];
+  float* s0 = RES ? rs0 : P.s[0];
+  float* s1 = RES ? rs1 : P.s[1];
+  const int64_t off0 = RES ? lo0 : 0, off1 = RES ? lo1 : 0;
   int flag = 0;
-  int h = 0;
-  small_half<C, RES, kHalfInit>(P.F[1], P.w[1], P.shift[1], P.s[1], P.t[1], rows1, lo1, hi1, M, tb,
-                                pb + (h & 1) * ldr, red, ldr, flag);
-  ++h;
+  small_half<C, RES, kHalfInit>(P.F[1], w1, P.shift[1], s1, off1, P.t[1], rows1, lo1, hi1, M, tb,
+                                red, ldr, ex, flag);
   for (int it = 0; it < A.iters; ++it) {
-    small_half<C, RES, kHalfUpdate>(P.F[0], P.w[0], P.shift[0], P.s[0], P.t[0], rows0, lo0, hi0, M,
-                                    tb, pb + (h & 1) * ldr, red, ldr, flag);
-    ++h;
-    small_half<C, RES, kHalfUpdate>(P.F[1], P.w[1], P.shift[1], P.s[1], P.t[1], rows1, lo1, hi1, M,
-                                    tb, pb + (h & 1) * ldr, red, ldr, flag);
-    ++h;
+    small_half<C, RES, kHalfUpdate>(P.F[0], w0, P.shift[0], s0, off0, P.t[0], rows0, lo0, hi0, M,
+                                    tb, red, ldr, ex, flag);
+    small_half<C, RES, kHalfUpdate>(P.F[1], w1, P.shift[1], s1, off1, P.t[1], rows1, lo1, hi1, M,
+                                    tb, red, ldr, ex, flag);
   }
-  const double res = small_half<C, RES, kHalfDot>(P.F[0], P.w[0], P.shift[0], P.s[0], P.t[0], rows0,
-                                                  lo0, hi0, M, tb, pb, red, ldr, flag);
+  const double res = small_half<C, RES, kHalfDot>(P.F[0], w0, P.shift[0], s0, off0, P.t[0], rows0,
+                                                  lo0, hi0, M, tb, red, ldr, ex, flag);
+  if (RES) {
+    // the scalings go out once, at the end
+    for (int64_t q = threadIdx.x; q < nr0; q += blockDim.x) P.s[0][lo0 + q] = rs0[q];
+    for (int64_t q = threadIdx.x; q < nr1; q += blockDim.x) P.s[1][lo1 + q] = rs1[q];
+  }
   if (lane == 0) s_dred[warp] = res;
   if (flag) atomicOr(&P.result->status, flag);
   __syncthreads();
@@ -284,8 +337,8 @@ int g_small_policy = 1;                  // 0 never, 1 by size, 2 whenever possi
 int64_t g_small_max_entries = 1LL << 24;  // (n + m) * ldr limit of the size rule
 
 size_t small_smem(int ldr, int64_t rows, bool res) {
-  return sizeof(float) * (static_cast<size_t>(3 + kSmallWarps) * ldr +
-                          (res ? static_cast<size_t>(rows) * ldr : 0));
+  return sizeof(float) * (static_cast<size_t>(1 + kSmallWarps + 2 * kMaxCluster) * ldr +
+                          (res ? static_cast<size_t>(rows) * (ldr + 2) : 0));
 }
 
 template <int C, bool RES>
