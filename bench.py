@@ -67,6 +67,7 @@ def parse():
                     choices=["large", "batched", "serving", "diff", "tiny", "arccos"])
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=32)
     return ap.parse_args()
 
 
@@ -321,7 +322,7 @@ def run_serving(args):
     warm = make()[: min(8, count)]
     serve.Server(budget_bytes=40e9).serve(warm, realtime=False)
     torch.cuda.synchronize()
-    srv = serve.Server(budget_bytes=40e9, slots=16)
+    srv = serve.Server(budget_bytes=40e9, slots=args.slots)
     mixed = srv.serve(make(), realtime=True)
     st_mixed = serve.latency_stats(mixed)
     seq = serve.serve_sequential(make(), realtime=True)
@@ -334,7 +335,7 @@ def run_serving(args):
         "config": {"workload": f"serving: Poisson stream of {count} debiased-divergence requests at "
                                f"{args.rate:g}/s, n,m log-uniform [2^8, 2^18], d in {{2,3,16}}, "
                                f"r in {{128,512}}, eps in {{0.05,0.2,1.0}}, mixture clouds, uniform "
-                               f"weights, {iters} iterations, 40 GB admission budget, 16 slots"},
+                               f"weights, {iters} iterations, 40 GB admission budget, {args.slots} slots"},
         "served": {**st_mixed, "peak_inflight": srv.peak_inflight, "peak_bytes": srv.peak_bytes,
                    "nonfinite_requests": nonfinite},
         "plain_sequential": st_seq,

@@ -90,7 +90,11 @@ typedef struct {
   double W;          /* Eq. (6) estimate eps (a^T log u + b^T log v); set by lsf_divergence  */
   double residual;   /* ||u o (K v) - a||_1 after the last v-half (Alg. 1 stopping quantity)  */
   double log_scale;  /* M, the global factor of the scalings (see conventions)                */
-  int32_t status;    /* OR of device-side status bits (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT)    */
+  int32_t status;    /* OR of device-side status bits (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT).
+                        Once a scaling-domain run (stored or recompute) has set
+                        LSF_ERR_NONFINITE, its remaining passes stream nothing: the
+                        run is void and W, the scalings and the r-vectors are not
+                        meaningful (repeat it with LSF_MODE_LOG).                    */
   int32_t iters;     /* iterations run                                                         */
 } lsf_result;
 

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
   __shared__ double s_res[kConsumerWarps][2];
   __shared__ int s_flag;
   __shared__ int s_last;
+  __shared__ int s_skip;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -59,6 +60,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
     ring_init(ring, kConsumerWarps);
     fence_mbarrier_init();
     s_flag = 0;
+    // a scaling-domain run that already produced a non-finite scaling is void
+    // (it is repeated in the log domain): stream no tiles, but take part in the
+    // cross-CTA reduction so that its counters stay consistent. Read once per
+    // CTA, so the producer and the consumers agree.
+    s_skip = (*reinterpret_cast<volatile int*>(a.status) & LSF_ERR_NONFINITE) != 0;
   }
   if (kTsmem && kNeedT) {
     for (int idx = threadIdx.x; idx < NRHS * 128 * C; idx += blockDim.x) {
@@ -79,8 +85,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[k][j][e] = 0.f;
   }
+  const int64_t ntiles = s_skip ? 0 : a.ntiles;
   if (warp == kConsumerWarps) {
-    ring_produce<NRHS>(ring, a.F, a.n, a.ntiles, a.rhs, MODE != kPassAxpy, lane, flag);
+    ring_produce<NRHS>(ring, a.F, a.n, ntiles, a.rhs, MODE != kPassAxpy, lane, flag);
   } else {
     float t[kTsmem ? 1 : NRHS][C][4];
     bool has_old[NRHS];
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
 
     int it = 0;
     bool dead = false;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && !dead; tile += static_cast<int64_t>(TP) * gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < ntiles && !dead; tile += static_cast<int64_t>(TP) * gridDim.x) {
       // the TP tiles this step works on: tile, tile + grid, ... (consecutive ring stages)
       int rows_u[TP];
       int64_t row0_u[TP];
@@ -116,7 +123,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
         row0_u[u] = 0;
         tF_u[u] = ring.sF;
         vbase_u[u] = ring.sV;
-        if (tu < a.ntiles) {
+        if (tu < ntiles) {
           const int s = (it + u) % S;
           if (!ring_wait_full(ring, it + u, lane)) {
             flag |= LSF_ERR_TIMEOUT;

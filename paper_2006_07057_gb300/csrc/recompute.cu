@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   __shared__ __align__(16) float4 s_rows[3][RPB * SV];
   __shared__ __align__(16) float s_red[2][NRHS][kRcRB][kRcWarps];  // per-warp partial row products
   __shared__ double s_res[kRcWarps][2];
-  __shared__ int s_flag, s_last;
+  __shared__ int s_flag, s_last, s_skip;
   extern __shared__ __align__(16) float s_part[];  // [NG][NRHS * ldr] at the end
 
   const bool kUpd = mode == kPassUpdate, kAx = mode == kPassAxpy, kDt = mode == kPassDot;
@@ -65,7 +65,13 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   const int ldr = a.ldr, d = a.d;
   const int col0 = 4 * tg;                  // my four columns
 
-  if (tid == 0) s_flag = 0;
+  if (tid == 0) {
+    s_flag = 0;
+    // a run that already produced a non-finite scaling is void (repeated in the
+    // log domain): process no rows, but take part in the cross-CTA reduction
+    s_skip = (*reinterpret_cast<volatile int*>(a.status) & LSF_ERR_NONFINITE) != 0;
+  }
+  __syncthreads();
   // per-column constants
   float Ap[4], Wp[4][D];
 #pragma unroll
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   }
   int flag = 0;
 
-  const int64_t nbatch = (a.n + RPB - 1) / RPB;
+  const int64_t nbatch = s_skip ? 0 : (a.n + RPB - 1) / RPB;
   // register prefetch of one row's record by threads tid < RPB
   float4 pre[SV];
   auto load_rows = [&](int64_t b) {
