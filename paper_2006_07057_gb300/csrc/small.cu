@@ -118,16 +118,37 @@ __device__ __forceinline__ double small_half(const float* F, const float* w, con
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   double res = 0.0;
+  // rows read from L2 are prefetched one step ahead (shared-memory rows need not)
+  float4 na[C], nb[C];
+  auto fetch = [&](int64_t i) {
+    if (i < hi) small_load<C, RES>(na, F, rows, i, lo, ldr, lane);
+    if (i + kSmallWarps < hi) {
+      small_load<C, RES>(nb, F, rows, i + kSmallWarps, lo, ldr, lane);
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) nb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (!RES) fetch(lo + warp);
   for (int64_t i = lo + warp; i < hi; i += 2 * kSmallWarps) {
     const int64_t i2 = i + kSmallWarps;
     const bool has2 = i2 < hi;
     float4 fa[C], fb[C];
-    small_load<C, RES>(fa, F, rows, i, lo, ldr, lane);
-    if (has2) {
-      small_load<C, RES>(fb, F, rows, i2, lo, ldr, lane);
+    if (RES) {
+      small_load<C, RES>(fa, F, rows, i, lo, ldr, lane);
+      if (has2) {
+        small_load<C, RES>(fb, F, rows, i2, lo, ldr, lane);
+      } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j) fb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     } else {
 #pragma unroll
-      for (int j = 0; j < C; ++j) fb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < C; ++j) {
+        fa[j] = na[j];
+        fb[j] = nb[j];
+      }
+      fetch(i + 2 * kSmallWarps);
     }
     float sa, sb = 0.f;
     if (KIND == kHalfInit) {
