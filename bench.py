@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--batch-strategy", type=int, default=0, choices=[0, 1, 2])
     return ap.parse_args()
 
 
@@ -220,6 +221,7 @@ def run_batched(args):
     import torch
     import paper_2006_07057_gb300 as lsf
     torch.cuda.set_device(0)
+    lsf.lsf_set_batch_strategy(args.batch_strategy)
     iters = 100
     probs = synth.batched_problems(seed=0, count=args.count, iters=iters)
     dev = torch.device("cuda", 0)
@@ -282,9 +284,12 @@ def run_batched(args):
         "data": "synthetic",
         "config": {"workload": f"batched: {n} problems, n,m log-uniform [2^10, 2^16], d in {{2,3,16}}, "
                                f"r in {{128,256}}, eps log-uniform [0.05,1], mixture clouds, Dirichlet(1) "
-                               f"weights, {iters} iterations, one graph-captured persistent launch per "
-                               f"feature width, stored features resident",
+                               f"weights, {iters} iterations, CUDA-graph captured, one launch per feature "
+                               f"width and domain (one cluster per problem or one persistent kernel), "
+                               f"stored features resident",
                    "groups": {str(sv.ldr): [{"mode": b.mode, "problems": len(idx),
+                                             "strategy": ("clusters" if b.info.strategy == 1
+                                                          else "persistent"),
                                              "tile_bytes": b.tile_bytes, "tile_rows": b.info.tile_rows,
                                              "stages": b.info.stages} for b, idx in sv.batches]
                               for sv in solvers}},

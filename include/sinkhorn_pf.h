@@ -318,6 +318,7 @@ typedef struct {
   int64_t rows_y;     /* sum of m over the batch                   */
   size_t plan_bytes;  /* device plan size                          */
   size_t smem_bytes;  /* dynamic shared memory of the kernel       */
+  int strategy;       /* 0 persistent kernel, 1 one cluster per problem */
 } lsf_batch_info;
 
 /*
@@ -343,6 +344,20 @@ int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr, int mode,
  * kernel. Only kernel launches: capturable in a CUDA graph.
  */
 int lsf_solve_batched(const lsf_batch_info* info, void* plan, int iters, void* stream);
+
+/*
+ * How lsf_batch_plan lays out a stored batch (the iterates are the same): 0 one
+ * persistent kernel streaming all problems' tiles every round (problems of any
+ * size); 1 one 8-CTA thread-block cluster per problem, all problems in one
+ * launch, each cluster running its problem's iterations with its features read
+ * from L2; 2 the cluster layout when the batch has at least 2 * SMs / 8
+ * problems and each has (n + m) * ldr <= 2^18. The default is 0 (on the batched
+ * workload of n, m up to 2^16 the persistent kernel is 1.4x faster). Log-domain
+ * batches always use the persistent kernel. Recorded in
+ * lsf_batch_info.strategy; process-wide.
+ * Errors: LSF_ERR_ARG for a value outside 0..2.
+ */
+int lsf_set_batch_strategy(int strategy);
 
 /* ---------------------------------------------------------------- adjoint */
 

@@ -340,6 +340,11 @@ def lsf_anchor_gradient(theta: Theta, x: Cloud, y: Cloud, s_xy: Scalings, s_xx: 
           "lsf_anchor_gradient")
 
 
+def lsf_set_batch_strategy(strategy: int) -> None:
+    """0: persistent kernel (default), 1: one cluster per problem, 2: by rule."""
+    check(lib().lsf_set_batch_strategy(int(strategy)), "lsf_set_batch_strategy")
+
+
 def lsf_set_small_solver(policy: int, max_entries: int = 1 << 24) -> None:
     """0: never use the cluster small-problem solver, 1: by size (default), 2: always."""
     check(lib().lsf_set_small_solver(int(policy), int(max_entries)), "lsf_set_small_solver")

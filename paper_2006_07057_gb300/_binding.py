@@ -78,7 +78,8 @@ class LsfBatchProblem(ctypes.Structure):
 class LsfBatchInfo(ctypes.Structure):
     _fields_ = [("count", c_int), ("ldr", c_int), ("mode", c_int), ("tile_rows", c_int), ("stages", c_int),
                 ("grid", c_int), ("tiles_x", c_int64), ("tiles_y", c_int64), ("rows_x", c_int64),
-                ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t)]
+                ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t),
+                ("strategy", c_int)]
 
 _P = ctypes.POINTER
 _SIGNATURES = {
@@ -118,6 +119,7 @@ _SIGNATURES = {
     "lsf_batch_plan": (c_int, [_P(LsfBatchProblem), c_int, c_int, c_int, c_int, _P(LsfBatchInfo),
                                c_void_p, c_size_t, c_void_p]),
     "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),
+    "lsf_set_batch_strategy": (c_int, [c_int]),
     "lsf_set_pass_tiling": (c_int, [c_int, c_int]),
     "lsf_set_small_solver": (c_int, [c_int, ctypes.c_int64]),
     "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),

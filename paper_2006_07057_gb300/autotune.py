@@ -57,6 +57,10 @@ def best_batch_tile(solver, candidates=CANDIDATES, use_cache: bool = True) -> in
     if key in cache:
         return int(cache[key]["tile_bytes"])
     stream = solver.stream or torch.cuda.current_stream()
+    info, _ = lsf_batch_plan(solver.records, solver.ldr, candidates[0], stream,
+                             mode=getattr(solver, "mode", "stored"))
+    if info.strategy == 1:
+        return candidates[0]  # one cluster per problem: no tiles to size
     timings = {}
     for tb in candidates:
         info, plan = lsf_batch_plan(solver.records, solver.ldr, tb, stream,

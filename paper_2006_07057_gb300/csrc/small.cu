@@ -40,6 +40,7 @@ enum SmallHalf : int { kHalfInit = 0, kHalfUpdate = 1, kHalfDot = 2 };
 
 struct SmallArgs {
   SProb probs[kSmallMaxProblems];
+  const SProb* table;  // device problem table (batches), or NULL: probs[] above
   int ldr;
   int iters;
 };
@@ -249,11 +250,15 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
   const unsigned CL = cluster.num_blocks();
   const unsigned rank = cluster.block_rank();
   const unsigned pid = blockIdx.x / CL;
-  // the problem record, picked by compile-time indices
+  // the problem record: from the device table, or picked by compile-time indices
   SProb P = A.probs[0];
+  if (A.table) {
+    P = A.table[pid];
+  } else {
 #pragma unroll
-  for (int q = 1; q < kSmallMaxProblems; ++q)
-    if (pid == static_cast<unsigned>(q)) P = A.probs[q];
+    for (int q = 1; q < kSmallMaxProblems; ++q)
+      if (pid == static_cast<unsigned>(q)) P = A.probs[q];
+  }
   const int ldr = A.ldr;
   extern __shared__ __align__(16) float sm[];
   float* tb = sm;                                   // [ldr] current r-vector
@@ -294,6 +299,13 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     mbar_arrive_expect_tx(s_gbar + 0, CL * ldr * 4u);
     mbar_arrive_expect_tx(s_gbar + 1, CL * ldr * 4u);
   }
+  if (A.table && rank == 0 && threadIdx.x == 0) {
+    // batches: the record is cleared before the cluster barrier below, so before
+    // any CTA can OR its status bits into it
+    P.result->W = 0.0;
+    P.result->residual = 0.0;
+    P.result->status = 0;
+  }
   // M = max_j shift_y(j) over the whole cloud (the start v = 1 as v~ = exp(shift - M))
   float m = -INFINITY;
   for (int64_t j = lo1 + threadIdx.x; j < hi1; j += blockDim.x) m = fmaxf(m, P.shift[1][j]);
@@ -313,6 +325,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     P.result->log_scale = static_cast<double>(M);
     P.result->iters = A.iters;
   }
+
 
   Exchange ex{gbuf, s_gbar, rank, CL, 0};
   const float* w0 = RES ? rw0 : P.w[0];
@@ -364,6 +377,7 @@ size_t small_smem(int ldr, int64_t rows, bool res) {
 
 template <int C, bool RES>
 int launch_small_c(const SmallArgs& a, int count, size_t smem, cudaStream_t st) {
+  const int prefs[2] = {a.table ? 8 : 16, 8};
   void (*kern)(SmallArgs) = small_solve_kernel<C, RES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
@@ -381,7 +395,7 @@ int launch_small_c(const SmallArgs& a, int count, size_t smem, cudaStream_t st) 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int cl = 0;
-  for (int want : {16, 8}) {
+  for (int want : prefs) {
     attr[0].val.clusterDim.x = want;
     cfg.gridDim = dim3(static_cast<unsigned>(want), 1, 1);
     int nclusters = 0;
@@ -416,6 +430,16 @@ bool small_solver_takes(int64_t n, int64_t m, int ldr) {
   if (g_small_policy == 0) return false;
   if (g_small_policy == 2) return true;
   return (n + m) * static_cast<int64_t>(ldr) <= g_small_max_entries;
+}
+
+int small_solve_table(const SProb* table, int count, int ldr, int iters, cudaStream_t st) {
+  if (!table || count < 1) return fail(LSF_ERR_ARG, "small solve: empty problem table");
+  SmallArgs a{};
+  a.table = table;
+  a.ldr = ldr;
+  a.iters = iters;
+  LaunchScope ls(st, LSF_KERNEL_SMALL, 0.0);
+  return launch_small<false>(a, count, small_smem(ldr, 0, false), st);
 }
 
 int small_solve(const SProb* probs, int count, int ldr, int iters, cudaStream_t st) {

@@ -30,4 +30,9 @@ bool small_solver_takes(int64_t n, int64_t m, int ldr);
 // Alg. 1, then the residual. One launch, one cluster per problem.
 int small_solve(const SProb* probs, int count, int ldr, int iters, cudaStream_t st);
 
+// As small_solve for a batch: `count` problems from a device table (any count),
+// one 8-CTA cluster each, rows read from L2. The kernel also clears each
+// problem's result record (W, residual, status) before solving it.
+int small_solve_table(const SProb* table, int count, int ldr, int iters, cudaStream_t st);
+
 }  // namespace lsf

@@ -1,7 +1,8 @@
 """Batched persistent solver vs per-problem solves and the oracle (GPU).
 
 Each problem of a batch is Alg. 1 on its own factored kernel; the batched
-kernel only changes how rows are scheduled and reduced, so its divergences must
+layouts (one persistent kernel over all tiles, or one thread-block cluster per
+problem) only change how rows are scheduled and reduced, so its divergences must
 match the oracle at the usual tolerances (1e-4 relative, residual 1e-5) and
 agree with lsf_solve on the same problem. Cases cover fewer tiles than CTAs
 (empty CTA ranges), many tiny problems straddling CTA boundaries, uneven n/m,
@@ -25,7 +26,16 @@ def lsf():
         pytest.skip("needs a CUDA device")
     import paper_2006_07057_gb300 as m
     m.lib()
-    return m
+    yield m
+    m.lsf_set_batch_strategy(0)
+
+
+@pytest.fixture(params=[0, 1], ids=["persistent", "clusters"])
+def strategy(lsf, request):
+    """Both layouts of a stored batch: one persistent kernel, or one cluster per problem."""
+    lsf.lsf_set_batch_strategy(request.param)
+    yield request.param
+    lsf.lsf_set_batch_strategy(0)
 
 
 class P:
@@ -61,14 +71,15 @@ def check_against_oracle(vals, probs):
     (3, 25, 100, 5000, 256),
     (4, 200, 5, 80, 128),       # many tiny problems across CTA boundaries
 ])
-def test_batched_matches_oracle(lsf, seed, count, n_lo, n_hi, r):
+def test_batched_matches_oracle(lsf, strategy, seed, count, n_lo, n_hi, r):
     probs = make_batch(seed, count, n_lo, n_hi, r, 25)
     solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=32 * 1024)
+    assert solver.info.strategy == strategy
     solver.run(25)
     check_against_oracle(solver.values(), probs)
 
 
-def test_batched_agrees_with_single_solves(lsf):
+def test_batched_agrees_with_single_solves(lsf, strategy):
     probs = make_batch(5, 12, 500, 20000, 256, 30)
     solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=44 * 1024)
     solver.run(30)
@@ -82,7 +93,7 @@ def test_batched_agrees_with_single_solves(lsf):
         assert abs(v["residual"] - s["res_xy"]) <= 1e-6
 
 
-def test_batched_graph_replay_and_determinism(lsf):
+def test_batched_graph_replay_and_determinism(lsf, strategy):
     probs = make_batch(6, 30, 200, 4000, 128, 20)
     solver = lsf.BatchedSolver([P(p) for p in probs], tile_bytes=32 * 1024)
     solver.run(20)
