@@ -174,6 +174,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: every rank's timed region counts (replicas only)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, ms: float) -> float:
+    """Units all ranks processed per second of the slowest rank's step."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -594,12 +610,8 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(ms):
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+    def slowest(ms):
+        return max_over_ranks(ms, world, dev)
 
     def measure(mode):
         """Warm-up, then K timed steps of one variant with inputs resident."""
@@ -629,7 +641,7 @@ def main():
         barrier()
         launches = lsf.lsf_launch_count()
         clocks = sampler.stop()
-        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        ms = slowest(e0.elapsed_time(e1) / args.steps)
         cls = {"stored": lsf.LSF_KERNEL_PASS, "recompute": lsf.LSF_KERNEL_PASS_RECOMPUTE,
                "log": lsf.LSF_KERNEL_PASS_LOG}[mode]
         k_ms, k_n, k_bytes = lsf.lsf_profile_read(cls)
@@ -661,7 +673,7 @@ def main():
                     "peak_kind": f"derived: 128/7 entries/clk/SM (FP32 pipe) x {SMS} SMs x {sm_mhz:.0f} MHz",
                     "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / max(k_n, 1),
                     "share_of_step": share}
-        return {"mode": mode, "ms": ms, "value": updates * world / (ms / 1e3), "launches": launches,
+        return {"mode": mode, "ms": ms, "value": whole_job_value(updates, world, ms), "launches": launches,
                 "clocks": clocks, "roofline": roof, "vals": vals,
                 "features_ms_per_step": feat_ms / args.steps}
 
@@ -691,8 +703,8 @@ def main():
             step_e2e()
         f1.record(stream)
         barrier()
-        ms_e2e = max_over_ranks(f0.elapsed_time(f1) / args.steps)
-        e2e = {"value": updates * world / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+        ms_e2e = slowest(f0.elapsed_time(f1) / args.steps)
+        e2e = {"value": whole_job_value(updates, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
 
     cpu = None
