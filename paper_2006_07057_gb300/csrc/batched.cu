@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
             t[j][0] = tv.x; t[j][1] = tv.y; t[j][2] = tv.z; t[j][3] = tv.w;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              acc[j][e] = z;
+              acc[j][e] = LOGD ? kLogFloor : 0.f;  // empty online log-sum-exp, or 0
               if (LOGD) lsum[LOGD ? j : 0][e] = 0.f;
             }
           }

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
     for (int j = 0; j < C; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        lm[k][j][e] = -INFINITY;
+        lm[k][j][e] = kLogFloor;
         ls[k][j][e] = 0.f;
       }
   }

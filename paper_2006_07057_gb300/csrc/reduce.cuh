@@ -136,10 +136,12 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
 
 // Online log-sum-exp: (m, s) represents log(s e^m); adding one term y gives
 // (max(m, y), s e^(m - max) + e^(y - max)). One of the two exponentials is
-// e^0 = 1, so one ex2 per term suffices. m = -inf, s = 0 is the empty sum.
+// e^0 = 1, so one ex2 per term suffices. The empty sum is (kLogFloor, 0): a
+// finite floor far below any log-domain value, so a term y = -inf (no mass)
+// adds e^-inf = 0 without a branch, and merges skip partials with s = 0.
+constexpr float kLogFloor = -1e30f;
 __device__ __forceinline__ void lse_push(float& m, float& s, float y) {
-  if (y == -INFINITY) return;
-  const float d = y - m;  // +inf while the sum is empty
+  const float d = y - m;
   const float e = ex2_approx(-fabsf(d) * kLog2e);
   s = (d > 0.f) ? fmaf(s, e, 1.f) : s + e;
   m = fmaxf(m, y);
