@@ -8,7 +8,10 @@
 // (the expansion of c_k - (2/eps)||x_i - u_k||^2 - shift_i, Lemma 1), then one
 // hardware ex2 per entry, shared by the row product and the transposed
 // accumulation of the same pass. HBM traffic drops to the points and vectors;
-// the bound becomes the FMA and MUFU pipes.
+// the bound becomes instruction issue. The FP32 arithmetic runs on column pairs
+// with the packed two-lane instructions (fma/add/mul .f32x2): a thread's four
+// columns are two pairs, so the exponent's affine form, the row products and the
+// transposed accumulation take half the instructions of scalar code.
 //
 // Layout: 256 threads; a row group of GW warps covers a row, each thread holding
 // four consecutive feature columns (their A_k and W_kd stay in registers for the
@@ -36,12 +39,13 @@ constexpr int kRcThreads = 256;
 constexpr int kRcWarps = kRcThreads / 32;
 constexpr int kRcRB = 8;  // rows per group per batch
 
-// Row record in shared memory, in float4s: x_0 .. x_{D-1}, B (padded to a float4
-// boundary), then (w, old) of each right-hand side.
+// Row record in shared memory, in float4s: (x_0, x_0, x_1, x_1), ..., (B, B)
+// (each value twice, so one load gives the broadcast pair a packed instruction
+// takes; padded to a float4 boundary), then (w, old) of each right-hand side.
 template <int D>
 struct RowPack {
-  static constexpr int kXV = (D + 1 + 3) / 4;  // float4s of x and B
-  static constexpr int kSV = kXV + 1;          // + (w0, old0, w1, old1)
+  static constexpr int kXV = (2 * (D + 1) + 3) / 4;  // float4s of x and B, doubled
+  static constexpr int kSV = kXV + 1;                // + (w0, old0, w1, old1)
 };
 
 template <int GW, int D, int NRHS>
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     s_skip = (*reinterpret_cast<volatile int*>(a.status) & LSF_ERR_NONFINITE) != 0;
   }
   __syncthreads();
-  // per-column constants
+  // per-column constants, as column pairs (col0, col0 + 1), (col0 + 2, col0 + 3)
   float Ap[4], Wp[4][D];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -92,7 +96,15 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
       Ap[e] = -INFINITY;  // ex2(-inf) = 0: padded columns carry no mass
     }
   }
-  float t[NRHS][4], acc[NRHS][4];
+  float2 A2[2], W2[2][D];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    A2[p] = make_float2(Ap[2 * p], Ap[2 * p + 1]);
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) W2[p][dd] = make_float2(Wp[2 * p][dd], Wp[2 * p + 1][dd]);
+  }
+  float t[NRHS][4];
+  float2 t2[NRHS][2], acc2[NRHS][2];
   double res[NRHS];
   bool has_old[NRHS];
 #pragma unroll
@@ -103,7 +115,11 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     for (int e = 0; e < 4; ++e) {
       const int col = col0 + e;
       t[k][e] = (!kAx && col < ldr) ? a.rhs[k].t_in[col] : 0.f;
-      acc[k][e] = 0.f;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      t2[k][p] = make_float2(t[k][2 * p], t[k][2 * p + 1]);
+      acc2[k][p] = make_float2(0.f, 0.f);
     }
   }
   int flag = 0;
@@ -122,17 +138,18 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
 #pragma unroll
       for (int dd = 0; dd < D; ++dd) {
         const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
-        rec[dd] = x;
+        rec[2 * dd] = x;
+        rec[2 * dd + 1] = x;
         nrm = fmaf(x, x, nrm);
       }
-      rec[D] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
+      rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) {
         rec[4 * XV + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
         rec[4 * XV + 2 * k + 1] = has_old[k] ? a.rhs[k].old[i] : 0.f;
       }
     } else {
-      rec[D] = -INFINITY;  // rows past the end carry no mass
+      rec[2 * D] = rec[2 * D + 1] = -INFINITY;  // rows past the end carry no mass
     }
 #pragma unroll
     for (int v = 0; v < SV; ++v) pre[v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
@@ -164,27 +181,30 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight while this batch computes
     const float4* rows = s_rows[it % 3];
     const int64_t row0 = b * RPB;
-    float F[kRcRB][4];
+    float2 F[kRcRB][2];  // the row's four entries as two column pairs
     float dots[NRHS][kRcRB];
 #pragma unroll
     for (int q = 0; q < kRcRB; ++q) {
       const float4* rw = rows + (g * kRcRB + q) * SV;
-      float xb[4 * XV];
+      float2 xb[2 * XV];  // (x_dd, x_dd) for dd < D, then (B, B)
 #pragma unroll
       for (int v = 0; v < XV; ++v) {
         const float4 f4 = rw[v];
-        xb[4 * v] = f4.x; xb[4 * v + 1] = f4.y; xb[4 * v + 2] = f4.z; xb[4 * v + 3] = f4.w;
+        xb[2 * v] = make_float2(f4.x, f4.y);
+        xb[2 * v + 1] = make_float2(f4.z, f4.w);
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float E = Ap[e] + xb[D];
+      for (int p = 0; p < 2; ++p) {
+        float2 E = __fadd2_rn(A2[p], xb[D]);
 #pragma unroll
-        for (int dd = 0; dd < D; ++dd) E = fmaf(xb[dd], Wp[e][dd], E);
-        F[q][e] = ex2_approx(E);
+        for (int dd = 0; dd < D; ++dd) E = __ffma2_rn(xb[dd], W2[p][dd], E);
+        F[q][p] = make_float2(ex2_approx(E.x), ex2_approx(E.y));
       }
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k)
-        dots[k][q] = fmaf(F[q][0], t[k][0], fmaf(F[q][1], t[k][1], fmaf(F[q][2], t[k][2], F[q][3] * t[k][3])));
+      for (int k = 0; k < NRHS; ++k) {
+        const float2 P = __ffma2_rn(F[q][0], t2[k][0], __fmul2_rn(F[q][1], t2[k][1]));
+        dots[k][q] = P.x + P.y;
+      }
     }
     float sc[NRHS][kRcRB];
     const int q = lane >> 2;
@@ -258,9 +278,11 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
 #pragma unroll
       for (int k = 0; k < NRHS; ++k)
 #pragma unroll
-        for (int qq = 0; qq < kRcRB; ++qq)
+        for (int qq = 0; qq < kRcRB; ++qq) {
+          const float2 s2 = make_float2(sc[k][qq], sc[k][qq]);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[k][e] = fmaf(sc[k][qq], F[qq][e], acc[k][e]);
+          for (int p = 0; p < 2; ++p) acc2[k][p] = __ffma2_rn(s2, F[qq][p], acc2[k][p]);
+        }
     }
   }
 
@@ -271,7 +293,8 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int col = col0 + e;
-        if (col < ldr) s_part[static_cast<size_t>(g) * NRHS * ldr + k * ldr + col] = acc[k][e];
+        const float v = (e & 1) ? acc2[k][e >> 1].y : acc2[k][e >> 1].x;
+        if (col < ldr) s_part[static_cast<size_t>(g) * NRHS * ldr + k * ldr + col] = v;
       }
   }
   // residual terms live in the threads that finished rows: per-warp sums, then
