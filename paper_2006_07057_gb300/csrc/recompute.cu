@@ -13,17 +13,20 @@
 // columns are two pairs, so the exponent's affine form, the row products and the
 // transposed accumulation take half the instructions of scalar code.
 //
-// Layout: 256 threads; a row group of GW warps covers a row, each thread holding
-// four consecutive feature columns (their A_k and W_kd stay in registers for the
-// whole launch). A batch gives every group 8 rows. A warp folds its 8 row
-// products with the multi-row butterfly (9 shuffles) and writes them to shared
-// memory; after one barrier every warp of the group sums the group's partials
-// for the 8 rows in the same fixed order and forms the new scalings itself (the
-// first warp of the group also writes them, with the residual terms and the
-// status), so no warp waits for another to finish a row. One barrier per batch
+// Layout: 8 compute warps and one service warp. A row group of GW compute warps
+// covers a row, each thread holding four consecutive feature columns (their
+// A_k and W_kd stay in registers for the whole launch). A batch gives every
+// group 8 rows. A warp folds its 8 row products with the multi-row butterfly (9
+// shuffles) and writes them to shared memory; after one barrier every compute
+// warp of the group sums the group's partials for the 8 rows in the same fixed
+// order and forms the new scalings itself, so no warp waits for another to
+// finish a row. The side work of a batch (building the rows' records two
+// batches ahead, writing the new scalings, the residual terms and the status)
+// belongs to the service warp, so the compute warps carry identical
+// instruction streams and meet at the barrier together (done by one of them,
+// that work made the other seven wait at every barrier). One barrier per batch
 // suffices: the partials are double-buffered, and the rows' records (x, B,
-// weights, previous scalings; float4-packed) go through a three-deep ring,
-// loaded two batches ahead and parked after the barrier.
+// weights, previous scalings; float4-packed) go through a three-deep ring.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,8 +38,8 @@
 namespace lsf {
 namespace {
 
-constexpr int kRcThreads = 256;
-constexpr int kRcWarps = kRcThreads / 32;
+constexpr int kRcWarps = 8;                      // compute warps
+constexpr int kRcThreads = (kRcWarps + 1) * 32;  // + the service warp
 constexpr int kRcRB = 8;  // rows per group per batch
 
 // Row record in shared memory, in float4s: (x_0, x_0, x_1, x_1), ..., (B, B)
@@ -48,6 +51,24 @@ struct RowPack {
   static constexpr int kSV = kXV + 1;                // + (w0, old0, w1, old1)
 };
 
+// The GW warp partials of one row, summed in a fixed tree order (vector loads;
+// the partials of a row are contiguous and GW-aligned).
+template <int GW>
+__device__ __forceinline__ float sum_partials(const float* p) {
+  if constexpr (GW == 8) {
+    const float4 lo = reinterpret_cast<const float4*>(p)[0], hi = reinterpret_cast<const float4*>(p)[1];
+    return ((lo.x + lo.y) + (lo.z + lo.w)) + ((hi.x + hi.y) + (hi.z + hi.w));
+  } else if constexpr (GW == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return (v.x + v.y) + (v.z + v.w);
+  } else if constexpr (GW == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return v.x + v.y;
+  } else {
+    return p[0];
+  }
+}
+
 template <int GW, int D, int NRHS>
 __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     recompute_kernel(const RecomputeArgs a, const int mode) {
@@ -56,15 +77,17 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   constexpr int TPG = GW * 32;              // threads per group
   constexpr int XV = RowPack<D>::kXV;
   constexpr int SV = RowPack<D>::kSV;
+  constexpr int kItems = NG * NRHS * kRcRB;  // (group, rhs, row) records per batch
   __shared__ __align__(16) float4 s_rows[3][RPB * SV];
   __shared__ __align__(16) float s_red[2][NRHS][kRcRB][kRcWarps];  // per-warp partial row products
-  __shared__ double s_res[kRcWarps][2];
+  __shared__ double s_res[kRcWarps + 1][2];
   __shared__ int s_flag, s_last, s_skip;
   extern __shared__ __align__(16) float s_part[];  // [NG][NRHS * ldr] at the end
 
   const bool kUpd = mode == kPassUpdate, kAx = mode == kPassAxpy, kDt = mode == kPassDot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = warp / GW;                  // my group
+  const bool service = warp == kRcWarps;
+  const int g = service ? 0 : warp / GW;    // my group
   const int tg = tid - g * TPG;             // my thread index inside the group
   const int ldr = a.ldr, d = a.d;
   const int col0 = 4 * tg;                  // my four columns
@@ -76,205 +99,215 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     s_skip = (*reinterpret_cast<volatile int*>(a.status) & LSF_ERR_NONFINITE) != 0;
   }
   __syncthreads();
-  // per-column constants, as column pairs (col0, col0 + 1), (col0 + 2, col0 + 3)
-  float Ap[4], Wp[4][D];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int k = col0 + e;
-    if (k < a.r) {
-      float nrm = 0.f;
-#pragma unroll
-      for (int dd = 0; dd < D; ++dd) {
-        const float u = (dd < d) ? a.U[static_cast<int64_t>(k) * d + dd] : 0.f;
-        nrm = fmaf(u, u, nrm);
-        Wp[e][dd] = kLog2e * (2.f * a.two_over_eps) * u;
-      }
-      Ap[e] = kLog2e * (a.c[k] - a.two_over_eps * nrm);
-    } else {
-#pragma unroll
-      for (int dd = 0; dd < D; ++dd) Wp[e][dd] = 0.f;
-      Ap[e] = -INFINITY;  // ex2(-inf) = 0: padded columns carry no mass
-    }
-  }
-  float2 A2[2], W2[2][D];
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    A2[p] = make_float2(Ap[2 * p], Ap[2 * p + 1]);
-#pragma unroll
-    for (int dd = 0; dd < D; ++dd) W2[p][dd] = make_float2(Wp[2 * p][dd], Wp[2 * p + 1][dd]);
-  }
-  float t[NRHS][4];
-  float2 t2[NRHS][2], acc2[NRHS][2];
+  const int64_t nbatch = s_skip ? 0 : (a.n + RPB - 1) / RPB;
   double res[NRHS];
-  bool has_old[NRHS];
+  float2 acc2[NRHS][2];
 #pragma unroll
   for (int k = 0; k < NRHS; ++k) {
     res[k] = 0.0;
-    has_old[k] = a.rhs[k].old != nullptr;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int col = col0 + e;
-      t[k][e] = (!kAx && col < ldr) ? a.rhs[k].t_in[col] : 0.f;
-    }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      t2[k][p] = make_float2(t[k][2 * p], t[k][2 * p + 1]);
-      acc2[k][p] = make_float2(0.f, 0.f);
-    }
+    acc2[k][0] = acc2[k][1] = make_float2(0.f, 0.f);
   }
   int flag = 0;
 
-  const int64_t nbatch = s_skip ? 0 : (a.n + RPB - 1) / RPB;
-  // register prefetch of one row's record by threads tid < RPB
-  float4 pre[SV];
-  auto load_rows = [&](int64_t b) {
-    if (tid >= RPB) return;
-    const int64_t i = b * RPB + tid;
-    float rec[4 * SV];
+  if (service) {
+    // ---- service warp: row records in, scalings out ----
+    bool has_old[NRHS];
 #pragma unroll
-    for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
-    if (b < nbatch && i < a.n) {
-      float nrm = 0.f;
+    for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    constexpr int kPer = (RPB + 31) / 32;  // rows per lane
+    float4 pre[kPer][SV];
+    auto load_rows = [&](int64_t b) {
 #pragma unroll
-      for (int dd = 0; dd < D; ++dd) {
-        const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
-        rec[2 * dd] = x;
-        rec[2 * dd + 1] = x;
-        nrm = fmaf(x, x, nrm);
+      for (int u = 0; u < kPer; ++u) {
+        const int rr = lane + 32 * u;
+        const int64_t i = b * RPB + rr;
+        float rec[4 * SV];
+#pragma unroll
+        for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
+        if (b < nbatch && i < a.n) {
+          float nrm = 0.f;
+#pragma unroll
+          for (int dd = 0; dd < D; ++dd) {
+            const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
+            rec[2 * dd] = x;
+            rec[2 * dd + 1] = x;
+            nrm = fmaf(x, x, nrm);
+          }
+          rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) {
+            rec[4 * XV + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
+            rec[4 * XV + 2 * k + 1] = has_old[k] ? a.rhs[k].old[i] : 0.f;
+          }
+        } else {
+          rec[2 * D] = rec[2 * D + 1] = -INFINITY;  // rows past the end carry no mass
+        }
+#pragma unroll
+        for (int v = 0; v < SV; ++v)
+          pre[u][v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
       }
-      rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
+    };
+    auto park_rows = [&](int bf) {
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k) {
-        rec[4 * XV + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
-        rec[4 * XV + 2 * k + 1] = has_old[k] ? a.rhs[k].old[i] : 0.f;
+      for (int u = 0; u < kPer; ++u) {
+        const int rr = lane + 32 * u;
+        if (rr < RPB)
+#pragma unroll
+          for (int v = 0; v < SV; ++v) s_rows[bf][rr * SV + v] = pre[u][v];
       }
-    } else {
-      rec[2 * D] = rec[2 * D + 1] = -INFINITY;  // rows past the end carry no mass
-    }
-#pragma unroll
-    for (int v = 0; v < SV; ++v) pre[v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
-  };
-  auto park_rows = [&](int bf) {
-    if (tid >= RPB) return;
-#pragma unroll
-    for (int v = 0; v < SV; ++v) s_rows[bf][tid * SV + v] = pre[v];
-  };
-  // the new scaling of one row (Update), its residual term, status and output
-  auto finish_row = [&](int k, int64_t i, float s, float wi, float oi) -> float {
-    if (has_old[k])
-      res[k] += fabs(static_cast<double>(oi) * static_cast<double>(s) - static_cast<double>(wi));
-    if (!kUpd) return 0.f;
-    const float sc = wi * __frcp_rn(s);
-    a.rhs[k].out[i] = sc;
-    if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
-    return sc;
-  };
-
-  // prime the ring with the first two batches
-  load_rows(blockIdx.x);
-  park_rows(0);
-  load_rows(static_cast<int64_t>(blockIdx.x) + gridDim.x);
-  park_rows(1);
-  __syncthreads();
-  int it = 0;
-  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
-    load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight while this batch computes
-    const float4* rows = s_rows[it % 3];
-    const int64_t row0 = b * RPB;
-    float2 F[kRcRB][2];  // the row's four entries as two column pairs
-    float dots[NRHS][kRcRB];
-#pragma unroll
-    for (int q = 0; q < kRcRB; ++q) {
-      const float4* rw = rows + (g * kRcRB + q) * SV;
-      float2 xb[2 * XV];  // (x_dd, x_dd) for dd < D, then (B, B)
-#pragma unroll
-      for (int v = 0; v < XV; ++v) {
-        const float4 f4 = rw[v];
-        xb[2 * v] = make_float2(f4.x, f4.y);
-        xb[2 * v + 1] = make_float2(f4.z, f4.w);
-      }
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float2 E = __fadd2_rn(A2[p], xb[D]);
-#pragma unroll
-        for (int dd = 0; dd < D; ++dd) E = __ffma2_rn(xb[dd], W2[p][dd], E);
-        F[q][p] = make_float2(ex2_approx(E.x), ex2_approx(E.y));
-      }
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) {
-        const float2 P = __ffma2_rn(F[q][0], t2[k][0], __fmul2_rn(F[q][1], t2[k][1]));
-        dots[k][q] = P.x + P.y;
-      }
-    }
-    float sc[NRHS][kRcRB];
-    const int q = lane >> 2;
-    const bool lead = (lane & 3) == 0;
-    if (kAx) {
-#pragma unroll
-      for (int qq = 0; qq < kRcRB; ++qq) {
-        const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
-        sc[0][qq] = wo.y;
-        if (NRHS > 1) sc[NRHS - 1][qq] = wo.w;
-      }
+    };
+    // prime the ring with the first two batches
+    load_rows(blockIdx.x);
+    park_rows(0);
+    load_rows(static_cast<int64_t>(blockIdx.x) + gridDim.x);
+    park_rows(1);
+    __syncthreads();
+    int it = 0;
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+      load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight across the barrier
       __syncthreads();
-    } else if (GW == 1) {
-      // warp partials of the 8 rows: lanes 4q .. 4q + 3 hold row q; a group is one
-      // warp, so its quad leaders finish the rows
-      float v[NRHS];
+      if (!kAx) {
+        // the batch's records: row sums from the group partials (the same fixed
+        // order the compute warps use), new scalings, residual terms, status
+        const float4* rows = s_rows[it % 3];
+        const int64_t row0 = b * RPB;
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
-      const int64_t i = row0 + g * kRcRB + q;
-      const float4 wo = rows[(g * kRcRB + q) * SV + XV];
-      float mine[NRHS];
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) {
-        mine[k] = 0.f;
-        if (lead && i < a.n) mine[k] = finish_row(k, i, v[k], k == 0 ? wo.x : wo.z, k == 0 ? wo.y : wo.w);
-      }
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k)
-#pragma unroll
-        for (int qq = 0; qq < kRcRB; ++qq) sc[k][qq] = __shfl_sync(0xffffffffu, mine[k], qq << 2);
-      __syncthreads();
-    } else {
-      float v[NRHS];
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
-      if (lead)
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) s_red[it & 1][k][q][warp] = v[k];
-      __syncthreads();
-      // every warp of the group: lane (k, qq) sums the group's warps for row qq, in order
-      const int kq = lane >> 3, qq = lane & 7;
-      float scl = 0.f;
-      if (kq < NRHS) {
-        const float* pr = &s_red[it & 1][kq][qq][g * GW];
-        float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < GW; ++w) s += pr[w];
-        const int64_t i = row0 + g * kRcRB + qq;
-        if (i < a.n) {
-          const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
-          const float wi = (NRHS == 1 || kq == 0) ? wo.x : wo.z;
-          const float oi = (NRHS == 1 || kq == 0) ? wo.y : wo.w;
-          if (warp == g * GW) {
-            // the group's first warp records the row (compile-time rhs index)
-            if (NRHS == 1 || kq == 0) scl = finish_row(0, i, s, wi, oi);
-            else scl = finish_row(NRHS - 1, i, s, wi, oi);
-          } else if (kUpd) {
-            scl = wi * __frcp_rn(s);
+        for (int item0 = 0; item0 < kItems; item0 += 32) {
+          const int item = item0 + lane;
+          if (item < kItems) {
+            const int gg = item / (NRHS * kRcRB), kq = (item / kRcRB) % NRHS, qq = item % kRcRB;
+            const int64_t i = row0 + gg * kRcRB + qq;
+            if (i < a.n) {
+              const float s = sum_partials<GW>(&s_red[it & 1][kq][qq][gg * GW]);
+              const float4 wo = rows[(gg * kRcRB + qq) * SV + XV];
+              // compile-time rhs index on each side of the branch
+              if (NRHS == 1 || kq == 0) {
+                if (has_old[0])
+                  res[0] += fabs(static_cast<double>(wo.y) * static_cast<double>(s) - static_cast<double>(wo.x));
+                if (kUpd) {
+                  const float sc = wo.x * __frcp_rn(s);
+                  a.rhs[0].out[i] = sc;
+                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
+                }
+              } else {
+                if (has_old[NRHS - 1])
+                  res[NRHS - 1] +=
+                      fabs(static_cast<double>(wo.w) * static_cast<double>(s) - static_cast<double>(wo.z));
+                if (kUpd) {
+                  const float sc = wo.z * __frcp_rn(s);
+                  a.rhs[NRHS - 1].out[i] = sc;
+                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
+                }
+              }
+            }
           }
         }
       }
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k)
-#pragma unroll
-        for (int r8 = 0; r8 < kRcRB; ++r8) sc[k][r8] = __shfl_sync(0xffffffffu, scl, k * 8 + r8);
+      // the batch two ahead goes to the slot the compute warps last read in the
+      // previous batch (before this barrier)
+      park_rows((it + 2) % 3);
     }
-    // after this batch's barrier: park the batch two ahead (its ring slot was last
-    // read in the previous batch, before that barrier)
-    park_rows((it + 2) % 3);
-    if (!kDt) {
+  } else {
+    // ---- compute warps ----
+    // per-column constants, as column pairs (col0, col0 + 1), (col0 + 2, col0 + 3)
+    float2 A2[2], W2[2][D];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      float Ap[2], Wp[2][D];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = col0 + 2 * p + h;
+        if (k < a.r) {
+          float nrm = 0.f;
+#pragma unroll
+          for (int dd = 0; dd < D; ++dd) {
+            const float u = (dd < d) ? a.U[static_cast<int64_t>(k) * d + dd] : 0.f;
+            nrm = fmaf(u, u, nrm);
+            Wp[h][dd] = kLog2e * (2.f * a.two_over_eps) * u;
+          }
+          Ap[h] = kLog2e * (a.c[k] - a.two_over_eps * nrm);
+        } else {
+#pragma unroll
+          for (int dd = 0; dd < D; ++dd) Wp[h][dd] = 0.f;
+          Ap[h] = -INFINITY;  // ex2(-inf) = 0: padded columns carry no mass
+        }
+      }
+      A2[p] = make_float2(Ap[0], Ap[1]);
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) W2[p][dd] = make_float2(Wp[0][dd], Wp[1][dd]);
+    }
+    float2 t2[NRHS][2];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int c = col0 + 2 * p;
+        t2[k][p] = make_float2((!kAx && c < ldr) ? a.rhs[k].t_in[c] : 0.f,
+                               (!kAx && c + 1 < ldr) ? a.rhs[k].t_in[c + 1] : 0.f);
+      }
+    __syncthreads();  // the ring is primed
+    int it = 0;
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+      const float4* rows = s_rows[it % 3];
+      float2 F[kRcRB][2];  // the row's four entries as two column pairs
+      float dots[NRHS][kRcRB];
+#pragma unroll
+      for (int q = 0; q < kRcRB; ++q) {
+        const float4* rw = rows + (g * kRcRB + q) * SV;
+        float2 xb[2 * XV];  // (x_dd, x_dd) for dd < D, then (B, B)
+#pragma unroll
+        for (int v = 0; v < XV; ++v) {
+          const float4 f4 = rw[v];
+          xb[2 * v] = make_float2(f4.x, f4.y);
+          xb[2 * v + 1] = make_float2(f4.z, f4.w);
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          float2 E = __fadd2_rn(A2[p], xb[D]);
+#pragma unroll
+          for (int dd = 0; dd < D; ++dd) E = __ffma2_rn(xb[dd], W2[p][dd], E);
+          F[q][p] = make_float2(ex2_approx(E.x), ex2_approx(E.y));
+        }
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          const float2 P = __ffma2_rn(F[q][0], t2[k][0], __fmul2_rn(F[q][1], t2[k][1]));
+          dots[k][q] = P.x + P.y;
+        }
+      }
+      if (!kAx) {
+        // warp partials of the 8 rows: lanes 4q .. 4q + 3 hold row q after the fold
+        float v[NRHS];
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) v[k] = fold_rows<kRcRB>(dots[k], lane, OpAdd());
+        if ((lane & 3) == 0)
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) s_red[it & 1][k][lane >> 2][warp] = v[k];
+      }
+      __syncthreads();
+      if (kDt) continue;
+      float sc[NRHS][kRcRB];
+      if (kAx) {
+#pragma unroll
+        for (int qq = 0; qq < kRcRB; ++qq) {
+          const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
+          sc[0][qq] = wo.y;
+          if (NRHS > 1) sc[NRHS - 1][qq] = wo.w;
+        }
+      } else {
+        // lane (kq, qq) forms the scaling of row qq of rhs kq from the group's
+        // partials, in the order the service warp uses
+        const int kq = lane >> 3, qq = lane & 7;
+        float scl = 0.f;  // rows past the end: 0 (their weight over their zero sum is NaN)
+        if (kq < NRHS && b * RPB + g * kRcRB + qq < a.n) {
+          const float s = sum_partials<GW>(&s_red[it & 1][kq][qq][g * GW]);
+          const float4 wo = rows[(g * kRcRB + qq) * SV + XV];
+          scl = ((NRHS == 1 || kq == 0) ? wo.x : wo.z) * __frcp_rn(s);
+        }
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+          for (int r8 = 0; r8 < kRcRB; ++r8) sc[k][r8] = __shfl_sync(0xffffffffu, scl, k * 8 + r8);
+      }
 #pragma unroll
       for (int k = 0; k < NRHS; ++k)
 #pragma unroll
@@ -287,7 +320,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   }
 
   // partials: group g writes its columns into s_part[g][k][col]
-  if (!kDt) {
+  if (!kDt && !service) {
 #pragma unroll
     for (int k = 0; k < NRHS; ++k)
 #pragma unroll
@@ -297,8 +330,8 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
         if (col < ldr) s_part[static_cast<size_t>(g) * NRHS * ldr + k * ldr + col] = v;
       }
   }
-  // residual terms live in the threads that finished rows: per-warp sums, then
-  // all warps into slot 0 in order (the other slots zero)
+  // residual terms live in the service warp: per-warp sums, then all warps into
+  // slot 0 in order (the other slots zero)
 #pragma unroll
   for (int k = 0; k < NRHS; ++k) {
     double r = res[k];
@@ -311,9 +344,9 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   if (tid == 0) {
     for (int k = 0; k < NRHS; ++k) {
       double r = 0.0;
-      for (int w = 0; w < kRcWarps; ++w) r += s_res[w][k];
+      for (int w = 0; w <= kRcWarps; ++w) r += s_res[w][k];
       s_res[0][k] = r;
-      for (int w = 1; w < kRcWarps; ++w) s_res[w][k] = 0.0;
+      for (int w = 1; w <= kRcWarps; ++w) s_res[w][k] = 0.0;
     }
   }
   __syncthreads();
