@@ -13,8 +13,14 @@
 // Layout is that of the stored pass (same copy ring; a warp takes RW = 8/C rows at
 // full width): the RW row maxima and then the shifted row sums are folded across
 // the warp by the multi-row butterfly; the column side keeps a running (max, sum)
-// pair per column, updated online with one ex2 per entry, and warps then CTAs are
-// merged in a fixed order at the end. A two right-hand-side pass at C >= 4 runs as
+// pair per column, updated online as m' = max(m, y), s' = s e^(m - m') +
+// e^(y - m') (two exponentials and no branch: one of the two is exactly 1, so
+// this equals the one-exponential update with a branch on the sign of y - m, in
+// fewer instructions), and warps then CTAs are merged in a fixed order at the
+// end. Every exponent is a difference taken in natural units before the scaling
+// by log2(e) (exact near the maximum), so no rounding is shared by all the terms
+// of a sum. The FP32 arithmetic runs on column pairs with the packed two-lane
+// instructions (add/mul/fma .f32x2). A two right-hand-side pass at C >= 4 runs as
 // two one-RHS launches: two (max, sum) states per column would not fit in
 // registers, and the pass is bound by ex2, not by the second read of F.
 #include <cuda_runtime.h>
@@ -57,7 +63,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
   __syncthreads();
 
   int flag = 0;
-  float lm[NRHS][C][4], ls[NRHS][C][4];  // running column (max, sum)
+  // running column (max, sum), as column pairs
+  float2 lm[NRHS][C][2], ls[NRHS][C][2];
   double res[NRHS];
 #pragma unroll
   for (int k = 0; k < NRHS; ++k) {
@@ -65,11 +72,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 #pragma unroll
     for (int j = 0; j < C; ++j)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        lm[k][j][e] = kLogFloor;
-        ls[k][j][e] = 0.f;
+      for (int h = 0; h < 2; ++h) {
+        lm[k][j][h] = make_float2(kLogFloor, kLogFloor);
+        ls[k][j][h] = make_float2(0.f, 0.f);
       }
   }
+  const float2 kL2 = make_float2(kLog2e, kLog2e);
+  const float2 kNeg1 = make_float2(-1.f, -1.f);
   if (warp == kConsumerWarps) {
     ring_produce<NRHS>(ring, a.F, a.n, a.ntiles, a.rhs, MODE != kPassAxpy, lane, flag);
   } else {
@@ -116,8 +125,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 #pragma unroll
               for (int j = 0; j < C; ++j) {
                 const float4 lt = *reinterpret_cast<const float4*>(&s_lt[k][4 * lane + 128 * j]);
-                m = fmaxf(m, fmaxf(fmaxf(f[q][j].x + lt.x, f[q][j].y + lt.y),
-                                   fmaxf(f[q][j].z + lt.z, f[q][j].w + lt.w)));
+                const float2 y0 = __fadd2_rn(make_float2(f[q][j].x, f[q][j].y), make_float2(lt.x, lt.y));
+                const float2 y1 = __fadd2_rn(make_float2(f[q][j].z, f[q][j].w), make_float2(lt.z, lt.w));
+                m = fmaxf(m, fmaxf(fmaxf(y0.x, y0.y), fmaxf(y1.x, y1.y)));
               }
               p[q] = m;
             }
@@ -125,16 +135,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
               const float mq = __shfl_sync(0xffffffffu, mrow, q << SH);
-              float sum = 0.f;
+              const float2 nm = make_float2(-mq, -mq);
+              float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
               for (int j = 0; j < C; ++j) {
                 const float4 lt = *reinterpret_cast<const float4*>(&s_lt[k][4 * lane + 128 * j]);
-                sum += ex2_approx((f[q][j].x + lt.x - mq) * kLog2e) +
-                       ex2_approx((f[q][j].y + lt.y - mq) * kLog2e) +
-                       ex2_approx((f[q][j].z + lt.z - mq) * kLog2e) +
-                       ex2_approx((f[q][j].w + lt.w - mq) * kLog2e);
+                const float2 y0 = __fadd2_rn(make_float2(f[q][j].x, f[q][j].y), make_float2(lt.x, lt.y));
+                const float2 y1 = __fadd2_rn(make_float2(f[q][j].z, f[q][j].w), make_float2(lt.z, lt.w));
+                const float2 e0 = __fmul2_rn(__fadd2_rn(y0, nm), kL2);
+                const float2 e1 = __fmul2_rn(__fadd2_rn(y1, nm), kL2);
+                sum = __fadd2_rn(sum, make_float2(ex2_approx(e0.x), ex2_approx(e0.y)));
+                sum = __fadd2_rn(sum, make_float2(ex2_approx(e1.x), ex2_approx(e1.y)));
               }
-              p[q] = sum;
+              p[q] = sum.x + sum.y;
             }
             const float srow = fold_rows<RW>(p, lane, OpAdd());
             const int row = rr + myq;
@@ -158,16 +171,26 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
             for (int q = 0; q < RW; ++q) fq[q] = __shfl_sync(0xffffffffu, fi, q << SH);
           }
           if (kAcc) {
-            // column side: online (max, sum) per column, one ex2 per entry
+            // column side: online (max, sum) per column
 #pragma unroll
-            for (int j = 0; j < C; ++j)
+            for (int q = 0; q < RW; ++q) {
+              const float2 fq2 = make_float2(fq[q], fq[q]);
 #pragma unroll
-              for (int q = 0; q < RW; ++q) {
-                lse_push(lm[k][j][0], ls[k][j][0], f[q][j].x + fq[q]);
-                lse_push(lm[k][j][1], ls[k][j][1], f[q][j].y + fq[q]);
-                lse_push(lm[k][j][2], ls[k][j][2], f[q][j].z + fq[q]);
-                lse_push(lm[k][j][3], ls[k][j][3], f[q][j].w + fq[q]);
-              }
+              for (int j = 0; j < C; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const float2 fp = h ? make_float2(f[q][j].z, f[q][j].w) : make_float2(f[q][j].x, f[q][j].y);
+                  const float2 y = __fadd2_rn(fp, fq2);
+                  float2& m = lm[k][j][h];
+                  const float2 mn = make_float2(fmaxf(m.x, y.x), fmaxf(m.y, y.y));
+                  // m - m' and y - m' (one of them is 0), in log2 units
+                  const float2 a1 = __fmul2_rn(__ffma2_rn(mn, kNeg1, m), kL2);
+                  const float2 a2 = __fmul2_rn(__ffma2_rn(mn, kNeg1, y), kL2);
+                  ls[k][j][h] = __ffma2_rn(ls[k][j][h], make_float2(ex2_approx(a1.x), ex2_approx(a1.y)),
+                                           make_float2(ex2_approx(a2.x), ex2_approx(a2.y)));
+                  m = mn;
+                }
+            }
           }
         }
       }
@@ -194,9 +217,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
           if (col < ldr) {
             float* rg = red + (static_cast<size_t>(warp) * NRHS + k) * 2 * ldr;
             *reinterpret_cast<float4*>(rg + col) =
-                make_float4(lm[k][j][0], lm[k][j][1], lm[k][j][2], lm[k][j][3]);
+                make_float4(lm[k][j][0].x, lm[k][j][0].y, lm[k][j][1].x, lm[k][j][1].y);
             *reinterpret_cast<float4*>(rg + ldr + col) =
-                make_float4(ls[k][j][0], ls[k][j][1], ls[k][j][2], ls[k][j][3]);
+                make_float4(ls[k][j][0].x, ls[k][j][0].y, ls[k][j][1].x, ls[k][j][1].y);
           }
         }
     }
