@@ -22,6 +22,9 @@ What it computes, in the paper's order and notation (Scetbon & Cuturi,
   v <- b/(K^T u) from v = 1 (one iteration = one u-half then one v-half); the
   reported residual is ||u o (K v) - a||_1 after the last v-half.
 * Eq. (6): W_hat = eps (a^T log u + b^T log v).
+* App. A.2: accelerated Sinkhorn, read as the accelerated alternating
+  minimisation the appendix cites (its listing is garbled; see
+  ``sinkhorn_accelerated``).
 * Eq. (2): debiased W_bar = W(a,b) - (W(a,a) + W(b,b))/2 with one shared theta.
 * Sec. 3.2 and its appendix lemma: the perturbed arc-cosine kernel k_s + kappa
   with features (sigma^{d/2} sqrt(2) max(0, u.x)^s exp(-||u||^2 (1 - 1/sigma^2)/4),
@@ -57,6 +60,8 @@ __all__ = [
     "sinkhorn_log",
     "sinkhorn_scaled",
     "sinkhorn_dense",
+    "dual_phi",
+    "sinkhorn_accelerated",
     "dual_estimate",
     "dual_objective",
     "primal_objective",
@@ -253,6 +258,96 @@ def sinkhorn_scaled(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray
     logu = np.log(u) - mx - M
     logv = np.log(v) - my + M
     return {"logu": logu, "logv": logv, "residual": residual}
+
+
+def dual_phi(Lx, Ly, a, b, eta1, eta2) -> float:
+    """phi(eta) = log <e^eta1, K e^eta2> - <eta1, a> - <eta2, b> (App. A.2, the dual
+    of Eq. (5) in the coordinates eta = (alpha, beta)/eps, sign flipped so that it
+    is minimised: W = -eps min phi)."""
+    logKv, _ = _log_Kv(Lx, Ly, eta2)
+    return float(lse(eta1 + logKv, axis=0) - eta1 @ a - eta2 @ b)
+
+
+def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray,
+                         iters: int, L0: float = 1.0) -> dict:
+    """Accelerated Sinkhorn (App. A.2) on K = exp(Lx) exp(Ly)^T in the log domain, FP64.
+
+    The appendix's listing is garbled (its interpolation mixes zeta with itself,
+    the function it differentiates is unnamed, the untouched block is assigned an
+    undefined iterate, L is halved twice); this follows the accelerated
+    alternating minimisation it cites (Guminov et al. 2019), restated:
+    minimise phi (``dual_phi``) from eta = zeta = 0, A = 0, with an estimate L of
+    the gradient's Lipschitz constant, halved at the start of every iteration and
+    doubled after every rejected attempt.  One attempt:
+        a_+  = 1/(2L) + sqrt(1/(4L^2) + A/L)      (the root of L a^2 = A + a)
+        tau  = a_+ / (A + a_+)
+        lam  = tau zeta + (1 - tau) eta
+        g    = grad phi(lam) = (P 1 - a, P^T 1 - b),  P = diag(e^lam1) K diag(e^lam2) / c
+        eta' = lam with the block of larger ||g_i|| replaced by its exact minimiser,
+               a Sinkhorn half-step: eta1' = log a - log K e^lam2 (block 1) or
+               eta2' = log b - log K^T e^lam1 (block 2)
+        accept when phi(eta') <= phi(lam) - ||g||^2 / (2 L).
+    After an accepted attempt zeta <- zeta - a_+ g, eta <- eta', A <- A + a_+.
+    The averaged primal plan of the listing (n x m) is not formed.
+
+    Returns log u = eta1, log v = eta2 after ``iters`` accepted iterations, the
+    value phi(eta) after each, A_k, L_k, the attempts of each iteration, the
+    blocks chosen, the smallest relative margins of the two decisions (block
+    choice, acceptance), and ||P 1 - a||_1 + ||P^T 1 - b||_1 at the final eta.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    loga, logb = np.log(a), np.log(b)
+    eta1, eta2 = np.zeros(Lx.shape[0]), np.zeros(Ly.shape[0])
+    zeta1, zeta2 = eta1.copy(), eta2.copy()
+    A, L = 0.0, float(L0)
+    phis, As, Ls, attempts, blocks = [], [], [], [], []
+    block_margin, accept_margin = np.inf, np.inf
+    for _ in range(iters):
+        L = L / 2.0
+        tries = 0
+        while True:
+            tries += 1
+            an = 1.0 / (2.0 * L) + math.sqrt(1.0 / (4.0 * L * L) + A / L)
+            tau = an / (A + an)
+            lam1 = tau * zeta1 + (1.0 - tau) * eta1
+            lam2 = tau * zeta2 + (1.0 - tau) * eta2
+            logKv, _ = _log_Kv(Lx, Ly, lam2)       # log K e^lam2
+            logKtu, _ = _log_Kv(Ly, Lx, lam1)      # log K^T e^lam1
+            logc = float(lse(lam1 + logKv, axis=0))
+            g1 = np.exp(lam1 + logKv - logc) - a
+            g2 = np.exp(lam2 + logKtu - logc) - b
+            n1, n2 = float(g1 @ g1), float(g2 @ g2)
+            phi_lam = logc - lam1 @ a - lam2 @ b
+            blk = 1 if n1 >= n2 else 2
+            if blk == 1:
+                new1, new2 = loga - logKv, lam2
+            else:
+                new1, new2 = lam1, logb - logKtu
+            phi_new = dual_phi(Lx, Ly, a, b, new1, new2)
+            bound = phi_lam - (n1 + n2) / (2.0 * L)
+            if n1 + n2 > 0:
+                block_margin = min(block_margin, abs(n1 - n2) / (n1 + n2))
+            accept_margin = min(accept_margin, abs(phi_new - bound) / max(1.0, abs(bound)))
+            if phi_new <= bound:
+                break
+            L = 2.0 * L
+        zeta1, zeta2 = zeta1 - an * g1, zeta2 - an * g2
+        eta1, eta2 = new1, new2
+        A += an
+        phis.append(phi_new)
+        As.append(A)
+        Ls.append(L)
+        attempts.append(tries)
+        blocks.append(blk)
+    logKv, _ = _log_Kv(Lx, Ly, eta2)
+    logKtu, _ = _log_Kv(Ly, Lx, eta1)
+    logc = float(lse(eta1 + logKv, axis=0))
+    residual = float(np.abs(np.exp(eta1 + logKv - logc) - a).sum()
+                     + np.abs(np.exp(eta2 + logKtu - logc) - b).sum())
+    return {"logu": eta1, "logv": eta2, "phi": phis, "A": As, "L": Ls, "attempts": attempts,
+            "blocks": blocks, "block_margin": block_margin, "accept_margin": accept_margin,
+            "residual": residual}
 
 
 def sinkhorn_dense(K: np.ndarray, a: np.ndarray, b: np.ndarray, iters: int) -> dict:

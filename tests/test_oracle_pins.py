@@ -455,3 +455,63 @@ def test_arccos_factored_sinkhorn_matches_dense_textbook():
     dense = o.sinkhorn_dense(K, a, b, 60)
     np.testing.assert_allclose(out["xy"]["logu"], dense["logu"], rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(out["W_xy"], o.dual_estimate(a, b, dense["logu"], dense["logv"], 1.0), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Accelerated Sinkhorn (App. A.2, read as accelerated alternating minimisation)
+# --------------------------------------------------------------------------
+
+def _acc_case(seed, n, m, d, r, eps):
+    p = synth.small_problem(seed, n, m, d, r, eps, 10, weights="dirichlet")
+    th = o.make_theta(p.X, p.Y, p.Z, p.eps)
+    return p, o.log_features(p.X, th.U, p.eps, th.q), o.log_features(p.Y, th.U, p.eps, th.q)
+
+
+ACC_CASES = [(1, 60, 50, 2, 40, 0.5), (2, 80, 70, 3, 64, 0.1), (3, 100, 90, 2, 100, 0.05)]
+
+
+@pytest.mark.parametrize("seed,n,m,d,r,eps", ACC_CASES)
+def test_accelerated_reaches_the_sinkhorn_optimum(seed, n, m, d, r, eps):
+    # both methods solve the same dual problem: the limit is the converged W of Alg. 1
+    p, Lx, Ly = _acc_case(seed, n, m, d, r, eps)
+    ref = o.sinkhorn_log(Lx, Ly, p.a, p.b, 4000)
+    W_star = o.dual_estimate(p.a, p.b, ref["logu"], ref["logv"], eps)
+    acc = o.sinkhorn_accelerated(Lx, Ly, p.a, p.b, 600)
+    W = o.dual_estimate(p.a, p.b, acc["logu"], acc["logv"], eps)
+    assert abs(W - W_star) <= 1e-7 * abs(W_star)
+    assert acc["residual"] <= 1e-3
+    # the reported value is Eq. (6) at a point whose plan has the mass of the
+    # fitted marginal (1 up to the FP32 rounding of the stored weights)
+    mass = max(abs(math.log(float(np.sum(p.a, dtype=np.float64)))),
+               abs(math.log(float(np.sum(p.b, dtype=np.float64)))))
+    assert abs(-eps * acc["phi"][-1] - W) <= eps * mass + 1e-12 * abs(W)
+
+
+@pytest.mark.parametrize("seed,n,m,d,r,eps", ACC_CASES)
+def test_accelerated_values_obey_duality_and_the_estimate_sequence_bound(seed, n, m, d, r, eps):
+    # every accepted point is dual feasible: -eps phi <= W* (weak duality); and the
+    # accelerated analysis gives phi(eta_k) - phi* <= ||eta* - eta_0||^2 / (2 A_k)
+    # for the optimal point eta* nearest the start eta_0 = 0 (optimal points differ
+    # by a shift (c, -c) of the two blocks)
+    p, Lx, Ly = _acc_case(seed, n, m, d, r, eps)
+    ref = o.sinkhorn_log(Lx, Ly, p.a, p.b, 4000)
+    phi_star = o.dual_phi(Lx, Ly, p.a, p.b, ref["logu"], ref["logv"])
+    e1, e2 = ref["logu"], ref["logv"]
+    c = (e2.sum() - e1.sum()) / (len(e1) + len(e2))
+    R2 = float(((e1 + c) ** 2).sum() + ((e2 - c) ** 2).sum())
+    acc = o.sinkhorn_accelerated(Lx, Ly, p.a, p.b, 200)
+    gaps = np.asarray(acc["phi"]) - phi_star
+    assert np.all(gaps >= -1e-10)
+    assert np.all(gaps <= R2 / (2.0 * np.asarray(acc["A"])))
+    # A_k grows at least like k^2 / (8 L_max) when L never exceeds L_max
+    k = np.arange(1, len(acc["A"]) + 1)
+    assert np.all(np.asarray(acc["A"]) >= k ** 2 / (8.0 * max(acc["L"]) * 4.0))
+
+
+def test_accelerated_single_point_is_the_closed_form():
+    # n = m = 1: phi(eta) = log K for every eta, so W = -eps log K (Eq. 7) at once
+    p, Lx, Ly = _acc_case(5, 1, 1, 2, 16, 0.3)
+    logK = float(o.lse(Lx[0] + Ly[0], axis=0))
+    acc = o.sinkhorn_accelerated(Lx, Ly, p.a, p.b, 5)
+    W = o.dual_estimate(p.a, p.b, acc["logu"], acc["logv"], 0.3)
+    assert abs(W - (-0.3 * logK)) <= 1e-12 * abs(logK)
