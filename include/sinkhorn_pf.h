@@ -434,6 +434,52 @@ int lsf_set_small_solver(int policy, int64_t max_entries);
 
 /* ---------------------------------------------------------------- measurement */
 
+/* ---------------------------------------------------------------- accelerated */
+
+/* Statistics of an accelerated solve (host memory, filled on return). */
+typedef struct {
+  int32_t iters;     /* accepted iterations                                   */
+  int32_t attempts;  /* line-search attempts (three log-domain passes each)   */
+  double A;          /* A_k after the last iteration (the estimate sequence)  */
+  double L;          /* Lipschitz estimate of the last accepted attempt       */
+} lsf_accel_info;
+
+/*
+ * Bytes of workspace lsf_solve_accelerated needs for n points in x, m in y and
+ * row stride ldr: the pass workspace of lsf_workspace_bytes(ldr) followed by
+ * six n-vectors, six m-vectors, two r-vectors and the reduction partials.
+ */
+int lsf_accel_workspace_bytes(int64_t n, int64_t m, int ldr, size_t* bytes);
+
+/*
+ * Accelerated Sinkhorn (App. A.2) on the factored kernel, log domain only. The
+ * appendix's listing is garbled; this follows the accelerated alternating
+ * minimisation it cites: minimise phi(eta) = log <e^eta1, K e^eta2> -
+ * <eta1, a> - <eta2, b> (W = -eps min phi) from eta = zeta = 0 with an estimate
+ * sequence and an adaptive Lipschitz estimate L (starting at L0 > 0, halved at
+ * every iteration, doubled after every rejected attempt). An attempt
+ * interpolates lam = tau zeta + (1 - tau) eta, takes the gradient
+ * (P 1 - a, P^T 1 - b) at lam, refits the block with the larger gradient norm by
+ * a Sinkhorn half-step and accepts when phi drops by ||g||^2/(2L); then
+ * zeta -= a_k g. Each attempt is three log-domain passes (x->F, y->F hold log
+ * features from lsf_log_features) and four small kernels.
+ *
+ * Writes out->u = log u~ = eta1 + x->shift and out->v = log v~ = eta2 + y->shift
+ * (the LSF_MODE_LOG conventions, so lsf_divergence(..., LSF_MODE_LOG) gives
+ * Eq. (6) at the final point), out->t_u, out->t_v (log r-vectors at that point),
+ * result->residual = ||P 1 - a||_1 + ||P^T 1 - b||_1 there, result->iters, and
+ * *info (may be NULL). An iteration with more than 30 attempts ends the solve
+ * early (the required decrease is below the rounding of phi: the point is
+ * stationary to working precision); result->iters and info->iters then count
+ * the iterations done. Synchronises `stream` once per attempt (the host reads
+ * the acceptance decision). Errors: LSF_ERR_ARG for iters < 1 or L0 not
+ * positive, LSF_ERR_WORKSPACE below lsf_accel_workspace_bytes,
+ * LSF_ERR_NONFINITE when a dual value is not finite.
+ */
+int lsf_solve_accelerated(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
+                          double L0, const lsf_scalings* out, lsf_result* result,
+                          lsf_accel_info* info, void* workspace, size_t ws_bytes, void* stream);
+
 /* Kernel classes timed by the optional event recorder. */
 typedef enum {
   LSF_KERNEL_PASS = 0,       /* fused Sinkhorn passes (stored features)   */

@@ -268,6 +268,9 @@ def dual_phi(Lx, Ly, a, b, eta1, eta2) -> float:
     return float(lse(eta1 + logKv, axis=0) - eta1 @ a - eta2 @ b)
 
 
+MAX_ATTEMPTS = 30  # line-search attempts per accelerated iteration before stopping
+
+
 def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray,
                          iters: int, L0: float = 1.0) -> dict:
     """Accelerated Sinkhorn (App. A.2) on K = exp(Lx) exp(Ly)^T in the log domain, FP64.
@@ -288,12 +291,18 @@ def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.nd
                eta2' = log b - log K^T e^lam1 (block 2)
         accept when phi(eta') <= phi(lam) - ||g||^2 / (2 L).
     After an accepted attempt zeta <- zeta - a_+ g, eta <- eta', A <- A + a_+.
+    An iteration that needs more than ``MAX_ATTEMPTS`` attempts ends the run: the
+    required decrease has fallen below what the arithmetic resolves, i.e. eta is
+    stationary to working precision (``stopped`` is then set and fewer than
+    ``iters`` iterations are reported).
     The averaged primal plan of the listing (n x m) is not formed.
 
     Returns log u = eta1, log v = eta2 after ``iters`` accepted iterations, the
     value phi(eta) after each, A_k, L_k, the attempts of each iteration, the
     blocks chosen, the smallest relative margins of the two decisions (block
-    choice, acceptance), and ||P 1 - a||_1 + ||P^T 1 - b||_1 at the final eta.
+    choice over the attempts without an exact tie, acceptance), the number of
+    exact ties (block 1 is taken), the largest |entry| of zeta and eta over
+    the run, and ||P 1 - a||_1 + ||P^T 1 - b||_1 at the final eta.
     """
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -303,10 +312,15 @@ def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.nd
     A, L = 0.0, float(L0)
     phis, As, Ls, attempts, blocks = [], [], [], [], []
     block_margin, accept_margin = np.inf, np.inf
+    ties = 0
+    vmax = 0.0  # largest |entry| of zeta and eta over the run
+    stopped = False
     for _ in range(iters):
+        L_prev = L
         L = L / 2.0
         tries = 0
-        while True:
+        accepted = False
+        while tries < MAX_ATTEMPTS:
             tries += 1
             an = 1.0 / (2.0 * L) + math.sqrt(1.0 / (4.0 * L * L) + A / L)
             tau = an / (A + an)
@@ -326,14 +340,23 @@ def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.nd
                 new1, new2 = lam1, logb - logKtu
             phi_new = dual_phi(Lx, Ly, a, b, new1, new2)
             bound = phi_lam - (n1 + n2) / (2.0 * L)
-            if n1 + n2 > 0:
+            if n1 == n2:
+                ties += 1  # exact: blocks holding the same data (self terms of Eq. (2))
+            elif n1 + n2 > 0:
                 block_margin = min(block_margin, abs(n1 - n2) / (n1 + n2))
             accept_margin = min(accept_margin, abs(phi_new - bound) / max(1.0, abs(bound)))
             if phi_new <= bound:
+                accepted = True
                 break
             L = 2.0 * L
+        if not accepted:
+            stopped = True
+            L = L_prev
+            break
         zeta1, zeta2 = zeta1 - an * g1, zeta2 - an * g2
         eta1, eta2 = new1, new2
+        vmax = max(vmax, float(np.abs(zeta1).max()), float(np.abs(zeta2).max()),
+                   float(np.abs(eta1).max()), float(np.abs(eta2).max()))
         A += an
         phis.append(phi_new)
         As.append(A)
@@ -347,7 +370,8 @@ def sinkhorn_accelerated(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.nd
                      + np.abs(np.exp(eta2 + logKtu - logc) - b).sum())
     return {"logu": eta1, "logv": eta2, "phi": phis, "A": As, "L": Ls, "attempts": attempts,
             "blocks": blocks, "block_margin": block_margin, "accept_margin": accept_margin,
-            "residual": residual}
+            "residual": residual, "iters": len(phis), "stopped": stopped, "ties": ties,
+            "vmax": vmax}
 
 
 def sinkhorn_dense(K: np.ndarray, a: np.ndarray, b: np.ndarray, iters: int) -> dict:

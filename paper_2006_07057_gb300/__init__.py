@@ -23,7 +23,7 @@ import torch
 from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,  # noqa: F401
                        LSF_KERNEL_BATCHED, LSF_KERNEL_SMALL,
                        LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
-                       LsfBatchInfo, LsfBatchProblem,
+                       LsfAccelInfo, LsfBatchInfo, LsfBatchProblem,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
                        LsfArccos, LsfTheta, check, header_symbols, lib)
@@ -271,6 +271,33 @@ def lsf_solve(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, out: Scal
                           workspace.numel(), _stream(stream)), "lsf_solve")
 
 
+def lsf_accel_workspace_bytes(n: int, m: int, ldr: int) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().lsf_accel_workspace_bytes(int(n), int(m), int(ldr), ctypes.byref(b)),
+          "lsf_accel_workspace_bytes")
+    return int(b.value)
+
+
+def alloc_accel_workspace(n: int, m: int, ldr: int, device) -> torch.Tensor:
+    nbytes = lsf_accel_workspace_bytes(n, m, ldr)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + nbytes]
+
+
+def lsf_solve_accelerated(theta: Theta, x: Cloud, y: Cloud, iters: int, out: Scalings, result,
+                          workspace, L0: float = 1.0, stream=None) -> dict:
+    """Accelerated Sinkhorn (App. A.2) in the log domain; returns the line-search
+    statistics (iters, attempts, A, L). Synchronises the stream once per attempt."""
+    th, cx, cy, so = theta.as_c(), x.as_c(), y.as_c(), out.as_c()
+    info = LsfAccelInfo()
+    check(lib().lsf_solve_accelerated(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy),
+                                      int(iters), float(L0), ctypes.byref(so), _p(result),
+                                      ctypes.byref(info), _p(workspace), workspace.numel(),
+                                      _stream(stream)), "lsf_solve_accelerated")
+    return {"iters": info.iters, "attempts": info.attempts, "A": info.A, "L": info.L}
+
+
 def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, out: Scalings,
                       result, stream=None):
     """lsf_solve without a workspace, for callers that cannot allocate device memory.
@@ -513,6 +540,34 @@ class SinkhornProblem:
                       self.workspace, self.stream)
             lsf_divergence(self.theta, [self.x], [self.y], [self.s_xy], [r0], [1.0], self.wbar,
                            self.workspace, self.stream, mode=self.mode)
+
+    def run_accelerated(self, iters: int, debiased: bool = True, L0: float = 1.0) -> list[dict]:
+        """Accelerated Sinkhorn (App. A.2) for each solve of the divergence, then Eq. (6)
+        (and Eq. (2)). Log domain only (``mode="log"``); synchronises once per
+        line-search attempt. Returns the line-search statistics of each solve."""
+        if self.mode != "log":
+            raise ValueError("the accelerated solver runs in the log domain (mode='log')")
+        self.debiased = bool(debiased)
+        self.iters = iters
+        n, m = self.x.n, self.y.n
+        if getattr(self, "_accel_ws", None) is None:
+            big = max(n, m)
+            self._accel_ws = alloc_accel_workspace(big, big, self.theta.ldr, self.X.device)
+        pairs = [(self.x, self.y, self.s_xy)]
+        if self.debiased:
+            pairs += [(self.x, self.x, self.s_xx), (self.y, self.y, self.s_yy)]
+        stats = []
+        for k, (cx, cy, s) in enumerate(pairs):
+            stats.append(lsf_solve_accelerated(self.theta, cx, cy, iters, s, self.result_view(k),
+                                               self._accel_ws, L0=L0, stream=self.stream))
+        xs = [p[0] for p in pairs]
+        ys = [p[1] for p in pairs]
+        coef = [1.0, -0.5, -0.5][:len(pairs)]
+        lsf_divergence(self.theta, xs, ys, [p[2] for p in pairs],
+                       [self.result_view(k) for k in range(len(pairs))], coef, self.wbar,
+                       self.workspace, self.stream, mode="log")
+        self.accel_stats = stats
+        return stats
 
     def values(self) -> dict:
         """Host copy of the results of the last run (synchronises)."""

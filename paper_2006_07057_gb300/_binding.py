@@ -81,6 +81,11 @@ class LsfBatchInfo(ctypes.Structure):
                 ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t),
                 ("strategy", c_int)]
 
+class LsfAccelInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("attempts", ctypes.c_int32), ("A", c_double),
+                ("L", c_double)]
+
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "lsf_version": (c_int, []),
@@ -100,6 +105,10 @@ _SIGNATURES = {
     "lsf_log_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
                                  c_void_p]),
     "lsf_workspace_bytes": (c_int, [c_int, _P(c_size_t)]),
+    "lsf_accel_workspace_bytes": (c_int, [c_int64, c_int64, c_int, _P(c_size_t)]),
+    "lsf_solve_accelerated": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double,
+                                      _P(LsfScalings), c_void_p, _P(LsfAccelInfo), c_void_p,
+                                      c_size_t, c_void_p]),
     "lsf_solve": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                           _P(LsfScalings), c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_divergence": (c_int, [_P(LsfTheta), c_int, _P(_P(LsfCloud)), _P(_P(LsfCloud)),

@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
   constexpr int RW = 8 / C;
   constexpr int SH = RowFold<RW>::kShift;
   constexpr bool kNeedT = MODE != kPassAxpy;
-  constexpr bool kAcc = MODE != kPassDot;
+  constexpr bool kAcc = MODE != kPassDot && MODE != kPassRows;
+  constexpr bool kRowsOut = MODE == kPassRows || MODE == kPassRowsAxpy;  // log s to `out`
+  constexpr bool kGivenF = MODE == kPassAxpy || MODE == kPassRowsAxpy;   // column side from `old`
   extern __shared__ __align__(128) unsigned char smem[];
   const int ldr = a.ldr;
   const Ring ring = ring_layout(smem, a.nstages, a.tile_rows, ldr);
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
   const float2 kL2 = make_float2(kLog2e, kLog2e);
   const float2 kNeg1 = make_float2(-1.f, -1.f);
   if (warp == kConsumerWarps) {
-    ring_produce<NRHS>(ring, a.F, a.n, a.ntiles, a.rhs, MODE != kPassAxpy, lane, flag);
+    ring_produce<NRHS>(ring, a.F, a.n, a.ntiles, a.rhs, MODE == kPassUpdate || MODE == kPassDot, lane, flag);
   } else {
     bool has_old[NRHS];
 #pragma unroll
@@ -152,7 +154,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
             const float srow = fold_rows<RW>(p, lane, OpAdd());
             const int row = rr + myq;
             float fi = -INFINITY;
-            if (row < rows) {
+            if (kRowsOut) {
+              if (row < rows && owner) a.rhs[k].out[row0 + row] = mrow + logf(srow);
+            } else if (row < rows) {
               const float logs = mrow + logf(srow);
               const float wi = vw[row];
               if (has_old[k] && owner)
@@ -167,8 +171,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
                 if (!isfinite(fi)) fi = -INFINITY;
               }
             }
+            if (kGivenF) {
 #pragma unroll
-            for (int q = 0; q < RW; ++q) fq[q] = __shfl_sync(0xffffffffu, fi, q << SH);
+              for (int q = 0; q < RW; ++q) fq[q] = (rr + q < rows) ? vold[rr + q] : -INFINITY;
+            } else {
+#pragma unroll
+              for (int q = 0; q < RW; ++q) fq[q] = __shfl_sync(0xffffffffu, fi, q << SH);
+            }
           }
           if (kAcc) {
             // column side: online (max, sum) per column
@@ -238,7 +247,13 @@ int launch_log_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, c
   void (*kern)(PassArgs) = nullptr;
   if (mode == kPassUpdate) kern = logpass_kernel<C, NRHS, kPassUpdate>;
   else if (mode == kPassAxpy) kern = logpass_kernel<C, NRHS, kPassAxpy>;
-  else kern = logpass_kernel<C, NRHS, kPassDot>;
+  else if (mode == kPassDot) kern = logpass_kernel<C, NRHS, kPassDot>;
+  else if constexpr (NRHS == 1) {
+    if (mode == kPassRows) kern = logpass_kernel<C, 1, kPassRows>;
+    else kern = logpass_kernel<C, 1, kPassRowsAxpy>;
+  } else {
+    return fail(LSF_ERR_UNSUPPORTED, "logpass: row-product modes take one right-hand side");
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "logpass: smem attribute: %s", cudaGetErrorString(e));

@@ -316,6 +316,8 @@ double pass_bytes(int mode, int nrhs, int64_t n, int ldr, bool with_old) {
   if (mode == kPassUpdate) per_row += nrhs * 4.0 * (2 + (with_old ? 1 : 0));  // w, out, old
   if (mode == kPassAxpy) per_row += nrhs * 4.0;                                // given scaling
   if (mode == kPassDot) per_row += nrhs * 8.0;                                 // w, old
+  if (mode == kPassRows) per_row += nrhs * 4.0;                                // out
+  if (mode == kPassRowsAxpy) per_row += nrhs * 8.0;                            // out, given scaling
   return per_row * static_cast<double>(n);
 }
 

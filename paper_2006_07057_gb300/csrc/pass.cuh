@@ -8,16 +8,19 @@ namespace lsf {
 enum PassMode : int {
   kPassUpdate = 0,  // s = F t; res += |old s - w|; new = w / s; t' += new F
   kPassAxpy = 1,    // t' += given F            (given scaling in `old`)
-  kPassDot = 2      // s = F t; res += |old s - w|  (no update)
+  kPassDot = 2,     // s = F t; res += |old s - w|  (no update)
+  // log-domain pass only (the products of the accelerated solver):
+  kPassRows = 3,     // out = log s, s = F t
+  kPassRowsAxpy = 4  // out = log s, s = F t; and t' = the transposed product with `old`
 };
 
 // One right-hand side of a pass: the r-vector it multiplies and what it updates.
 struct PassRhs {
-  const float* t_in;  // ldr   (Update, Dot)
+  const float* t_in;  // ldr   (Update, Dot, Rows, RowsAxpy)
   const float* w;     // n     weights (Update, Dot)
-  const float* old;   // n     previous scaling (residual) or the given scaling (Axpy); may be NULL in Update
-  float* out;         // n     new scaling (Update)
-  float* t_out;       // ldr   reduced F^T new (Update, Axpy)
+  const float* old;   // n     previous scaling (residual) or the given scaling (Axpy, RowsAxpy); may be NULL in Update
+  float* out;         // n     new scaling (Update) or log of the row product (Rows, RowsAxpy)
+  float* t_out;       // ldr   reduced F^T new (Update, Axpy, RowsAxpy)
   double* res_out;    // 1     residual sum |old s - w| (Update with old, Dot)
 };
 

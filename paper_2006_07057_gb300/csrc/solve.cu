@@ -8,6 +8,7 @@
 #include "pass.cuh"
 #include "recompute.cuh"
 #include "small.cuh"
+#include "solve.cuh"
 
 namespace lsf {
 namespace {
@@ -162,6 +163,8 @@ __global__ void __launch_bounds__(256) divergence_kernel(const DivArgs a) {
   *a.counter = 0u;
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------- validation
 
 int check_theta(const lsf_theta* th) {
@@ -201,12 +204,6 @@ int check_scalings(const lsf_scalings* s, const char* name) {
     return fail(LSF_ERR_ARG, "%s scalings: t_u, t_v must be 16-byte aligned", name);
   return LSF_OK;
 }
-
-#define LSF_TRY(expr)          \
-  do {                         \
-    int _rc = (expr);          \
-    if (_rc != LSF_OK) return _rc; \
-  } while (0)
 
 // One fused pass on one cloud in the chosen mode.
 int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int nrhs,
@@ -253,6 +250,8 @@ int start_solve(void* workspace, size_t ws_bytes, int ldr, lsf_result* result, i
     return fail(LSF_ERR_CUDA, "solve: memset failed");
   return LSF_OK;
 }
+
+namespace {
 
 int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double* ls_b, int mode,
               cudaStream_t st) {
