@@ -19,7 +19,7 @@ and the read-back of the result. ``roofline`` reports the dominant kernel of
 the reported variant (the fused pass) against the measured HBM copy bandwidth
 (stored) or the derived ex2 rate (recompute). ``cpu_baseline`` times the FP64
 oracle on a bounded sample of the same workload on the host cores. Other
-workloads: ``--workload tiny|diff|batched|serving|arccos|accel`` print their own line.
+workloads: ``--workload tiny|diff|batched|serving|arccos|accel|multi`` print their own line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batched", "serving", "diff", "tiny", "arccos", "accel"])
+                    choices=["large", "batched", "serving", "diff", "tiny", "arccos", "accel", "multi"])
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--slots", type=int, default=32)
@@ -644,6 +644,93 @@ def run_accel(args):
     return 0
 
 
+def run_multi(args):
+    """Many weight vectors on one support (the tensor-core pass): k = 16 pairs of
+    Dirichlet(1) weights on the large two-cloud shape (n = m = 2^20 in R^3, eps = 0.1,
+    r = 1024), 200 iterations of Alg. 1 for each pair and Eq. (6). A step = features,
+    their bf16 pair split, the multi-right-hand-side solve. Compared with the same 16
+    pairs solved one after another by the stored-feature single solve."""
+    import torch
+    import paper_2006_07057_gb300 as lsf
+    torch.cuda.set_device(0)
+    lsf.lib()
+    n = args.n
+    k = 16
+    p = synth.large_problem(seed=0, n=n, iters=args.iters)
+    rng = np.random.default_rng(7)
+    A = rng.exponential(size=(k, n))
+    B = rng.exponential(size=(k, n))
+    A = (A / A.sum(axis=1, keepdims=True)).astype(np.float32)
+    B = (B / B.sum(axis=1, keepdims=True)).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    t = {q: torch.from_numpy(getattr(p, q)).to(dev) for q in ("X", "Y", "Z")}
+    tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    stream = torch.cuda.current_stream()
+    holder = {}
+
+    def step():
+        prob = lsf.MultiSinkhornProblem(t["X"], t["Y"], tA, tB, t["Z"], p.eps)
+        prob.run(args.iters)
+        holder["prob"] = prob
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    vals = holder["prob"].values()
+    if any(v["status"] != 0 for v in vals):
+        raise SystemExit(f"multi solve reported status {[v['status'] for v in vals]}")
+    sampler = ClockSampler(0)
+    sampler.start()
+    lsf.lsf_profile_enable(True)
+    lsf.lsf_launch_count_reset()
+    ms = _timed(step, args.steps, stream)
+    launches = lsf.lsf_launch_count()
+    peak, peak_kind = load_peaks()
+    roof = _profile_roofline(lsf, lsf.LSF_KERNEL_PASS_MULTI,
+                             "multi_pass_kernel (tcgen05 bf16-pair passes, 16 right-hand sides)",
+                             peak, peak_kind, ms * args.steps)
+    feat_ms, _, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
+    lsf.lsf_profile_enable(False)
+    clocks = sampler.stop()
+
+    # the same pairs one after another through the single solve (stored features)
+    def sequential():
+        out = []
+        single = lsf.SinkhornProblem(t["X"], t["Y"], tA[0].contiguous(), tB[0].contiguous(),
+                                     t["Z"], p.eps, mode="stored")
+        for q in range(k):
+            single.x.w = tA[q].contiguous()
+            single.y.w = tB[q].contiguous()
+            single.run(args.iters, debiased=False)
+            out.append(single.values()["W_xy"])
+        return out
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_W = sequential()
+    torch.cuda.synchronize()
+    ms_seq = (time.perf_counter() - t0) * 1e3
+    worst = max(abs(v["W"] - w) / abs(w) for v, w in zip(vals, seq_W))
+    updates = k * args.iters * (p.n + p.m) * p.r
+    line = {
+        "metric": METRIC, "value": updates / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2/f32", "data": "synthetic",
+        "config": {"workload": f"{k} weight pairs (Dirichlet(1)) on one support: the large two-cloud "
+                               f"shape n=m={p.n}, d=3, eps={p.eps}, r={p.r}, {args.iters} iterations "
+                               f"per pair, Eq. (6) per pair; tensor-core multi-right-hand-side passes",
+                   "l2": "inputs larger than L2 (two 4 GiB bf16-pair feature matrices per pass)"},
+        "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
+        "features_ms_per_step": feat_ms / args.steps,
+        "sequential_single_solves_ms": ms_seq,
+        "speedup_vs_sequential": ms_seq / ms,
+        "max_rel_W_diff_vs_single": worst,
+        "result": {"W": [v["W"] for v in vals[:4]], "residual": [v["residual"] for v in vals[:4]]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -658,6 +745,8 @@ def main():
         return run_tiny(args)
     if args.workload == "accel":
         return run_accel(args)
+    if args.workload == "multi":
+        return run_multi(args)
     if args.workload == "arccos":
         return run_arccos(args)
     import torch

@@ -480,6 +480,61 @@ int lsf_solve_accelerated(const lsf_theta* theta, const lsf_cloud* x, const lsf_
                           double L0, const lsf_scalings* out, lsf_result* result,
                           lsf_accel_info* info, void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------ many weight vectors on one support */
+
+/*
+ * Features in the form the tensor-core pass reads (lsf_solve_multi): two bf16
+ * planes of n x ldr2 in one buffer, plane 0 (F2[0 .. n*ldr2)) hi = RN_bf16(F) and
+ * plane 1 (F2[n*ldr2 .. 2*n*ldr2)) lo = RN_bf16(F - hi), so that hi + lo equals
+ * the shifted features F of lsf_features to 2^-16 relative, in the same 4 bytes
+ * per entry. Columns r..ldr2-1 are zero. Row shifts are those of lsf_features.
+ * F: n x ldr FP32 (device); F2: 2 x n x ldr2 uint16 bf16 bit patterns (device,
+ * 256-byte aligned for lsf_solve_multi). ldr2 is a multiple of 128, <= 1024, >= r.
+ * Errors: LSF_ERR_ARG (NULL, n < 1, r outside [1, min(ldr, ldr2)]),
+ * LSF_ERR_UNSUPPORTED (ldr2).
+ */
+int lsf_split_features(const float* F, int64_t n, int ldr, int r, uint16_t* F2, int ldr2,
+                       void* stream);
+
+/* One cloud with k weight vectors (device pointers). */
+typedef struct {
+  const uint16_t* F2;   /* bf16 pair planes, 2 x n x ldr2 (lsf_split_features)       */
+  const float* shift;   /* n row log-shifts                                           */
+  const float* W;       /* k x n weights: row p is the p-th measure's weights         */
+  int64_t n;            /* number of points, >= 1                                     */
+} lsf_multi_cloud;
+
+/* Scalings of k solves on one support (device pointers, caller-owned). */
+typedef struct {
+  float* U;    /* k x n   u~ of each solve (the lsf_scalings conventions)             */
+  float* V;    /* k x m   v~                                                          */
+  float* Tu;   /* kp x ldr2 xi~^T u~ per solve, kp = 16 if k <= 16 else 32; rows k..kp-1 zero */
+  float* Tv;   /* kp x ldr2 zeta~^T v~                                                */
+} lsf_multi_scalings;
+
+/* Workspace bytes of lsf_solve_multi for row stride ldr2 and k solves. */
+int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes);
+
+/*
+ * Alg. 1 (Sec. 2) on the factored kernel K = xi zeta^T (Sec. 3.1) for k pairs of
+ * weights (a_p, b_p) on the same two point clouds and features, then Eq. (6) for
+ * each: results[p] gets W, the residual ||u_p o (K v_p) - a_p||_1 after the last
+ * v-half, log_scale, status and iters, exactly as lsf_solve + lsf_divergence
+ * give them for the p-th pair alone. With many potentials on one support, each
+ * half iteration becomes two n x r x k contractions, which run on the tensor
+ * cores (tcgen05, bf16 pair features and bf16 pair splits of the scalings and
+ * r-vectors, FP32 accumulation): one read of the features serves all k solves.
+ * k in [1, 32]; ldr2 a multiple of 128 with r <= ldr2 <= 1024, and the
+ * accumulators 2 kp (1 + ldr2/128) <= 512 TMEM columns (k <= 16: any ldr2; k <= 32:
+ * ldr2 <= 640). theta supplies r and eps (its ldr is not used). Iterates start
+ * from v = 1 as in lsf_solve. Errors: LSF_ERR_ARG, LSF_ERR_UNSUPPORTED (shapes
+ * above), LSF_ERR_WORKSPACE (below lsf_multi_workspace_bytes), LSF_ERR_CUDA;
+ * device status bits per solve in results[p].status.
+ */
+int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
+                    const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* out,
+                    lsf_result* results, void* workspace, size_t ws_bytes, void* stream);
+
 /* Kernel classes timed by the optional event recorder. */
 typedef enum {
   LSF_KERNEL_PASS = 0,       /* fused Sinkhorn passes (stored features)   */
@@ -490,6 +545,7 @@ typedef enum {
   LSF_KERNEL_BATCHED,        /* batched persistent solver                 */
   LSF_KERNEL_ADJOINT,        /* gradient kernels (points, weights, anchors) */
   LSF_KERNEL_SMALL,          /* cluster-persistent small-problem solver   */
+  LSF_KERNEL_PASS_MULTI,     /* tensor-core passes, many right-hand sides */
   LSF_KERNEL_NCLASSES
 } lsf_kernel_class;
 

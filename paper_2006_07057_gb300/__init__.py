@@ -20,10 +20,12 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._binding import (LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,  # noqa: F401
+from ._binding import (LSF_ERR_ARG, LSF_ERR_UNSUPPORTED, LSF_ERR_WORKSPACE,  # noqa: F401
+                       LSF_ERR_NONFINITE, LSF_ERR_TIMEOUT, LSF_KERNEL_ADJOINT,
                        LSF_KERNEL_BATCHED, LSF_KERNEL_SMALL,
                        LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
-                       LsfAccelInfo, LsfBatchInfo, LsfBatchProblem,
+                       LsfAccelInfo, LsfBatchInfo, LsfBatchProblem, LsfMultiCloud,
+                       LsfMultiScalings, LSF_KERNEL_PASS_MULTI,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
                        LsfArccos, LsfTheta, check, header_symbols, lib)
@@ -309,6 +311,49 @@ def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, o
     check(lib().lsf_solve_noalloc(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy),
                                   int(iters), MODES[mode], ctypes.byref(so), _p(result),
                                   _stream(stream)), "lsf_solve_noalloc")
+
+
+def ldr2_for(r: int) -> int:
+    """Row stride of the bf16 pair features of the tensor-core pass: r rounded up to 128."""
+    return (r + 127) // 128 * 128
+
+
+def multi_kp(k: int) -> int:
+    """Right-hand sides the tensor-core pass computes for k solves (16 or 32)."""
+    return 16 if k <= 16 else 32
+
+
+def lsf_split_features(F: torch.Tensor, r: int, ldr2: int | None = None, F2=None,
+                       stream=None) -> torch.Tensor:
+    """bf16 pair planes (2 x n x ldr2, hi and lo) of stored FP32 features F (n x ldr)."""
+    _f32(F)
+    n, ldr = F.shape
+    ldr2 = ldr2 if ldr2 is not None else ldr2_for(r)
+    if F2 is None:
+        F2 = torch.empty((2, n, ldr2), dtype=torch.bfloat16, device=F.device)
+    check(lib().lsf_split_features(_p(F), int(n), int(ldr), int(r), _p(F2), int(ldr2),
+                                   _stream(stream)), "lsf_split_features")
+    return F2
+
+
+def lsf_multi_workspace_bytes(ldr2: int, k: int) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().lsf_multi_workspace_bytes(int(ldr2), int(k), ctypes.byref(b)),
+          "lsf_multi_workspace_bytes")
+    return int(b.value)
+
+
+def lsf_solve_multi(theta: Theta, ldr2: int, F2x, shift_x, Wx, F2y, shift_y, Wy, iters: int,
+                    U, V, Tu, Tv, results, workspace, stream=None) -> None:
+    """Alg. 1 and Eq. (6) for the k weight pairs (rows of Wx, Wy) on one support."""
+    k = int(Wx.shape[0])
+    th = theta.as_c()
+    cx = LsfMultiCloud(_p(F2x), _p(shift_x), _p(Wx), int(Wx.shape[1]))
+    cy = LsfMultiCloud(_p(F2y), _p(shift_y), _p(Wy), int(Wy.shape[1]))
+    so = LsfMultiScalings(_p(U), _p(V), _p(Tu), _p(Tv))
+    check(lib().lsf_solve_multi(ctypes.byref(th), int(ldr2), ctypes.byref(cx), ctypes.byref(cy), k,
+                                int(iters), ctypes.byref(so), _p(results), _p(workspace),
+                                workspace.numel(), _stream(stream)), "lsf_solve_multi")
 
 
 def lsf_debiased(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, s_xy: Scalings,
@@ -812,3 +857,60 @@ class BatchedSolver:
                 v["mode"] = b.mode
                 out[k] = v
         return out
+
+
+class MultiSinkhornProblem:
+    """k pairs of weights (rows of A: k x n, B: k x m) on the same two clouds.
+
+    One theta, one set of features (split into the bf16 pair planes of the
+    tensor-core pass), and one multi-right-hand-side solve per ``run``: every
+    half iteration of Alg. 1 for all k pairs is two n x r x k contractions on
+    the tensor cores. ``values`` returns, per pair, Eq. (6), the residual and
+    the status, as a single solve of that pair reports them.
+    """
+
+    def __init__(self, X, Y, A, B, Z, eps: float, stream=None):
+        for t in (X, Y, A, B, Z):
+            _f32(t)
+        if A.dim() != 2 or B.dim() != 2 or A.shape[0] != B.shape[0]:
+            raise ValueError("A (k x n) and B (k x m) need the same number of rows")
+        if A.shape[1] != X.shape[0] or B.shape[1] != Y.shape[0]:
+            raise ValueError("A must have n columns and B m columns")
+        self.stream = stream
+        self.k = int(A.shape[0])
+        dev = X.device
+        n, d = X.shape
+        m = Y.shape[0]
+        r = Z.shape[0]
+        R = float(lsf_radius(X, Y, stream=stream).item())
+        q, sig = lsf_gaussian_params(R, eps, d)
+        U, c = lsf_anchors(Z, q, sig, eps, stream=stream)
+        self.theta = Theta(U, c, r, ldr_for(r), d, float(eps), R, q, sig)
+        self.ldr2 = ldr2_for(r)
+        Fx, self.shift_x = lsf_features(X, self.theta, stream=stream)
+        Fy, self.shift_y = lsf_features(Y, self.theta, stream=stream)
+        self.F2x = lsf_split_features(Fx, r, self.ldr2, stream=stream)
+        self.F2y = lsf_split_features(Fy, r, self.ldr2, stream=stream)
+        del Fx, Fy
+        self.A, self.B = A, B
+        kp = multi_kp(self.k)
+        self.U = torch.zeros((self.k, n), dtype=torch.float32, device=dev)
+        self.V = torch.zeros((self.k, m), dtype=torch.float32, device=dev)
+        self.Tu = torch.zeros((kp, self.ldr2), dtype=torch.float32, device=dev)
+        self.Tv = torch.zeros((kp, self.ldr2), dtype=torch.float32, device=dev)
+        self.results = alloc_results(self.k, dev)
+        nbytes = lsf_multi_workspace_bytes(self.ldr2, self.k)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        off = (-ws.data_ptr()) % 256
+        self.workspace = ws[off:off + nbytes]
+
+    def run(self, iters: int) -> None:
+        """Launch the k solves and their Eq. (6) reductions on the stream (asynchronous)."""
+        lsf_solve_multi(self.theta, self.ldr2, self.F2x, self.shift_x, self.A, self.F2y,
+                        self.shift_y, self.B, iters, self.U, self.V, self.Tu, self.Tv,
+                        self.results, self.workspace, self.stream)
+
+    def values(self) -> list[dict]:
+        """Per pair: W (Eq. (6)), residual, status, iters (synchronises)."""
+        return [{"W": r["W"], "residual": r["residual"], "status": r["status"], "iters": r["iters"],
+                 "log_scale": r["log_scale"]} for r in read_results(self.results)]

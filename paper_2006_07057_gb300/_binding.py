@@ -39,6 +39,7 @@ LSF_KERNEL_PASS_LOG = 4
 LSF_KERNEL_BATCHED = 5
 LSF_KERNEL_ADJOINT = 6
 LSF_KERNEL_SMALL = 7
+LSF_KERNEL_PASS_MULTI = 8
 
 
 class LsfTheta(ctypes.Structure):
@@ -81,6 +82,14 @@ class LsfBatchInfo(ctypes.Structure):
                 ("rows_y", c_int64), ("plan_bytes", c_size_t), ("smem_bytes", c_size_t),
                 ("strategy", c_int)]
 
+class LsfMultiCloud(ctypes.Structure):
+    _fields_ = [("F2", c_void_p), ("shift", c_void_p), ("W", c_void_p), ("n", c_int64)]
+
+
+class LsfMultiScalings(ctypes.Structure):
+    _fields_ = [("U", c_void_p), ("V", c_void_p), ("Tu", c_void_p), ("Tv", c_void_p)]
+
+
 class LsfAccelInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("attempts", ctypes.c_int32), ("A", c_double),
                 ("L", c_double)]
@@ -109,6 +118,11 @@ _SIGNATURES = {
     "lsf_solve_accelerated": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double,
                                       _P(LsfScalings), c_void_p, _P(LsfAccelInfo), c_void_p,
                                       c_size_t, c_void_p]),
+    "lsf_split_features": (c_int, [c_void_p, c_int64, c_int, c_int, c_void_p, c_int, c_void_p]),
+    "lsf_multi_workspace_bytes": (c_int, [c_int, c_int, _P(c_size_t)]),
+    "lsf_solve_multi": (c_int, [_P(LsfTheta), c_int, _P(LsfMultiCloud), _P(LsfMultiCloud), c_int,
+                                c_int, _P(LsfMultiScalings), c_void_p, c_void_p, c_size_t,
+                                c_void_p]),
     "lsf_solve": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                           _P(LsfScalings), c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_divergence": (c_int, [_P(LsfTheta), c_int, _P(_P(LsfCloud)), _P(_P(LsfCloud)),

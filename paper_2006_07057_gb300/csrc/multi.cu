@@ -1,0 +1,822 @@
+// Many weight vectors on one support: Alg. 1 for k right-hand sides at once, the
+// fused pass written as a tensor-core contraction (tcgen05, TMEM accumulators,
+// TMA-staged bf16 pair features).
+//
+// k pairs of weights (a_p, b_p), p < k, on the same points share the features of
+// Sec. 3.1, so one half iteration of Alg. 1 for all of them is
+//   S  = F T^T        n x kp   row products s_p = xi~ t_p         (T: kp x ldr2)
+//   u_p = a_p / s_p             elementwise, per right-hand side
+//   T' = U F          kp x ldr2 transposed products t'_p = xi~^T u_p
+// two n x r x kp contractions that read F once. kp is k rounded up to 16 (the
+// MMA's N granularity); the padding sides carry u = 0 and t = 0.
+//
+// Precision. F is stored as a pair of bf16 planes, hi = RN(F) and lo = RN(F - hi),
+// so hi + lo equals F to 2^-16 relative (4 bytes per entry, as FP32). The small
+// operands are split the same way each pass (T and U into hi, lo), and each
+// product takes the three terms hi*hi + hi*lo + lo*hi, accumulated in FP32 in
+// TMEM; the dropped lo*lo term is below 2^-16 relative.
+//
+// Kernel. One CTA per SM, persistent over tiles of 128 points. Per tile the
+// producer warp streams the tile's feature chunks (128 points x 128 features,
+// both planes, 64 KB) into a shared-memory ring with TMA (128-byte swizzle), twice:
+// first for the row products, then again (from L2) for the transposed products.
+// One elected thread issues the MMAs:
+//   row sweep:  D_S (128 x 2kp)  += A . [T_hi; T_lo]^T   A = F chunk, K-major (K = features)
+//               D_S (128 x kp)   += A_lo . T_hi^T
+//   col sweep:  D_T[c] (128 x 2kp) += A^T . [U_hi; U_lo]  A^T = the same smem chunk read
+//               MN-major (M = features, K = points), no transposed copy
+// Four epilogue warps read D_S from TMEM (thread = point), form u = a / s, write
+// it, split it into bf16 hi/lo and store it as the B operand of the col sweep.
+// D_T holds this CTA's partial T' for the whole launch; at the end it is read out
+// to a per-CTA slot and summed over the CTAs in a fixed order by a second kernel.
+// Every wait is bounded; a wait that runs out sets LSF_ERR_TIMEOUT and the CTA
+// still drains its copies and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "solve.cuh"
+
+namespace lsf {
+namespace {
+
+constexpr int kTileRows = 128;                 // points per tile (M of the row product)
+constexpr int kChunkCols = 128;                // features per chunk (M of the col product)
+constexpr int kBoxCols = 64;                   // features per TMA box: 128 B of bf16
+constexpr int kBoxBytes = kTileRows * kBoxCols * 2;   // 16 KB
+constexpr int kStageBytes = 4 * kBoxBytes;     // two boxes of each plane: 64 KB
+constexpr int kMultiThreads = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kMaxStages = 4;
+
+enum MultiMode : int { kMultiUpdate = 0, kMultiAxpy = 1, kMultiDot = 2 };
+
+struct MultiArgs {
+  int64_t n;
+  int64_t ntiles;
+  int ldr2;
+  int k;             // real right-hand sides (<= kp)
+  int mode;
+  int nstages;
+  uint32_t tmem_cols;
+  const float* t_in;   // kp x ldr2 r-vectors (Update, Dot)
+  const float* w;      // k x n weights (Update, Dot)
+  const float* old;    // k x n previous scalings (Dot) or the given scalings (Axpy)
+  float* out;          // k x n new scalings (Update)
+  float* part;         // [grid][kp][ldr2] per-CTA partial T' (Update, Axpy)
+  double* rpart;       // [grid][kp] per-CTA residual partials (Dot)
+  lsf_result* res;     // k result records (status bits)
+};
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version of the sm_100 family
+  d |= static_cast<uint64_t>(2) << 61;  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16 with bf16 A and B, FP32 D, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn_major) << 15) |
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (lane i of the warp reads
+// TMEM lane base + i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TMA: one 64-feature x 128-point box of plane z at feature x, point y.
+__device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                        uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Element (row, col) of a thread-written K-major operand region with the 128-byte
+// swizzle: rows of 64 bf16 (128 B), 16-byte chunk c stored at c ^ (row % 8).
+__device__ __forceinline__ int sw128(int row, int col) {
+  return row * 64 + ((((col >> 3) ^ row) & 7) << 3) + (col & 7);
+}
+
+__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
+}
+
+struct MultiSmem {
+  unsigned char* stages;  // [S][4][16 KB]: hi box 0, hi box 1, lo box 0, lo box 1
+  uint16_t* sT;           // [ldr2 / 64][2 kp][64]  (Update, Dot)
+  uint16_t* sU;           // [2][2 kp][64]
+  uint64_t* full;         // [S]
+  uint64_t* empty;        // [S]
+  uint64_t* s_full;
+  uint64_t* s_empty;
+  uint64_t* u_full;
+  uint64_t* u_empty;
+  uint64_t* t_done;
+  uint32_t* tmem_slot;
+  double* red;            // [4][kp]
+};
+
+__host__ __device__ inline size_t multi_t_bytes(int kp, int ldr2) {
+  return static_cast<size_t>(kp) * ldr2 * 4;
+}
+
+__host__ __device__ inline size_t multi_smem_bytes(int kp, int ldr2, int stages, bool rows) {
+  return 1024 + static_cast<size_t>(stages) * kStageBytes + (rows ? multi_t_bytes(kp, ldr2) : 0) +
+         static_cast<size_t>(kp) * 512 + 256 + static_cast<size_t>(4) * kp * 8;
+}
+
+__device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int ldr2, int stages,
+                                                  bool rows) {
+  MultiSmem s;
+  unsigned char* p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                                      ~static_cast<uintptr_t>(1023));
+  s.stages = p;
+  p += static_cast<size_t>(stages) * kStageBytes;
+  s.sT = reinterpret_cast<uint16_t*>(p);
+  if (rows) p += multi_t_bytes(kp, ldr2);
+  s.sU = reinterpret_cast<uint16_t*>(p);
+  p += static_cast<size_t>(kp) * 512;
+  uint64_t* b = reinterpret_cast<uint64_t*>(p);
+  s.full = b;
+  s.empty = b + kMaxStages;
+  s.s_full = b + 2 * kMaxStages;
+  s.s_empty = s.s_full + 1;
+  s.u_full = s.s_full + 2;
+  s.u_empty = s.s_full + 3;
+  s.t_done = s.s_full + 4;
+  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 5);
+  p += 256;
+  s.red = reinterpret_cast<double*>(p);
+  return s;
+}
+
+// Bounded wait by one lane, result broadcast to the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void flag_all(lsf_result* res, int k, int bits) {
+  for (int p = 0; p < k; ++p) atomicOr(&res[p].status, bits);
+}
+
+// ---------------------------------------------------------------- the pass kernel
+
+template <int KP>
+__global__ void __launch_bounds__(kMultiThreads, 1)
+    multi_pass_kernel(const __grid_constant__ CUtensorMap fmap, const MultiArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  const bool rows = a.mode != kMultiAxpy;
+  const bool cols = a.mode != kMultiDot;
+  const MultiSmem sm = multi_layout(smem_raw, KP, a.ldr2, a.nstages, rows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = a.ldr2 / kChunkCols;
+  const int64_t n = a.n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.nstages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(sm.s_full, 1);
+    mbar_init(sm.s_empty, 128);
+    mbar_init(sm.u_full, 128);
+    mbar_init(sm.u_empty, 1);
+    mbar_init(sm.t_done, 1);
+    fence_mbarrier_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(sm.tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the row products' B operand: T split into bf16 hi (rows 0..kp-1) and lo (kp..2kp-1)
+  if (rows) {
+    const int total = KP * a.ldr2;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int p = idx / a.ldr2, f = idx - p * a.ldr2;
+      uint16_t hi, lo;
+      split_bf16(__ldg(a.t_in + idx), hi, lo);
+      uint16_t* region = sm.sT + static_cast<size_t>(f >> 6) * (2 * KP * 64);
+      region[sw128(p, f & 63)] = hi;
+      region[sw128(KP + p, f & 63)] = lo;
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sm.tmem_slot;
+  const uint32_t tmem_S = tmem;             // 2 kp columns
+  const uint32_t tmem_T = tmem + 2 * KP;    // nchunks x 2 kp columns
+  int err = 0;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    int it = 0;
+    const int per_tile = (rows ? nchunks : 0) + (cols ? nchunks : 0);
+    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x) {
+      for (int q = 0; q < per_tile; ++q, ++it) {
+        const int s = it % a.nstages;
+        const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
+        if (!warp_wait(&sm.empty[s], ph ^ 1u, lane)) {
+          err = LSF_ERR_TIMEOUT;
+          break;
+        }
+        if (lane == 0) {
+          const int c = q % nchunks;
+          unsigned char* dst = sm.stages + static_cast<size_t>(s) * kStageBytes;
+          mbar_arrive_expect_tx(&sm.full[s], kStageBytes);
+          const int y = static_cast<int>(tile * kTileRows);
+          tma_box(dst, &fmap, c * kChunkCols, y, 0, &sm.full[s]);
+          tma_box(dst + kBoxBytes, &fmap, c * kChunkCols + kBoxCols, y, 0, &sm.full[s]);
+          tma_box(dst + 2 * kBoxBytes, &fmap, c * kChunkCols, y, 1, &sm.full[s]);
+          tma_box(dst + 3 * kBoxBytes, &fmap, c * kChunkCols + kBoxCols, y, 1, &sm.full[s]);
+        }
+        __syncwarp();
+      }
+    }
+    // drain: every issued copy has landed before the CTA may exit
+    const int used = min(it, a.nstages);
+    for (int j = 0; j < used; ++j) {
+      const int itj = it - 1 - j;
+      if (!warp_wait(&sm.full[itj % a.nstages], static_cast<uint32_t>(itj / a.nstages) & 1u, lane))
+        err = LSF_ERR_TIMEOUT;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer (one thread)
+    constexpr uint32_t kRowHi = idesc_bf16(2 * KP, 0);
+    constexpr uint32_t kRowLo = idesc_bf16(KP, 0);
+    constexpr uint32_t kColHi = idesc_bf16(2 * KP, 1);
+    constexpr uint32_t kColLo = idesc_bf16(KP, 1);
+    const uint32_t st_base = smem_u32(sm.stages);
+    const uint32_t sT_base = smem_u32(sm.sT);
+    const uint32_t sU_base = smem_u32(sm.sU);
+    const uint32_t region = 2 * KP * 128;  // bytes of one 64-wide K block of a B operand
+    int it = 0, j = 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x, ++j) {
+      if (rows) {
+        if (j > 0 && !warp_wait(sm.s_empty, static_cast<uint32_t>(j - 1) & 1u, lane)) {
+          err = LSF_ERR_TIMEOUT;
+          break;
+        }
+        tc_fence_after();
+        for (int c = 0; c < nchunks; ++c, ++it) {
+          const int s = it % a.nstages;
+          if (!warp_wait(&sm.full[s], static_cast<uint32_t>(it / a.nstages) & 1u, lane)) {
+            err = LSF_ERR_TIMEOUT;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t st = st_base + s * kStageBytes;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t a_hi = st + h * kBoxBytes + ks * 32;
+                const uint32_t b = sT_base + (2 * c + h) * region + ks * 32;
+                const uint64_t bd = smem_desc(b, 16, 1024);
+                mma_bf16(tmem_S, smem_desc(a_hi, 16, 1024), bd, kRowHi, (c | h | ks) != 0);
+                mma_bf16(tmem_S, smem_desc(a_hi + 2 * kBoxBytes, 16, 1024), bd, kRowLo, 1);
+              }
+            }
+            mma_commit(&sm.empty[s]);
+          }
+          __syncwarp();
+        }
+        if (err) break;
+        if (lane == 0) mma_commit(sm.s_full);
+        __syncwarp();
+      }
+      if (cols) {
+        if (!warp_wait(sm.u_full, static_cast<uint32_t>(j) & 1u, lane)) {
+          err = LSF_ERR_TIMEOUT;
+          break;
+        }
+        tc_fence_after();
+        for (int c = 0; c < nchunks; ++c, ++it) {
+          const int s = it % a.nstages;
+          if (!warp_wait(&sm.full[s], static_cast<uint32_t>(it / a.nstages) & 1u, lane)) {
+            err = LSF_ERR_TIMEOUT;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t st = st_base + s * kStageBytes;
+            const uint32_t dT = tmem_T + c * 2 * KP;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+              // A^T: M = the chunk's 128 features (two 64-feature atoms 16 KB apart),
+              // K = 16 points (two 8-point groups of 1024 B)
+              const uint32_t a_hi = st + ks * 2048;
+              const uint32_t b = sU_base + (ks >> 2) * region + (ks & 3) * 32;
+              const uint64_t bd = smem_desc(b, 16, 1024);
+              mma_bf16(dT, smem_desc(a_hi, kBoxBytes, 1024), bd, kColHi, (j > 0 || ks > 0) ? 1 : 0);
+              mma_bf16(dT, smem_desc(a_hi + 2 * kBoxBytes, kBoxBytes, 1024), bd, kColLo, 1);
+            }
+            mma_commit(&sm.empty[s]);
+          }
+          __syncwarp();
+        }
+        if (err) break;
+        if (lane == 0) mma_commit(sm.u_empty);
+        __syncwarp();
+      }
+    }
+    if (lane == 0) mma_commit(sm.t_done);
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ epilogue warps 2..5
+    const int quarter = warp & 3;               // TMEM lanes this warp may access
+    const int rloc = quarter * 32 + lane;       // point within the tile
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    double resid[KP];
+#pragma unroll
+    for (int p = 0; p < KP; ++p) resid[p] = 0.0;
+    uint32_t bad = 0u;
+    int j = 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x, ++j) {
+      const int64_t row = tile * kTileRows + rloc;
+      const bool valid = row < n;
+      float u[KP];
+      if (rows) {
+        if (!warp_wait(sm.s_full, static_cast<uint32_t>(j) & 1u, lane)) {
+          err = LSF_ERR_TIMEOUT;
+          break;
+        }
+        tc_fence_after();
+        float d[2 * KP];
+#pragma unroll
+        for (int h = 0; h < 2 * KP / 32; ++h) {
+          float v[32];
+          tmem_ld32(tmem_S + lane_base + 32 * h, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) d[32 * h + i] = v[i];
+        }
+        tc_fence_before();
+        mbar_arrive(sm.s_empty);
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+          const float s = d[p] + d[KP + p];
+          u[p] = 0.f;
+          if (p < a.k && valid) {
+            const float w = __ldg(a.w + p * n + row);
+            if (a.mode == kMultiUpdate) {
+              const float v = w / s;
+              if (!(v > 0.f && v < INFINITY)) bad |= 1u << p;
+              a.out[p * n + row] = v;
+              u[p] = v;
+            } else {
+              const float o = __ldg(a.old + p * n + row);
+              resid[p] += fabs(static_cast<double>(o) * static_cast<double>(s) - static_cast<double>(w));
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < KP; ++p) u[p] = (p < a.k && valid) ? __ldg(a.old + p * n + row) : 0.f;
+      }
+      if (cols) {
+        if (j > 0 && !warp_wait(sm.u_empty, static_cast<uint32_t>(j - 1) & 1u, lane)) {
+          err = LSF_ERR_TIMEOUT;
+          break;
+        }
+        uint16_t* region = sm.sU + (rloc >> 6) * (2 * KP * 64);
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+          uint16_t hi, lo;
+          split_bf16(u[p], hi, lo);
+          region[sw128(p, rloc & 63)] = hi;
+          region[sw128(KP + p, rloc & 63)] = lo;
+        }
+        fence_async_smem();
+        mbar_arrive(sm.u_full);
+      }
+    }
+    // the launch's partial T' (this CTA's points) out of TMEM
+    if (cols && !err) {
+      if (!warp_wait(sm.t_done, 0u, lane)) {
+        err = LSF_ERR_TIMEOUT;
+      } else {
+        tc_fence_after();
+        float* dst = a.part + static_cast<size_t>(blockIdx.x) * KP * a.ldr2;
+        for (int c = 0; c < nchunks; ++c) {
+          float d[2 * KP];
+#pragma unroll
+          for (int h = 0; h < 2 * KP / 32; ++h) {
+            float v[32];
+            tmem_ld32(tmem_T + c * 2 * KP + lane_base + 32 * h, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) d[32 * h + i] = v[i];
+          }
+          const int f = c * kChunkCols + rloc;
+#pragma unroll
+          for (int p = 0; p < KP; ++p) dst[static_cast<size_t>(p) * a.ldr2 + f] = d[p] + d[KP + p];
+        }
+      }
+    }
+    if (a.mode == kMultiDot) {
+      // fixed-order fold of the residual terms: lanes, then the four warps
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        double v = resid[p];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sm.red[quarter * KP + p] = v;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+      const unsigned any = __ballot_sync(0xffffffffu, (bad >> p) & 1u);
+      if (any && lane == 0) atomicOr(&a.res[p].status, LSF_ERR_NONFINITE);
+    }
+  }
+  if (err && lane == 0) flag_all(a.res, a.k, err);
+  tc_fence_before();
+  __syncthreads();
+  if (a.mode == kMultiDot && threadIdx.x < KP) {
+    const int p = threadIdx.x;
+    a.rpart[static_cast<size_t>(blockIdx.x) * KP + p] =
+        sm.red[0 * KP + p] + sm.red[1 * KP + p] + sm.red[2 * KP + p] + sm.red[3 * KP + p];
+  }
+  if (warp == 1) {
+    // every MMA has completed: the issuer's last commit (t_done) tracks all of them
+    if (!warp_wait(sm.t_done, 0u, lane) && lane == 0) flag_all(a.res, a.k, LSF_ERR_TIMEOUT);
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols)
+                 : "memory");
+  }
+}
+
+// Sum of the per-CTA partials in CTA order: a block covers 32 outputs with 8
+// warps, warp w summing CTAs w, w + 8, ...; the 8 warp sums are folded in order.
+__global__ void __launch_bounds__(256) multi_reduce_kernel(const float* __restrict__ part, int G,
+                                                           int total, float* __restrict__ t_out) {
+  __shared__ double s[8][33];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  if (idx < total)
+    for (int g = w; g < G; g += 8) acc += static_cast<double>(__ldcg(part + static_cast<size_t>(g) * total + idx));
+  s[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && idx < total) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += s[i][lane];
+    t_out[idx] = static_cast<float>(t);
+  }
+}
+
+__global__ void multi_residual_kernel(const double* __restrict__ rpart, int G, int kp, int k,
+                                      lsf_result* res) {
+  const int p = threadIdx.x;
+  if (p >= k) return;
+  KahanSum s;
+  for (int g = 0; g < G; ++g) s.add(rpart[static_cast<size_t>(g) * kp + p]);
+  res[p].residual = s.value();
+}
+
+__global__ void multi_max_kernel(const float* __restrict__ x, int64_t n, unsigned* __restrict__ key) {
+  float best = -INFINITY;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    best = fmaxf(best, x[i]);
+  best = warp_max(best);
+  if ((threadIdx.x & 31) == 0) atomicMax(key, float_key(best));
+}
+
+// v = 1 for every right-hand side in shifted form: v~_j = exp(shift_j - M).
+__global__ void multi_init_kernel(const float* __restrict__ shift, int64_t n, int k,
+                                  const unsigned* __restrict__ key, float* __restrict__ V,
+                                  lsf_result* res) {
+  const float M = key_float(*key);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float v = expf(shift[i] - M);
+    for (int p = 0; p < k; ++p) V[p * n + i] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < k) res[threadIdx.x].log_scale = static_cast<double>(M);
+}
+
+__global__ void multi_iters_kernel(lsf_result* res, int k, int iters) {
+  if (static_cast<int>(threadIdx.x) < k) res[threadIdx.x].iters = iters;
+}
+
+// bf16 pair planes from stored FP32 features (zero beyond r).
+__global__ void split_features_kernel(const float* __restrict__ F, int64_t n, int ldr, int r,
+                                      uint16_t* __restrict__ F2, int ldr2) {
+  const int64_t total = n * ldr2;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / ldr2;
+    const int k = static_cast<int>(idx - i * ldr2);
+    const float f = k < r ? F[i * ldr + k] : 0.f;
+    uint16_t hi, lo;
+    split_bf16(f, hi, lo);
+    F2[idx] = hi;
+    F2[total + idx] = lo;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q{};
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of the two bf16 planes: dims (ldr2, n, 2), boxes of 64 x 128 x 1,
+// 128-byte swizzle; rows past n read as zeros.
+int make_pair_map(const uint16_t* F2, int64_t n, int ldr2, CUtensorMap* map) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if (reinterpret_cast<uintptr_t>(F2) % 256 != 0)
+    return fail(LSF_ERR_ARG, "F2 must be 256-byte aligned");
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(ldr2), static_cast<cuuint64_t>(n), 2};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldr2) * 2, static_cast<cuuint64_t>(n) * ldr2 * 2};
+  cuuint32_t box[3] = {kBoxCols, kTileRows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(F2), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return LSF_OK;
+}
+
+int multi_kp(int k) { return k <= 16 ? 16 : 32; }
+
+uint32_t tmem_columns(int kp, int ldr2) {
+  const int need = 2 * kp * (1 + ldr2 / kChunkCols);
+  uint32_t c = 32;
+  while (static_cast<int>(c) < need) c <<= 1;
+  return c;
+}
+
+// The shapes this kernel takes: ldr2 a multiple of 128 up to 1024, k <= 32, the
+// accumulators within TMEM's 512 columns and the operands within shared memory.
+int check_multi_shape(int ldr2, int k) {
+  if (k < 1 || k > 32) return fail(LSF_ERR_UNSUPPORTED, "multi solve: k must be in [1, 32]");
+  if (ldr2 < 128 || ldr2 % 128 != 0 || ldr2 > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "multi solve: ldr2 must be a multiple of 128 in [128, 1024]");
+  const int kp = multi_kp(k);
+  if (2 * kp * (1 + ldr2 / kChunkCols) > 512)
+    return fail(LSF_ERR_UNSUPPORTED, "multi solve: %d right-hand sides at ldr2 = %d exceed TMEM", k, ldr2);
+  if (multi_smem_bytes(kp, ldr2, 2, true) > static_cast<size_t>(device_info().smem_optin))
+    return fail(LSF_ERR_UNSUPPORTED, "multi solve: %d right-hand sides at ldr2 = %d exceed shared memory", k, ldr2);
+  return LSF_OK;
+}
+
+int multi_grid_max() { return device_info().sms; }
+
+size_t align256m(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+size_t multi_extra_bytes(int ldr2, int kp) {
+  const size_t G = static_cast<size_t>(multi_grid_max());
+  return align256m(G * kp * ldr2 * sizeof(float)) + align256m(G * kp * sizeof(double));
+}
+
+struct MultiWs {
+  Workspace ws;
+  float* part;
+  double* rpart;
+};
+
+template <int KP>
+int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& map, cudaStream_t st, int* grid_out) {
+  MultiArgs a = a0;
+  const bool rows = a.mode != kMultiAxpy;
+  const size_t optin = static_cast<size_t>(device_info().smem_optin);
+  int stages = kMaxStages;
+  while (stages > 2 && multi_smem_bytes(KP, a.ldr2, stages, rows) > optin) --stages;
+  const size_t smem = multi_smem_bytes(KP, a.ldr2, stages, rows);
+  if (smem > optin) return fail(LSF_ERR_UNSUPPORTED, "multi pass: %zu bytes of shared memory", smem);
+  a.nstages = stages;
+  a.tmem_cols = tmem_columns(KP, a.ldr2);
+  static int configured[2] = {0, 0};
+  const int dev = device_info().device;
+  if (configured[KP == 32] != dev + 1) {
+    if (cudaFuncSetAttribute(multi_pass_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(optin)) != cudaSuccess)
+      return fail(LSF_ERR_CUDA, "multi pass: cannot raise the shared-memory limit");
+    configured[KP == 32] = dev + 1;
+  }
+  const int grid = static_cast<int>(std::min<int64_t>(multi_grid_max(), a.ntiles));
+  const double bytes = static_cast<double>(a.n) * a.ldr2 * 4.0 +
+                       static_cast<double>(a.n) * a.k * 4.0 * (a.mode == kMultiAxpy ? 1 : 2);
+  {
+    LaunchScope ls(st, LSF_KERNEL_PASS_MULTI, bytes);
+    multi_pass_kernel<KP><<<grid, kMultiThreads, smem, st>>>(map, a);
+    LSF_TRY(check_launch("multi_pass_kernel"));
+  }
+  *grid_out = grid;
+  return LSF_OK;
+}
+
+// One pass and its reduction. Returns LSF_OK or an error status.
+int multi_pass(int mode, int k, int64_t n, int ldr2, const CUtensorMap& map, const float* t_in,
+               const float* w, const float* old, float* out, float* t_out, lsf_result* res,
+               const MultiWs& mw, cudaStream_t st) {
+  const int kp = multi_kp(k);
+  MultiArgs a{};
+  a.n = n;
+  a.ntiles = (n + kTileRows - 1) / kTileRows;
+  a.ldr2 = ldr2;
+  a.k = k;
+  a.mode = mode;
+  a.t_in = t_in;
+  a.w = w;
+  a.old = old;
+  a.out = out;
+  a.part = mw.part;
+  a.rpart = mw.rpart;
+  a.res = res;
+  int grid = 0;
+  LSF_TRY(kp == 16 ? launch_multi_kp<16>(a, map, st, &grid) : launch_multi_kp<32>(a, map, st, &grid));
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 4.0 * grid * kp * ldr2);
+  if (mode == kMultiDot) {
+    multi_residual_kernel<<<1, 32, 0, st>>>(mw.rpart, grid, kp, k, res);
+    return check_launch("multi_residual_kernel");
+  }
+  const int total = kp * ldr2;
+  multi_reduce_kernel<<<(total + 31) / 32, 256, 0, st>>>(mw.part, grid, total, t_out);
+  return check_launch("multi_reduce_kernel");
+}
+
+}  // namespace
+}  // namespace lsf
+
+using namespace lsf;
+
+extern "C" {
+
+int lsf_split_features(const float* F, int64_t n, int ldr, int r, uint16_t* F2, int ldr2,
+                       void* stream) {
+  if (!F || !F2) return fail(LSF_ERR_ARG, "lsf_split_features: NULL pointer");
+  if (n < 1 || r < 1 || r > ldr || r > ldr2) return fail(LSF_ERR_ARG, "lsf_split_features: bad sizes");
+  if (ldr2 % 128 != 0 || ldr2 > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_split_features: ldr2 must be a multiple of 128, <= 1024");
+  cudaStream_t st = as_stream(stream);
+  const int grid = device_info().sms * 4;
+  LaunchScope ls(st, LSF_KERNEL_FEATURES, static_cast<double>(n) * (4.0 * ldr + 4.0 * ldr2));
+  split_features_kernel<<<grid, 256, 0, st>>>(F, n, ldr, r, F2, ldr2);
+  return check_launch("split_features_kernel");
+}
+
+int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes) {
+  if (!bytes) return fail(LSF_ERR_ARG, "lsf_multi_workspace_bytes: NULL output");
+  LSF_TRY(check_multi_shape(ldr2, k));
+  *bytes = align256m(workspace_bytes(ldr2)) + multi_extra_bytes(ldr2, multi_kp(k));
+  return LSF_OK;
+}
+
+int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
+                    const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* out,
+                    lsf_result* results, void* workspace, size_t ws_bytes, void* stream) {
+  LSF_TRY(check_theta(theta));
+  LSF_TRY(check_multi_shape(ldr2, k));
+  if (theta->r > ldr2) return fail(LSF_ERR_ARG, "multi solve: r exceeds ldr2");
+  if (!x || !y || !out || !results) return fail(LSF_ERR_ARG, "multi solve: NULL argument");
+  if (x->n < 1 || y->n < 1) return fail(LSF_ERR_ARG, "multi solve: a measure needs n >= 1 points");
+  if (!x->F2 || !y->F2 || !x->shift || !y->shift || !x->W || !y->W)
+    return fail(LSF_ERR_ARG, "multi solve: F2, shift and W are required on both sides");
+  if (!out->U || !out->V || !out->Tu || !out->Tv)
+    return fail(LSF_ERR_ARG, "multi solve: U, V, Tu, Tv are required");
+  if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+  if (x->n > (int64_t(1) << 31) - kTileRows || y->n > (int64_t(1) << 31) - kTileRows)
+    return fail(LSF_ERR_UNSUPPORTED, "multi solve: too many points for 32-bit TMA coordinates");
+  const int kp = multi_kp(k);
+  size_t need = 0;
+  LSF_TRY(lsf_multi_workspace_bytes(ldr2, k, &need));
+  if (ws_bytes < need)
+    return fail(LSF_ERR_WORKSPACE, "multi solve: workspace has %zu bytes, needs %zu", ws_bytes, need);
+  cudaStream_t st = as_stream(stream);
+  MultiWs mw{};
+  LSF_TRY(start_solve(workspace, ws_bytes, ldr2, results, k, &mw.ws, st));
+  char* p = static_cast<char*>(workspace) + align256m(workspace_bytes(ldr2));
+  mw.part = reinterpret_cast<float*>(p);
+  p += align256m(static_cast<size_t>(multi_grid_max()) * kp * ldr2 * sizeof(float));
+  mw.rpart = reinterpret_cast<double*>(p);
+  CUtensorMap mx, my;
+  LSF_TRY(make_pair_map(x->F2, x->n, ldr2, &mx));
+  LSF_TRY(make_pair_map(y->F2, y->n, ldr2, &my));
+  if (cudaMemsetAsync(out->Tu, 0, sizeof(float) * kp * ldr2, st) != cudaSuccess ||
+      cudaMemsetAsync(out->Tv, 0, sizeof(float) * kp * ldr2, st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "multi solve: memset failed");
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * y->n * (1 + k));
+    const int grid = device_info().sms * 2;
+    multi_max_kernel<<<grid, 256, 0, st>>>(y->shift, y->n, mw.ws.keys);
+    multi_init_kernel<<<grid, 256, 0, st>>>(y->shift, y->n, k, mw.ws.keys, out->V, results);
+    LSF_TRY(check_launch("multi_init_kernel"));
+  }
+  LSF_TRY(multi_pass(kMultiAxpy, k, y->n, ldr2, my, nullptr, nullptr, out->V, nullptr, out->Tv,
+                     results, mw, st));
+  for (int it = 0; it < iters; ++it) {
+    LSF_TRY(multi_pass(kMultiUpdate, k, x->n, ldr2, mx, out->Tv, x->W, nullptr, out->U, out->Tu,
+                       results, mw, st));
+    LSF_TRY(multi_pass(kMultiUpdate, k, y->n, ldr2, my, out->Tu, y->W, nullptr, out->V, out->Tv,
+                       results, mw, st));
+  }
+  LSF_TRY(multi_pass(kMultiDot, k, x->n, ldr2, mx, out->Tv, x->W, out->U, nullptr, nullptr, results,
+                     mw, st));
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    multi_iters_kernel<<<1, 32, 0, st>>>(results, k, iters);
+    LSF_TRY(check_launch("multi_iters_kernel"));
+  }
+  // Eq. (6) for every right-hand side, three per reduction launch
+  for (int p0 = 0; p0 < k; p0 += 3) {
+    const int nt = std::min(3, k - p0);
+    lsf_cloud cx[3], cy[3];
+    lsf_scalings ss[3];
+    const lsf_cloud* xs[3];
+    const lsf_cloud* ys[3];
+    const lsf_scalings* sp[3];
+    lsf_result* rs[3];
+    for (int t = 0; t < nt; ++t) {
+      const int q = p0 + t;
+      cx[t] = lsf_cloud{nullptr, nullptr, x->shift, x->W + static_cast<int64_t>(q) * x->n, x->n};
+      cy[t] = lsf_cloud{nullptr, nullptr, y->shift, y->W + static_cast<int64_t>(q) * y->n, y->n};
+      ss[t] = lsf_scalings{out->U + static_cast<int64_t>(q) * x->n, out->V + static_cast<int64_t>(q) * y->n,
+                           nullptr, nullptr};
+      xs[t] = &cx[t];
+      ys[t] = &cy[t];
+      sp[t] = &ss[t];
+      rs[t] = results + q;
+    }
+    LSF_TRY(launch_divergence(theta, nt, xs, ys, sp, rs, nullptr, nullptr, mw.ws, st, 0));
+  }
+  return LSF_OK;
+}
+
+}  // extern "C"

@@ -263,6 +263,8 @@ int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double
   return check_launch("init_scaling_kernel");
 }
 
+}  // namespace
+
 int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* xs,
                       const lsf_cloud* const* ys, const lsf_scalings* const* s,
                       lsf_result* const* res, const double* coef, double* combined,
@@ -290,7 +292,6 @@ int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* x
   return check_launch("divergence_kernel");
 }
 
-}  // namespace
 }  // namespace lsf
 
 using namespace lsf;
