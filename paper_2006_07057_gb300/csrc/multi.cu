@@ -63,7 +63,6 @@ struct MultiArgs {
   int mode;
   int nstages;
   uint32_t tmem_cols;
-  const float* t_in;   // kp x ldr2 r-vectors (Update, Dot)
   const float* w;      // k x n weights (Update, Dot)
   const float* old;    // k x n previous scalings (Dot) or the given scalings (Axpy)
   float* out;          // k x n new scalings (Update)
@@ -133,13 +132,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// TMA: one 64-feature x 128-point box of plane z at feature x, point y.
+// TMA: one 64-feature x 128-point box of plane z at feature x, point y (the 3-D
+// map of the feature planes).
 __device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x, int y, int z,
                                         uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
       "{%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// TMA: one box of a 2-D tensor map at (x, y).
+__device__ __forceinline__ void tma_box2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -156,50 +165,49 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
   lo = __bfloat16_as_ushort(l);
 }
 
+// Shared memory of the pass. A ring stage holds one feature chunk (both planes,
+// 64 KB) and, for a row-product item, the matching 128-feature block of the
+// split r-vectors [T_hi; T_lo] (2 kp rows x 128 features, loaded by TMA from the
+// pair buffer the previous pass's reduction wrote).
 struct MultiSmem {
-  unsigned char* stages;  // [S][4][16 KB]: hi box 0, hi box 1, lo box 0, lo box 1
-  uint16_t* sT;           // [ldr2 / 64][2 kp][64]  (Update, Dot)
-  uint16_t* sU;           // [2][2 kp][64]
+  unsigned char* stages;  // [S][64 KB features | 2 x (2 kp x 128 B) r-vector boxes]
+  uint16_t* sU;           // [2 K blocks][2 kp][64]: the split scalings of one tile
   uint64_t* full;         // [S]
   uint64_t* empty;        // [S]
-  uint64_t* s_full;
-  uint64_t* s_empty;
-  uint64_t* u_full;
-  uint64_t* u_empty;
-  uint64_t* t_done;
+  uint64_t* s_full;       // [2] row products of a tile in D_S[b]
+  uint64_t* s_empty;      // [2] D_S[b] read out
+  uint64_t* u_full;       // sU written
+  uint64_t* u_empty;      // sU read by the transposed products
+  uint64_t* t_done;       // every MMA of the launch completed
   uint32_t* tmem_slot;
   double* red;            // [4][kp]
 };
 
-__host__ __device__ inline size_t multi_t_bytes(int kp, int ldr2) {
-  return static_cast<size_t>(kp) * ldr2 * 4;
+__host__ __device__ inline int multi_tbox_bytes(int kp) { return 2 * kp * 128; }
+__host__ __device__ inline int multi_stage_bytes(int kp) { return kStageBytes + 2 * multi_tbox_bytes(kp); }
+
+__host__ __device__ inline size_t multi_smem_bytes(int kp, int stages) {
+  return 1024 + static_cast<size_t>(stages) * multi_stage_bytes(kp) + static_cast<size_t>(kp) * 512 +
+         256 + static_cast<size_t>(4) * kp * 8;
 }
 
-__host__ __device__ inline size_t multi_smem_bytes(int kp, int ldr2, int stages, bool rows) {
-  return 1024 + static_cast<size_t>(stages) * kStageBytes + (rows ? multi_t_bytes(kp, ldr2) : 0) +
-         static_cast<size_t>(kp) * 512 + 256 + static_cast<size_t>(4) * kp * 8;
-}
-
-__device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int ldr2, int stages,
-                                                  bool rows) {
+__device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int stages) {
   MultiSmem s;
   unsigned char* p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
                                                       ~static_cast<uintptr_t>(1023));
   s.stages = p;
-  p += static_cast<size_t>(stages) * kStageBytes;
-  s.sT = reinterpret_cast<uint16_t*>(p);
-  if (rows) p += multi_t_bytes(kp, ldr2);
+  p += static_cast<size_t>(stages) * multi_stage_bytes(kp);
   s.sU = reinterpret_cast<uint16_t*>(p);
   p += static_cast<size_t>(kp) * 512;
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   s.full = b;
   s.empty = b + kMaxStages;
   s.s_full = b + 2 * kMaxStages;
-  s.s_empty = s.s_full + 1;
-  s.u_full = s.s_full + 2;
-  s.u_empty = s.s_full + 3;
-  s.t_done = s.s_full + 4;
-  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 5);
+  s.s_empty = s.s_full + 2;
+  s.u_full = s.s_full + 4;
+  s.u_empty = s.s_full + 5;
+  s.t_done = s.s_full + 6;
+  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 7);
   p += 256;
   s.red = reinterpret_cast<double*>(p);
   return s;
@@ -216,26 +224,53 @@ __device__ __forceinline__ void flag_all(lsf_result* res, int k, int bits) {
   for (int p = 0; p < k; ++p) atomicOr(&res[p].status, bits);
 }
 
+// Order of the work of one CTA. Its tiles are j = 0 .. nt-1 (tile blockIdx.x +
+// j gridDim.x). With both products (Update), phase ph interleaves the
+// row-product chunks of tile ph (from HBM) with the transposed-product chunks
+// of tile ph - 1 (re-read from L2): R(ph, 0), C(ph-1, 0), R(ph, 1), C(ph-1, 1),
+// ...; so HBM loads stay in flight while tile ph - 1 finishes, and the
+// scalings of tile ph - 1 are formed while R(ph, 0) runs. Dot runs R items
+// only, Axpy C items only. The producer and the MMA issuer walk the same
+// sequence.
+struct Schedule {
+  int nt, nchunks, lag;
+  bool rows, cols;
+  __device__ int phases() const { return nt + lag; }
+  __device__ bool c_on(int ph) const { return cols && ph - lag >= 0 && ph - lag < nt; }
+  __device__ bool r_on(int ph) const { return rows && ph < nt; }
+};
+
 // ---------------------------------------------------------------- the pass kernel
 
 template <int KP>
 __global__ void __launch_bounds__(kMultiThreads, 1)
-    multi_pass_kernel(const __grid_constant__ CUtensorMap fmap, const MultiArgs a) {
+    multi_pass_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap tmap,
+                      const MultiArgs a) {
   extern __shared__ unsigned char smem_raw[];
   const bool rows = a.mode != kMultiAxpy;
   const bool cols = a.mode != kMultiDot;
-  const MultiSmem sm = multi_layout(smem_raw, KP, a.ldr2, a.nstages, rows);
+  const MultiSmem sm = multi_layout(smem_raw, KP, a.nstages);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = a.ldr2 / kChunkCols;
   const int64_t n = a.n;
+  const int stage_bytes = multi_stage_bytes(KP);
+  const int tbox = multi_tbox_bytes(KP);
+  Schedule sch;
+  sch.nt = static_cast<int>((a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  sch.nchunks = nchunks;
+  sch.rows = rows;
+  sch.cols = cols;
+  sch.lag = (rows && cols) ? 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.nstages; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    mbar_init(sm.s_full, 1);
-    mbar_init(sm.s_empty, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.s_full[b], 1);
+      mbar_init(&sm.s_empty[b], 128);
+    }
     mbar_init(sm.u_full, 128);
     mbar_init(sm.u_empty, 1);
     mbar_init(sm.t_done, 1);
@@ -248,50 +283,45 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // the row products' B operand: T split into bf16 hi (rows 0..kp-1) and lo (kp..2kp-1)
-  if (rows) {
-    const int total = KP * a.ldr2;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int p = idx / a.ldr2, f = idx - p * a.ldr2;
-      uint16_t hi, lo;
-      split_bf16(__ldg(a.t_in + idx), hi, lo);
-      uint16_t* region = sm.sT + static_cast<size_t>(f >> 6) * (2 * KP * 64);
-      region[sw128(p, f & 63)] = hi;
-      region[sw128(KP + p, f & 63)] = lo;
-    }
-  }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sm.tmem_slot;
-  const uint32_t tmem_S = tmem;             // 2 kp columns
-  const uint32_t tmem_T = tmem + 2 * KP;    // nchunks x 2 kp columns
+  const uint32_t tmem_S = tmem;             // D_S[b] at b * 2 kp
+  const uint32_t tmem_T = tmem + 4 * KP;    // D_T[c] at c * 2 kp
   int err = 0;
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
     int it = 0;
-    const int per_tile = (rows ? nchunks : 0) + (cols ? nchunks : 0);
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x) {
-      for (int q = 0; q < per_tile; ++q, ++it) {
-        const int s = it % a.nstages;
-        const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
-        if (!warp_wait(&sm.empty[s], ph ^ 1u, lane)) {
-          err = LSF_ERR_TIMEOUT;
-          break;
+    auto issue = [&](int64_t tile, int c, bool with_t) -> bool {
+      const int s = it % a.nstages;
+      const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
+      ++it;
+      if (!warp_wait(&sm.empty[s], ph ^ 1u, lane)) return false;
+      if (lane == 0) {
+        unsigned char* dst = sm.stages + static_cast<size_t>(s) * stage_bytes;
+        mbar_arrive_expect_tx(&sm.full[s], kStageBytes + (with_t ? 2 * tbox : 0));
+        const int y = static_cast<int>(tile * kTileRows);
+        const int x = c * kChunkCols;
+        tma_box(dst, &fmap, x, y, 0, &sm.full[s]);
+        tma_box(dst + kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s]);
+        tma_box(dst + 2 * kBoxBytes, &fmap, x, y, 1, &sm.full[s]);
+        tma_box(dst + 3 * kBoxBytes, &fmap, x + kBoxCols, y, 1, &sm.full[s]);
+        if (with_t) {
+          tma_box2d(dst + kStageBytes, &tmap, x, 0, &sm.full[s]);
+          tma_box2d(dst + kStageBytes + tbox, &tmap, x + kBoxCols, 0, &sm.full[s]);
         }
-        if (lane == 0) {
-          const int c = q % nchunks;
-          unsigned char* dst = sm.stages + static_cast<size_t>(s) * kStageBytes;
-          mbar_arrive_expect_tx(&sm.full[s], kStageBytes);
-          const int y = static_cast<int>(tile * kTileRows);
-          tma_box(dst, &fmap, c * kChunkCols, y, 0, &sm.full[s]);
-          tma_box(dst + kBoxBytes, &fmap, c * kChunkCols + kBoxCols, y, 0, &sm.full[s]);
-          tma_box(dst + 2 * kBoxBytes, &fmap, c * kChunkCols, y, 1, &sm.full[s]);
-          tma_box(dst + 3 * kBoxBytes, &fmap, c * kChunkCols + kBoxCols, y, 1, &sm.full[s]);
-        }
-        __syncwarp();
+      }
+      __syncwarp();
+      return true;
+    };
+    for (int ph = 0; ph < sch.phases() && !err; ++ph) {
+      const int64_t tc = blockIdx.x + static_cast<int64_t>(ph - sch.lag) * gridDim.x;
+      const int64_t tr = blockIdx.x + static_cast<int64_t>(ph) * gridDim.x;
+      for (int c = 0; c < nchunks && !err; ++c) {
+        if (sch.r_on(ph) && !issue(tr, c, true)) err = LSF_ERR_TIMEOUT;
+        if (!err && sch.c_on(ph) && !issue(tc, c, false)) err = LSF_ERR_TIMEOUT;
       }
     }
     // drain: every issued copy has landed before the CTA may exit
@@ -308,60 +338,60 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     constexpr uint32_t kColHi = idesc_bf16(2 * KP, 1);
     constexpr uint32_t kColLo = idesc_bf16(KP, 1);
     const uint32_t st_base = smem_u32(sm.stages);
-    const uint32_t sT_base = smem_u32(sm.sT);
     const uint32_t sU_base = smem_u32(sm.sU);
     const uint32_t region = 2 * KP * 128;  // bytes of one 64-wide K block of a B operand
-    int it = 0, j = 0;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x, ++j) {
-      if (rows) {
-        if (j > 0 && !warp_wait(sm.s_empty, static_cast<uint32_t>(j - 1) & 1u, lane)) {
+    int it = 0;
+    auto take = [&](uint32_t& st) -> bool {
+      const int s = it % a.nstages;
+      const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
+      ++it;
+      if (!warp_wait(&sm.full[s], ph, lane)) return false;
+      tc_fence_after();
+      st = st_base + s * stage_bytes;
+      return true;
+    };
+    auto release = [&]() {
+      if (lane == 0) mma_commit(&sm.empty[(it - 1) % a.nstages]);
+      __syncwarp();
+    };
+    for (int ph = 0; ph < sch.phases() && !err; ++ph) {
+      const int jc = ph - sch.lag, jr = ph;
+      const bool con = sch.c_on(ph), ron = sch.r_on(ph);
+      if (ron && jr >= 2) {
+        if (!warp_wait(&sm.s_empty[jr & 1], static_cast<uint32_t>((jr - 2) >> 1) & 1u, lane)) {
           err = LSF_ERR_TIMEOUT;
           break;
         }
         tc_fence_after();
-        for (int c = 0; c < nchunks; ++c, ++it) {
-          const int s = it % a.nstages;
-          if (!warp_wait(&sm.full[s], static_cast<uint32_t>(it / a.nstages) & 1u, lane)) {
-            err = LSF_ERR_TIMEOUT;
-            break;
-          }
-          tc_fence_after();
+      }
+      const uint32_t dS = tmem_S + (jr & 1) * 2 * KP;
+      for (int c = 0; c < nchunks && !err; ++c) {
+        uint32_t st;
+        if (ron) {
+          if (!take(st)) { err = LSF_ERR_TIMEOUT; break; }
           if (lane == 0) {
-            const uint32_t st = st_base + s * kStageBytes;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t a_hi = st + h * kBoxBytes + ks * 32;
-                const uint32_t b = sT_base + (2 * c + h) * region + ks * 32;
+                const uint32_t b = st + kStageBytes + h * tbox + ks * 32;
                 const uint64_t bd = smem_desc(b, 16, 1024);
-                mma_bf16(tmem_S, smem_desc(a_hi, 16, 1024), bd, kRowHi, (c | h | ks) != 0);
-                mma_bf16(tmem_S, smem_desc(a_hi + 2 * kBoxBytes, 16, 1024), bd, kRowLo, 1);
+                mma_bf16(dS, smem_desc(a_hi, 16, 1024), bd, kRowHi, (c | h | ks) != 0);
+                mma_bf16(dS, smem_desc(a_hi + 2 * kBoxBytes, 16, 1024), bd, kRowLo, 1);
               }
             }
-            mma_commit(&sm.empty[s]);
           }
-          __syncwarp();
+          release();
         }
-        if (err) break;
-        if (lane == 0) mma_commit(sm.s_full);
-        __syncwarp();
-      }
-      if (cols) {
-        if (!warp_wait(sm.u_full, static_cast<uint32_t>(j) & 1u, lane)) {
-          err = LSF_ERR_TIMEOUT;
-          break;
-        }
-        tc_fence_after();
-        for (int c = 0; c < nchunks; ++c, ++it) {
-          const int s = it % a.nstages;
-          if (!warp_wait(&sm.full[s], static_cast<uint32_t>(it / a.nstages) & 1u, lane)) {
-            err = LSF_ERR_TIMEOUT;
-            break;
+        if (con) {
+          if (c == 0) {
+            // the scalings of tile jc, formed while this phase's first row chunk ran
+            if (!warp_wait(sm.u_full, static_cast<uint32_t>(jc) & 1u, lane)) { err = LSF_ERR_TIMEOUT; break; }
+            tc_fence_after();
           }
-          tc_fence_after();
+          if (!take(st)) { err = LSF_ERR_TIMEOUT; break; }
           if (lane == 0) {
-            const uint32_t st = st_base + s * kStageBytes;
             const uint32_t dT = tmem_T + c * 2 * KP;
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
@@ -370,17 +400,19 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
               const uint32_t a_hi = st + ks * 2048;
               const uint32_t b = sU_base + (ks >> 2) * region + (ks & 3) * 32;
               const uint64_t bd = smem_desc(b, 16, 1024);
-              mma_bf16(dT, smem_desc(a_hi, kBoxBytes, 1024), bd, kColHi, (j > 0 || ks > 0) ? 1 : 0);
+              mma_bf16(dT, smem_desc(a_hi, kBoxBytes, 1024), bd, kColHi, (jc > 0 || ks > 0) ? 1 : 0);
               mma_bf16(dT, smem_desc(a_hi + 2 * kBoxBytes, kBoxBytes, 1024), bd, kColLo, 1);
             }
-            mma_commit(&sm.empty[s]);
           }
-          __syncwarp();
+          release();
         }
-        if (err) break;
-        if (lane == 0) mma_commit(sm.u_empty);
-        __syncwarp();
       }
+      if (err) break;
+      if (lane == 0) {
+        if (ron) mma_commit(&sm.s_full[jr & 1]);
+        if (con) mma_commit(sm.u_empty);
+      }
+      __syncwarp();
     }
     if (lane == 0) mma_commit(sm.t_done);
     __syncwarp();
@@ -393,13 +425,20 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 #pragma unroll
     for (int p = 0; p < KP; ++p) resid[p] = 0.0;
     uint32_t bad = 0u;
-    int j = 0;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles && !err; tile += gridDim.x, ++j) {
-      const int64_t row = tile * kTileRows + rloc;
+    for (int j = 0; j < sch.nt && !err; ++j) {
+      const int64_t row = (blockIdx.x + static_cast<int64_t>(j) * gridDim.x) * kTileRows + rloc;
       const bool valid = row < n;
+      // this tile's weights (and previous scalings) are fetched before the wait
+      float w[KP], o[KP];
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        const bool on = p < a.k && valid;
+        w[p] = (on && rows) ? __ldg(a.w + p * n + row) : 0.f;
+        o[p] = (on && a.mode != kMultiUpdate) ? __ldg(a.old + p * n + row) : 0.f;
+      }
       float u[KP];
       if (rows) {
-        if (!warp_wait(sm.s_full, static_cast<uint32_t>(j) & 1u, lane)) {
+        if (!warp_wait(&sm.s_full[j & 1], static_cast<uint32_t>(j >> 1) & 1u, lane)) {
           err = LSF_ERR_TIMEOUT;
           break;
         }
@@ -408,32 +447,30 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 #pragma unroll
         for (int h = 0; h < 2 * KP / 32; ++h) {
           float v[32];
-          tmem_ld32(tmem_S + lane_base + 32 * h, v);
+          tmem_ld32(tmem_S + (j & 1) * 2 * KP + lane_base + 32 * h, v);
 #pragma unroll
           for (int i = 0; i < 32; ++i) d[32 * h + i] = v[i];
         }
         tc_fence_before();
-        mbar_arrive(sm.s_empty);
+        mbar_arrive(&sm.s_empty[j & 1]);
 #pragma unroll
         for (int p = 0; p < KP; ++p) {
           const float s = d[p] + d[KP + p];
           u[p] = 0.f;
           if (p < a.k && valid) {
-            const float w = __ldg(a.w + p * n + row);
             if (a.mode == kMultiUpdate) {
-              const float v = w / s;
+              const float v = w[p] / s;
               if (!(v > 0.f && v < INFINITY)) bad |= 1u << p;
               a.out[p * n + row] = v;
               u[p] = v;
             } else {
-              const float o = __ldg(a.old + p * n + row);
-              resid[p] += fabs(static_cast<double>(o) * static_cast<double>(s) - static_cast<double>(w));
+              resid[p] += fabs(static_cast<double>(o[p]) * static_cast<double>(s) - static_cast<double>(w[p]));
             }
           }
         }
       } else {
 #pragma unroll
-        for (int p = 0; p < KP; ++p) u[p] = (p < a.k && valid) ? __ldg(a.old + p * n + row) : 0.f;
+        for (int p = 0; p < KP; ++p) u[p] = o[p];
       }
       if (cols) {
         if (j > 0 && !warp_wait(sm.u_empty, static_cast<uint32_t>(j - 1) & 1u, lane)) {
@@ -480,7 +517,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       for (int p = 0; p < KP; ++p) {
         double v = resid[p];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
         if (lane == 0) sm.red[quarter * KP + p] = v;
       }
     }
@@ -510,9 +547,13 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 
 // Sum of the per-CTA partials in CTA order: a block covers 32 outputs with 8
 // warps, warp w summing CTAs w, w + 8, ...; the 8 warp sums are folded in order.
+// Also writes the bf16 split of the result, [T_hi; T_lo] (2 kp x ldr2), which
+// the next pass's row products load with TMA.
 __global__ void __launch_bounds__(256) multi_reduce_kernel(const float* __restrict__ part, int G,
-                                                           int total, float* __restrict__ t_out) {
+                                                           int kp, int ldr2, float* __restrict__ t_out,
+                                                           uint16_t* __restrict__ t_pair) {
   __shared__ double s[8][33];
+  const int total = kp * ldr2;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * 32 + lane;
   double acc = 0.0;
@@ -524,7 +565,12 @@ __global__ void __launch_bounds__(256) multi_reduce_kernel(const float* __restri
     double t = 0.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) t += s[i][lane];
-    t_out[idx] = static_cast<float>(t);
+    const float tf = static_cast<float>(t);
+    t_out[idx] = tf;
+    uint16_t hi, lo;
+    split_bf16(tf, hi, lo);
+    t_pair[idx] = hi;           // row p of the hi block
+    t_pair[total + idx] = lo;   // row kp + p: the lo block
   }
 }
 
@@ -613,26 +659,44 @@ int make_pair_map(const uint16_t* F2, int64_t n, int ldr2, CUtensorMap* map) {
   return LSF_OK;
 }
 
+// Tensor map of a split r-vector block [T_hi; T_lo] (2 kp rows x ldr2 bf16):
+// boxes of 64 features x 2 kp rows, 128-byte swizzle (the K-major B layout).
+int make_t_map(const uint16_t* t_pair, int kp, int ldr2, CUtensorMap* map) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(ldr2), static_cast<cuuint64_t>(2 * kp)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldr2) * 2};
+  cuuint32_t box[2] = {kBoxCols, static_cast<cuuint32_t>(2 * kp)};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(t_pair), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return LSF_OK;
+}
+
 int multi_kp(int k) { return k <= 16 ? 16 : 32; }
 
+// TMEM columns: D_S double-buffered (2 x 2 kp) and one 2 kp block per feature chunk.
+int tmem_need(int kp, int ldr2) { return 2 * kp * (2 + ldr2 / kChunkCols); }
+
 uint32_t tmem_columns(int kp, int ldr2) {
-  const int need = 2 * kp * (1 + ldr2 / kChunkCols);
   uint32_t c = 32;
-  while (static_cast<int>(c) < need) c <<= 1;
+  while (static_cast<int>(c) < tmem_need(kp, ldr2)) c <<= 1;
   return c;
 }
 
 // The shapes this kernel takes: ldr2 a multiple of 128 up to 1024, k <= 32, the
-// accumulators within TMEM's 512 columns and the operands within shared memory.
+// accumulators within TMEM's 512 columns and two ring stages in shared memory.
 int check_multi_shape(int ldr2, int k) {
   if (k < 1 || k > 32) return fail(LSF_ERR_UNSUPPORTED, "multi solve: k must be in [1, 32]");
   if (ldr2 < 128 || ldr2 % 128 != 0 || ldr2 > 1024)
     return fail(LSF_ERR_UNSUPPORTED, "multi solve: ldr2 must be a multiple of 128 in [128, 1024]");
   const int kp = multi_kp(k);
-  if (2 * kp * (1 + ldr2 / kChunkCols) > 512)
+  if (tmem_need(kp, ldr2) > 512)
     return fail(LSF_ERR_UNSUPPORTED, "multi solve: %d right-hand sides at ldr2 = %d exceed TMEM", k, ldr2);
-  if (multi_smem_bytes(kp, ldr2, 2, true) > static_cast<size_t>(device_info().smem_optin))
-    return fail(LSF_ERR_UNSUPPORTED, "multi solve: %d right-hand sides at ldr2 = %d exceed shared memory", k, ldr2);
+  if (multi_smem_bytes(kp, 2) > static_cast<size_t>(device_info().smem_optin))
+    return fail(LSF_ERR_UNSUPPORTED, "multi solve: shared memory too small");
   return LSF_OK;
 }
 
@@ -642,23 +706,25 @@ size_t align256m(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 size_t multi_extra_bytes(int ldr2, int kp) {
   const size_t G = static_cast<size_t>(multi_grid_max());
-  return align256m(G * kp * ldr2 * sizeof(float)) + align256m(G * kp * sizeof(double));
+  return align256m(G * kp * ldr2 * sizeof(float)) + align256m(G * kp * sizeof(double)) +
+         2 * align256m(static_cast<size_t>(kp) * ldr2 * 4);
 }
 
 struct MultiWs {
   Workspace ws;
   float* part;
   double* rpart;
+  uint16_t* t_pair[2];  // bf16 splits of Tu (0) and Tv (1)
 };
 
 template <int KP>
-int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& map, cudaStream_t st, int* grid_out) {
+int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& fmap, const CUtensorMap& tmap,
+                    cudaStream_t st, int* grid_out) {
   MultiArgs a = a0;
-  const bool rows = a.mode != kMultiAxpy;
   const size_t optin = static_cast<size_t>(device_info().smem_optin);
   int stages = kMaxStages;
-  while (stages > 2 && multi_smem_bytes(KP, a.ldr2, stages, rows) > optin) --stages;
-  const size_t smem = multi_smem_bytes(KP, a.ldr2, stages, rows);
+  while (stages > 2 && multi_smem_bytes(KP, stages) > optin) --stages;
+  const size_t smem = multi_smem_bytes(KP, stages);
   if (smem > optin) return fail(LSF_ERR_UNSUPPORTED, "multi pass: %zu bytes of shared memory", smem);
   a.nstages = stages;
   a.tmem_cols = tmem_columns(KP, a.ldr2);
@@ -675,17 +741,19 @@ int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& map, cudaStream_t st
                        static_cast<double>(a.n) * a.k * 4.0 * (a.mode == kMultiAxpy ? 1 : 2);
   {
     LaunchScope ls(st, LSF_KERNEL_PASS_MULTI, bytes);
-    multi_pass_kernel<KP><<<grid, kMultiThreads, smem, st>>>(map, a);
+    multi_pass_kernel<KP><<<grid, kMultiThreads, smem, st>>>(fmap, tmap, a);
     LSF_TRY(check_launch("multi_pass_kernel"));
   }
   *grid_out = grid;
   return LSF_OK;
 }
 
-// One pass and its reduction. Returns LSF_OK or an error status.
-int multi_pass(int mode, int k, int64_t n, int ldr2, const CUtensorMap& map, const float* t_in,
-               const float* w, const float* old, float* out, float* t_out, lsf_result* res,
-               const MultiWs& mw, cudaStream_t st) {
+// One pass and its reduction. tmap: the split r-vectors the row products read
+// (Update, Dot); t_out, t_pair_out: the reduced transposed products and their
+// split (Update, Axpy). Returns LSF_OK or an error status.
+int multi_pass(int mode, int k, int64_t n, int ldr2, const CUtensorMap& fmap, const CUtensorMap& tmap,
+               const float* w, const float* old, float* out, float* t_out, uint16_t* t_pair_out,
+               lsf_result* res, const MultiWs& mw, cudaStream_t st) {
   const int kp = multi_kp(k);
   MultiArgs a{};
   a.n = n;
@@ -693,7 +761,6 @@ int multi_pass(int mode, int k, int64_t n, int ldr2, const CUtensorMap& map, con
   a.ldr2 = ldr2;
   a.k = k;
   a.mode = mode;
-  a.t_in = t_in;
   a.w = w;
   a.old = old;
   a.out = out;
@@ -701,14 +768,15 @@ int multi_pass(int mode, int k, int64_t n, int ldr2, const CUtensorMap& map, con
   a.rpart = mw.rpart;
   a.res = res;
   int grid = 0;
-  LSF_TRY(kp == 16 ? launch_multi_kp<16>(a, map, st, &grid) : launch_multi_kp<32>(a, map, st, &grid));
+  LSF_TRY(kp == 16 ? launch_multi_kp<16>(a, fmap, tmap, st, &grid)
+                   : launch_multi_kp<32>(a, fmap, tmap, st, &grid));
   LaunchScope ls(st, LSF_KERNEL_OTHER, 4.0 * grid * kp * ldr2);
   if (mode == kMultiDot) {
     multi_residual_kernel<<<1, 32, 0, st>>>(mw.rpart, grid, kp, k, res);
     return check_launch("multi_residual_kernel");
   }
   const int total = kp * ldr2;
-  multi_reduce_kernel<<<(total + 31) / 32, 256, 0, st>>>(mw.part, grid, total, t_out);
+  multi_reduce_kernel<<<(total + 31) / 32, 256, 0, st>>>(mw.part, grid, kp, ldr2, t_out, t_pair_out);
   return check_launch("multi_reduce_kernel");
 }
 
@@ -766,9 +834,15 @@ int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
   mw.part = reinterpret_cast<float*>(p);
   p += align256m(static_cast<size_t>(multi_grid_max()) * kp * ldr2 * sizeof(float));
   mw.rpart = reinterpret_cast<double*>(p);
-  CUtensorMap mx, my;
+  p += align256m(static_cast<size_t>(multi_grid_max()) * kp * sizeof(double));
+  mw.t_pair[0] = reinterpret_cast<uint16_t*>(p);
+  p += align256m(static_cast<size_t>(kp) * ldr2 * 4);
+  mw.t_pair[1] = reinterpret_cast<uint16_t*>(p);
+  CUtensorMap mx, my, mtu, mtv;
   LSF_TRY(make_pair_map(x->F2, x->n, ldr2, &mx));
   LSF_TRY(make_pair_map(y->F2, y->n, ldr2, &my));
+  LSF_TRY(make_t_map(mw.t_pair[0], kp, ldr2, &mtu));
+  LSF_TRY(make_t_map(mw.t_pair[1], kp, ldr2, &mtv));
   if (cudaMemsetAsync(out->Tu, 0, sizeof(float) * kp * ldr2, st) != cudaSuccess ||
       cudaMemsetAsync(out->Tv, 0, sizeof(float) * kp * ldr2, st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "multi solve: memset failed");
@@ -779,16 +853,17 @@ int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
     multi_init_kernel<<<grid, 256, 0, st>>>(y->shift, y->n, k, mw.ws.keys, out->V, results);
     LSF_TRY(check_launch("multi_init_kernel"));
   }
-  LSF_TRY(multi_pass(kMultiAxpy, k, y->n, ldr2, my, nullptr, nullptr, out->V, nullptr, out->Tv,
-                     results, mw, st));
+  // t_v = zeta~^T v~ from v = 1; then u-halves (row products with t_v) and v-halves
+  LSF_TRY(multi_pass(kMultiAxpy, k, y->n, ldr2, my, mtv, nullptr, out->V, nullptr, out->Tv,
+                     mw.t_pair[1], results, mw, st));
   for (int it = 0; it < iters; ++it) {
-    LSF_TRY(multi_pass(kMultiUpdate, k, x->n, ldr2, mx, out->Tv, x->W, nullptr, out->U, out->Tu,
-                       results, mw, st));
-    LSF_TRY(multi_pass(kMultiUpdate, k, y->n, ldr2, my, out->Tu, y->W, nullptr, out->V, out->Tv,
-                       results, mw, st));
+    LSF_TRY(multi_pass(kMultiUpdate, k, x->n, ldr2, mx, mtv, x->W, nullptr, out->U, out->Tu,
+                       mw.t_pair[0], results, mw, st));
+    LSF_TRY(multi_pass(kMultiUpdate, k, y->n, ldr2, my, mtu, y->W, nullptr, out->V, out->Tv,
+                       mw.t_pair[1], results, mw, st));
   }
-  LSF_TRY(multi_pass(kMultiDot, k, x->n, ldr2, mx, out->Tv, x->W, out->U, nullptr, nullptr, results,
-                     mw, st));
+  LSF_TRY(multi_pass(kMultiDot, k, x->n, ldr2, mx, mtv, x->W, out->U, nullptr, nullptr, nullptr,
+                     results, mw, st));
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
     multi_iters_kernel<<<1, 32, 0, st>>>(results, k, iters);
