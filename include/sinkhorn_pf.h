@@ -535,6 +535,18 @@ int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
                     const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* out,
                     lsf_result* results, void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * Tuning of lsf_solve_multi (process-wide, not thread-safe against concurrent
+ * solves). The pass reads each 128 x 128 feature chunk twice: from HBM for the
+ * row products and again, a tile later, for the transposed products, which
+ * must find it in L2. chunks: how many row chunks ahead of its shared-memory
+ * ring the pass requests into L2 (0 to 16; default 0). l2_hints: the L2
+ * eviction priority of the chunk reads: 0 default for both, 1 (default) evict
+ * first on the second read (the chunk's last use), 2 additionally evict last
+ * on the first read. Errors: LSF_ERR_ARG outside those ranges.
+ */
+int lsf_set_multi_prefetch(int chunks, int l2_hints);
+
 /* Kernel classes timed by the optional event recorder. */
 typedef enum {
   LSF_KERNEL_PASS = 0,       /* fused Sinkhorn passes (stored features)   */

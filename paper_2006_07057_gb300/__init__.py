@@ -336,6 +336,12 @@ def lsf_split_features(F: torch.Tensor, r: int, ldr2: int | None = None, F2=None
     return F2
 
 
+def lsf_set_multi_prefetch(chunks: int, l2_hints: int = 1) -> None:
+    """Feature chunks the multi-right-hand-side pass requests into L2 ahead of its
+    ring, and the L2 eviction hints of its two reads of each chunk (0, 1, 2)."""
+    check(lib().lsf_set_multi_prefetch(int(chunks), int(l2_hints)), "lsf_set_multi_prefetch")
+
+
 def lsf_multi_workspace_bytes(ldr2: int, k: int) -> int:
     b = ctypes.c_size_t(0)
     check(lib().lsf_multi_workspace_bytes(int(ldr2), int(k), ctypes.byref(b)),

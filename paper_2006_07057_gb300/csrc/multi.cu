@@ -62,6 +62,8 @@ struct MultiArgs {
   int k;             // real right-hand sides (<= kp)
   int mode;
   int nstages;
+  int prefetch;        // row chunks requested into L2 ahead of the ring
+  int l2_hints;        // 0 none, 1 evict-first on the re-read, 2 also evict-last on the first read
   uint32_t tmem_cols;
   const float* w;      // k x n weights (Update, Dot)
   const float* old;    // k x n previous scalings (Dot) or the given scalings (Axpy)
@@ -133,14 +135,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // TMA: one 64-feature x 128-point box of plane z at feature x, point y (the 3-D
-// map of the feature planes).
+// map of the feature planes), with an L2 eviction policy for the lines read.
 __device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                        uint64_t* bar) {
+                                        uint64_t* bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
+}
+
+// L2 policies: keep (a row chunk will be read again), drop first (its last read),
+// or the default priority.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// L2 prefetch of one box of the 3-D feature map (no shared memory is written).
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(map),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
 }
 
 // TMA: one box of a 2-D tensor map at (x, y).
@@ -294,7 +321,11 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
     int it = 0;
+    // L2 policy of the first (row) and the last (transposed) read of a chunk
+    const uint64_t pol_r = a.l2_hints == 2 ? policy_evict_last() : policy_evict_normal();
+    const uint64_t pol_c = a.l2_hints >= 1 ? policy_evict_first() : policy_evict_normal();
     auto issue = [&](int64_t tile, int c, bool with_t) -> bool {
+      const uint64_t pol = with_t ? pol_r : pol_c;
       const int s = it % a.nstages;
       const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
       ++it;
@@ -304,10 +335,10 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         mbar_arrive_expect_tx(&sm.full[s], kStageBytes + (with_t ? 2 * tbox : 0));
         const int y = static_cast<int>(tile * kTileRows);
         const int x = c * kChunkCols;
-        tma_box(dst, &fmap, x, y, 0, &sm.full[s]);
-        tma_box(dst + kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s]);
-        tma_box(dst + 2 * kBoxBytes, &fmap, x, y, 1, &sm.full[s]);
-        tma_box(dst + 3 * kBoxBytes, &fmap, x + kBoxCols, y, 1, &sm.full[s]);
+        tma_box(dst, &fmap, x, y, 0, &sm.full[s], pol);
+        tma_box(dst + kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s], pol);
+        tma_box(dst + 2 * kBoxBytes, &fmap, x, y, 1, &sm.full[s], pol);
+        tma_box(dst + 3 * kBoxBytes, &fmap, x + kBoxCols, y, 1, &sm.full[s], pol);
         if (with_t) {
           tma_box2d(dst + kStageBytes, &tmap, x, 0, &sm.full[s]);
           tma_box2d(dst + kStageBytes + tbox, &tmap, x + kBoxCols, 0, &sm.full[s]);
@@ -316,11 +347,31 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       __syncwarp();
       return true;
     };
+    // Row chunks come from HBM: a.prefetch of them ahead are requested into L2
+    // (no shared memory held), so more HBM requests are in flight than the ring
+    // holds; the distance stays small because L2 must also keep each tile until
+    // its transposed-product re-read.
+    const int rtotal = rows ? sch.nt * nchunks : 0;
+    auto prefetch = [&](int q) {
+      if (lane != 0 || q >= rtotal) return;
+      const int y = static_cast<int>((blockIdx.x + static_cast<int64_t>(q / nchunks) * gridDim.x) * kTileRows);
+      const int x = (q % nchunks) * kChunkCols;
+      tma_prefetch(&fmap, x, y, 0);
+      tma_prefetch(&fmap, x + kBoxCols, y, 0);
+      tma_prefetch(&fmap, x, y, 1);
+      tma_prefetch(&fmap, x + kBoxCols, y, 1);
+    };
+    for (int q = 0; q < a.prefetch; ++q) prefetch(q);
+    int rq = 0;
     for (int ph = 0; ph < sch.phases() && !err; ++ph) {
       const int64_t tc = blockIdx.x + static_cast<int64_t>(ph - sch.lag) * gridDim.x;
       const int64_t tr = blockIdx.x + static_cast<int64_t>(ph) * gridDim.x;
       for (int c = 0; c < nchunks && !err; ++c) {
-        if (sch.r_on(ph) && !issue(tr, c, true)) err = LSF_ERR_TIMEOUT;
+        if (sch.r_on(ph)) {
+          prefetch(rq + a.prefetch);
+          ++rq;
+          if (!issue(tr, c, true)) err = LSF_ERR_TIMEOUT;
+        }
         if (!err && sch.c_on(ph) && !issue(tc, c, false)) err = LSF_ERR_TIMEOUT;
       }
     }
@@ -677,6 +728,9 @@ int make_t_map(const uint16_t* t_pair, int kp, int ldr2, CUtensorMap* map) {
 
 int multi_kp(int k) { return k <= 16 ? 16 : 32; }
 
+int g_multi_prefetch = 0;  // row chunks prefetched into L2 (lsf_set_multi_prefetch)
+int g_multi_l2_hints = 1;  // L2 eviction hints of the chunk reads (lsf_set_multi_prefetch)
+
 // TMEM columns: D_S double-buffered (2 x 2 kp) and one 2 kp block per feature chunk.
 int tmem_need(int kp, int ldr2) { return 2 * kp * (2 + ldr2 / kChunkCols); }
 
@@ -727,6 +781,8 @@ int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& fmap, const CUtensor
   const size_t smem = multi_smem_bytes(KP, stages);
   if (smem > optin) return fail(LSF_ERR_UNSUPPORTED, "multi pass: %zu bytes of shared memory", smem);
   a.nstages = stages;
+  a.prefetch = g_multi_prefetch;
+  a.l2_hints = g_multi_l2_hints;
   a.tmem_cols = tmem_columns(KP, a.ldr2);
   static int configured[2] = {0, 0};
   const int dev = device_info().device;
@@ -798,6 +854,14 @@ int lsf_split_features(const float* F, int64_t n, int ldr, int r, uint16_t* F2, 
   LaunchScope ls(st, LSF_KERNEL_FEATURES, static_cast<double>(n) * (4.0 * ldr + 4.0 * ldr2));
   split_features_kernel<<<grid, 256, 0, st>>>(F, n, ldr, r, F2, ldr2);
   return check_launch("split_features_kernel");
+}
+
+int lsf_set_multi_prefetch(int chunks, int l2_hints) {
+  if (chunks < 0 || chunks > 16) return fail(LSF_ERR_ARG, "lsf_set_multi_prefetch: chunks must be in [0, 16]");
+  if (l2_hints < 0 || l2_hints > 2) return fail(LSF_ERR_ARG, "lsf_set_multi_prefetch: l2_hints must be 0, 1 or 2");
+  g_multi_prefetch = chunks;
+  g_multi_l2_hints = l2_hints;
+  return LSF_OK;
 }
 
 int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes) {
