@@ -16,19 +16,21 @@
 // product takes the three terms hi*hi + hi*lo + lo*hi, accumulated in FP32 in
 // TMEM; the dropped lo*lo term is below 2^-16 relative.
 //
-// Kernel. One CTA per SM, persistent over tiles of 128 points. Per tile the
-// producer warp streams the tile's feature chunks (128 points x 128 features,
-// both planes, 64 KB) into a shared-memory ring with TMA (128-byte swizzle), twice:
-// first for the row products, then again (from L2) for the transposed products.
-// One elected thread issues the MMAs:
-//   row sweep:  D_S (128 x 2kp)  += A . [T_hi; T_lo]^T   A = F chunk, K-major (K = features)
-//               D_S (128 x kp)   += A_lo . T_hi^T
+// Kernel. One CTA per SM, persistent over tiles of 64 points. Per tile the
+// producer warp streams the tile's feature chunks (64 points x 128 features,
+// both planes, 32 KB) into a shared-memory ring with TMA (128-byte swizzle), twice:
+// first for the row products, then again (from L2, a tile later) for the
+// transposed products. One elected thread issues the MMAs:
+//   row sweep:  D_S (64 x 2kp)    += A . [T_hi; T_lo]^T   A = F chunk, K-major (K = features)
+//               D_S (64 x kp)     += A_lo . T_hi^T
 //   col sweep:  D_T[c] (128 x 2kp) += A^T . [U_hi; U_lo]  A^T = the same smem chunk read
 //               MN-major (M = features, K = points), no transposed copy
-// Four epilogue warps read D_S from TMEM (thread = point), form u = a / s, write
-// it, split it into bf16 hi/lo and store it as the B operand of the col sweep.
-// D_T holds this CTA's partial T' for the whole launch; at the end it is read out
-// to a per-CTA slot and summed over the CTAs in a fixed order by a second kernel.
+// Four epilogue warps read D_S from TMEM (one point per thread, lanes 0-15 of
+// each warp), form u = a / s, write it, split it into bf16 hi/lo and store it as
+// the B operand of the col sweep. D_T holds this CTA's partial T' for the whole
+// launch; at the end it is read out to a per-CTA slot and summed over the CTAs
+// in a fixed order by a second kernel. 64-point tiles keep the data between a
+// chunk's two reads at 256 KB per SM, which L2 holds for all SMs at once.
 // Every wait is bounded; a wait that runs out sets LSF_ERR_TIMEOUT and the CTA
 // still drains its copies and frees its TMEM.
 #include <cuda.h>
@@ -45,13 +47,13 @@
 namespace lsf {
 namespace {
 
-constexpr int kTileRows = 128;                 // points per tile (M of the row product)
+constexpr int kTileRows = 64;                  // points per tile (M of the row product)
 constexpr int kChunkCols = 128;                // features per chunk (M of the col product)
 constexpr int kBoxCols = 64;                   // features per TMA box: 128 B of bf16
-constexpr int kBoxBytes = kTileRows * kBoxCols * 2;   // 16 KB
-constexpr int kStageBytes = 4 * kBoxBytes;     // two boxes of each plane: 64 KB
+constexpr int kBoxBytes = kTileRows * kBoxCols * 2;   // 8 KB
+constexpr int kStageBytes = 4 * kBoxBytes;     // two boxes of each plane: 32 KB
 constexpr int kMultiThreads = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 6;
 
 enum MultiMode : int { kMultiUpdate = 0, kMultiAxpy = 1, kMultiDot = 2 };
 
@@ -85,10 +87,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-// Instruction descriptor of kind::f16 with bf16 A and B, FP32 D, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n, int a_mn_major) {
+// Instruction descriptor of kind::f16 with bf16 A and B, FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, int a_mn_major) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn_major) << 15) |
-         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -192,19 +194,23 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
   lo = __bfloat16_as_ushort(l);
 }
 
-// Shared memory of the pass. A ring stage holds one feature chunk (both planes,
-// 64 KB) and, for a row-product item, the matching 128-feature block of the
-// split r-vectors [T_hi; T_lo] (2 kp rows x 128 features, loaded by TMA from the
-// pair buffer the previous pass's reduction wrote).
+// Shared memory of the pass. A ring stage holds one feature chunk (64 points x
+// 128 features, both planes, 32 KB) as four 8 KB boxes [hi h=0 | lo h=0 | hi h=1 |
+// lo h=1] (h: the 64-feature half), so that the hi and lo boxes of a half form
+// one 128-row K-major operand, and, for a row-product item, the matching
+// 128-feature block of the split r-vectors [T_hi; T_lo] (2 kp rows x 128
+// features, loaded by TMA from the pair buffer the previous pass's reduction
+// wrote).
 struct MultiSmem {
-  unsigned char* stages;  // [S][64 KB features | 2 x (2 kp x 128 B) r-vector boxes]
-  uint16_t* sU;           // [2 K blocks][2 kp][64]: the split scalings of one tile
+  unsigned char* stages;  // [S][32 KB features | 2 x (2 kp x 128 B) r-vector boxes]
+  uint16_t* sU;           // [2][2 kp][64]: the split scalings of a tile, double-buffered
+  float* xbuf;            // [2][64][kp]: lo-plane row products handed between epilogue warps
   uint64_t* full;         // [S]
   uint64_t* empty;        // [S]
   uint64_t* s_full;       // [2] row products of a tile in D_S[b]
   uint64_t* s_empty;      // [2] D_S[b] read out
-  uint64_t* u_full;       // sU written
-  uint64_t* u_empty;      // sU read by the transposed products
+  uint64_t* u_full;       // [2] sU[b] written
+  uint64_t* u_empty;      // [2] sU[b] read by the transposed products
   uint64_t* t_done;       // every MMA of the launch completed
   uint32_t* tmem_slot;
   double* red;            // [4][kp]
@@ -213,9 +219,13 @@ struct MultiSmem {
 __host__ __device__ inline int multi_tbox_bytes(int kp) { return 2 * kp * 128; }
 __host__ __device__ inline int multi_stage_bytes(int kp) { return kStageBytes + 2 * multi_tbox_bytes(kp); }
 
+__host__ __device__ inline size_t multi_u_bytes(int kp) { return static_cast<size_t>(2 * kp) * kTileRows * 2; }
+
+__host__ __device__ inline size_t multi_x_bytes(int kp) { return static_cast<size_t>(kTileRows) * kp * 4; }
+
 __host__ __device__ inline size_t multi_smem_bytes(int kp, int stages) {
-  return 1024 + static_cast<size_t>(stages) * multi_stage_bytes(kp) + static_cast<size_t>(kp) * 512 +
-         256 + static_cast<size_t>(4) * kp * 8;
+  return 1024 + static_cast<size_t>(stages) * multi_stage_bytes(kp) + 2 * multi_u_bytes(kp) +
+         2 * multi_x_bytes(kp) + 256 + static_cast<size_t>(4) * kp * 8;
 }
 
 __device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int stages) {
@@ -225,16 +235,18 @@ __device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, in
   s.stages = p;
   p += static_cast<size_t>(stages) * multi_stage_bytes(kp);
   s.sU = reinterpret_cast<uint16_t*>(p);
-  p += static_cast<size_t>(kp) * 512;
+  p += 2 * multi_u_bytes(kp);
+  s.xbuf = reinterpret_cast<float*>(p);
+  p += 2 * multi_x_bytes(kp);
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   s.full = b;
   s.empty = b + kMaxStages;
   s.s_full = b + 2 * kMaxStages;
   s.s_empty = s.s_full + 2;
   s.u_full = s.s_full + 4;
-  s.u_empty = s.s_full + 5;
-  s.t_done = s.s_full + 6;
-  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 7);
+  s.u_empty = s.s_full + 6;
+  s.t_done = s.s_full + 8;
+  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 9);
   p += 256;
   s.red = reinterpret_cast<double*>(p);
   return s;
@@ -261,6 +273,7 @@ __device__ __forceinline__ void flag_all(lsf_result* res, int k, int bits) {
 // sequence.
 struct Schedule {
   int nt, nchunks, lag;
+  int skew;  // row chunks issued in a phase before its first transposed chunk
   bool rows, cols;
   __device__ int phases() const { return nt + lag; }
   __device__ bool c_on(int ph) const { return cols && ph - lag >= 0 && ph - lag < nt; }
@@ -288,6 +301,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   sch.rows = rows;
   sch.cols = cols;
   sch.lag = (rows && cols) ? 1 : 0;
+  sch.skew = (rows && cols) ? min(3, nchunks) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.nstages; ++s) {
@@ -297,9 +311,9 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm.s_full[b], 1);
       mbar_init(&sm.s_empty[b], 128);
+      mbar_init(&sm.u_full[b], 64);
+      mbar_init(&sm.u_empty[b], 1);
     }
-    mbar_init(sm.u_full, 128);
-    mbar_init(sm.u_empty, 1);
     mbar_init(sm.t_done, 1);
     fence_mbarrier_init();
   }
@@ -336,8 +350,8 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         const int y = static_cast<int>(tile * kTileRows);
         const int x = c * kChunkCols;
         tma_box(dst, &fmap, x, y, 0, &sm.full[s], pol);
-        tma_box(dst + kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s], pol);
-        tma_box(dst + 2 * kBoxBytes, &fmap, x, y, 1, &sm.full[s], pol);
+        tma_box(dst + kBoxBytes, &fmap, x, y, 1, &sm.full[s], pol);
+        tma_box(dst + 2 * kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s], pol);
         tma_box(dst + 3 * kBoxBytes, &fmap, x + kBoxCols, y, 1, &sm.full[s], pol);
         if (with_t) {
           tma_box2d(dst + kStageBytes, &tmap, x, 0, &sm.full[s]);
@@ -366,13 +380,13 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     for (int ph = 0; ph < sch.phases() && !err; ++ph) {
       const int64_t tc = blockIdx.x + static_cast<int64_t>(ph - sch.lag) * gridDim.x;
       const int64_t tr = blockIdx.x + static_cast<int64_t>(ph) * gridDim.x;
-      for (int c = 0; c < nchunks && !err; ++c) {
-        if (sch.r_on(ph)) {
+      for (int i = 0; i < nchunks + sch.skew && !err; ++i) {
+        if (sch.r_on(ph) && i < nchunks) {
           prefetch(rq + a.prefetch);
           ++rq;
-          if (!issue(tr, c, true)) err = LSF_ERR_TIMEOUT;
+          if (!issue(tr, i, true)) err = LSF_ERR_TIMEOUT;
         }
-        if (!err && sch.c_on(ph) && !issue(tc, c, false)) err = LSF_ERR_TIMEOUT;
+        if (!err && sch.c_on(ph) && i >= sch.skew && !issue(tc, i - sch.skew, false)) err = LSF_ERR_TIMEOUT;
       }
     }
     // drain: every issued copy has landed before the CTA may exit
@@ -384,13 +398,17 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer (one thread)
-    constexpr uint32_t kRowHi = idesc_bf16(2 * KP, 0);
-    constexpr uint32_t kRowLo = idesc_bf16(KP, 0);
-    constexpr uint32_t kColHi = idesc_bf16(2 * KP, 1);
-    constexpr uint32_t kColLo = idesc_bf16(KP, 1);
+    // row products: M = 128 = the 64 points of the hi plane stacked on those of
+    // the lo plane; transposed products: M = 128 features
+    constexpr uint32_t kRow = idesc_bf16(2 * kTileRows, 2 * KP, 0);
+    constexpr uint32_t kColHi = idesc_bf16(kChunkCols, 2 * KP, 1);
+    constexpr uint32_t kColLo = idesc_bf16(kChunkCols, KP, 1);
+    // descriptors are built once; an operand at a byte offset o adds o >> 4 to
+    // the start-address field (addresses stay below 256 KB: no carry)
     const uint32_t st_base = smem_u32(sm.stages);
     const uint32_t sU_base = smem_u32(sm.sU);
-    const uint32_t region = 2 * KP * 128;  // bytes of one 64-wide K block of a B operand
+    const uint64_t dK0 = smem_desc(st_base, 16, 1024);         // K-major, 128-byte swizzle
+    const uint64_t dM0 = smem_desc(st_base, 2 * kBoxBytes, 1024);  // MN-major A^T: halves 16 KB apart
     int it = 0;
     auto take = [&](uint32_t& st) -> bool {
       const int s = it % a.nstages;
@@ -416,69 +434,84 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         tc_fence_after();
       }
       const uint32_t dS = tmem_S + (jr & 1) * 2 * KP;
-      for (int c = 0; c < nchunks && !err; ++c) {
+      const uint32_t sU_b = sU_base + (jc & 1) * static_cast<uint32_t>(multi_u_bytes(KP));
+      for (int i = 0; i < nchunks + sch.skew && !err; ++i) {
         uint32_t st;
-        if (ron) {
+        if (ron && i < nchunks) {
+          const int c = i;
           if (!take(st)) { err = LSF_ERR_TIMEOUT; break; }
           if (lane == 0) {
+            const uint64_t ds = dK0 + ((st - st_base) >> 4);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t a_hi = st + h * kBoxBytes + ks * 32;
-                const uint32_t b = st + kStageBytes + h * tbox + ks * 32;
-                const uint64_t bd = smem_desc(b, 16, 1024);
-                mma_bf16(dS, smem_desc(a_hi, 16, 1024), bd, kRowHi, (c | h | ks) != 0);
-                mma_bf16(dS, smem_desc(a_hi + 2 * kBoxBytes, 16, 1024), bd, kRowLo, 1);
+                // A: the hi and lo boxes of half h (128 rows), B: [T_hi; T_lo] of half h
+                const uint64_t ad = ds + ((h * 2 * kBoxBytes + ks * 32) >> 4);
+                const uint64_t bd = ds + ((kStageBytes + h * tbox + ks * 32) >> 4);
+                mma_bf16(dS, ad, bd, kRow, (c | h | ks) != 0);
               }
             }
+            // the tile's row products are complete once these MMAs are
+            if (c == nchunks - 1) mma_commit(&sm.s_full[jr & 1]);
           }
           release();
         }
-        if (con) {
+        if (con && i >= sch.skew) {
+          const int c = i - sch.skew;
           if (c == 0) {
-            // the scalings of tile jc, formed while this phase's first row chunk ran
-            if (!warp_wait(sm.u_full, static_cast<uint32_t>(jc) & 1u, lane)) { err = LSF_ERR_TIMEOUT; break; }
+            // the scalings of tile jc, formed while this phase's first row chunks ran
+            if (!warp_wait(&sm.u_full[jc & 1], static_cast<uint32_t>(jc >> 1) & 1u, lane)) {
+              err = LSF_ERR_TIMEOUT;
+              break;
+            }
             tc_fence_after();
           }
           if (!take(st)) { err = LSF_ERR_TIMEOUT; break; }
           if (lane == 0) {
             const uint32_t dT = tmem_T + c * 2 * KP;
+            const uint64_t dm = dM0 + ((st - st_base) >> 4);
+            const uint64_t du = dK0 + ((sU_b - st_base) >> 4);
 #pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-              // A^T: M = the chunk's 128 features (two 64-feature atoms 16 KB apart),
-              // K = 16 points (two 8-point groups of 1024 B)
-              const uint32_t a_hi = st + ks * 2048;
-              const uint32_t b = sU_base + (ks >> 2) * region + (ks & 3) * 32;
-              const uint64_t bd = smem_desc(b, 16, 1024);
-              mma_bf16(dT, smem_desc(a_hi, kBoxBytes, 1024), bd, kColHi, (jc > 0 || ks > 0) ? 1 : 0);
-              mma_bf16(dT, smem_desc(a_hi + 2 * kBoxBytes, kBoxBytes, 1024), bd, kColLo, 1);
+            for (int ks = 0; ks < kTileRows / 16; ++ks) {
+              // A^T: M = the chunk's 128 features (the two halves' boxes of a plane,
+              // 16 KB apart), K = 16 points (two 8-point groups of 1024 B)
+              const uint64_t bd = du + ((ks * 32) >> 4);
+              mma_bf16(dT, dm + ((ks * 2048) >> 4), bd, kColHi, (jc > 0 || ks > 0) ? 1 : 0);
+              mma_bf16(dT, dm + ((kBoxBytes + ks * 2048) >> 4), bd, kColLo, 1);
             }
+            if (c == nchunks - 1) mma_commit(&sm.u_empty[jc & 1]);
           }
           release();
         }
       }
       if (err) break;
-      if (lane == 0) {
-        if (ron) mma_commit(&sm.s_full[jr & 1]);
-        if (con) mma_commit(sm.u_empty);
-      }
       __syncwarp();
     }
     if (lane == 0) mma_commit(sm.t_done);
     __syncwarp();
   } else {
     // ------------------------------------------------ epilogue warps 2..5
+    // D_S has one TMEM lane per row of the stacked operand: lanes 0-63 hold the hi
+    // plane's row products of the tile's 64 points, lanes 64-127 the lo plane's.
+    // The warps on lanes 64-127 hand their partial sums to the owners of the
+    // points (lanes 0-63) through shared memory. Waits that run out are agreed on
+    // by all four warps at the per-tile named barrier, so they leave together.
     const int quarter = warp & 3;               // TMEM lanes this warp may access
-    const int rloc = quarter * 32 + lane;       // point within the tile
+    const bool owner = quarter < 2;
+    const int rloc = (quarter & 1) * 32 + lane;  // point within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     double resid[KP];
 #pragma unroll
     for (int p = 0; p < KP; ++p) resid[p] = 0.0;
     uint32_t bad = 0u;
-    for (int j = 0; j < sch.nt && !err; ++j) {
+    bool fail = false;
+    // with row products every exit goes through the per-tile named barrier, so the
+    // loop itself must not stop a warp on its own; without them (Axpy) there is no
+    // collective and a failed warp leaves at once
+    for (int j = 0; j < sch.nt && !(fail && !rows); ++j) {
       const int64_t row = (blockIdx.x + static_cast<int64_t>(j) * gridDim.x) * kTileRows + rloc;
-      const bool valid = row < n;
+      const bool valid = owner && row < n && !fail;
       // this tile's weights (and previous scalings) are fetched before the wait
       float w[KP], o[KP];
 #pragma unroll
@@ -489,9 +522,9 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       }
       float u[KP];
       if (rows) {
-        if (!warp_wait(&sm.s_full[j & 1], static_cast<uint32_t>(j >> 1) & 1u, lane)) {
+        if (!fail && !warp_wait(&sm.s_full[j & 1], static_cast<uint32_t>(j >> 1) & 1u, lane)) {
+          fail = true;
           err = LSF_ERR_TIMEOUT;
-          break;
         }
         tc_fence_after();
         float d[2 * KP];
@@ -504,18 +537,34 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         }
         tc_fence_before();
         mbar_arrive(&sm.s_empty[j & 1]);
+        float* xb = sm.xbuf + (j & 1) * (KP * kTileRows);
+        if (!owner) {
+#pragma unroll
+          for (int p = 0; p < KP; ++p) xb[p * kTileRows + rloc] = d[p] + d[KP + p];
+        }
+        // all four warps: the hand-over is visible, and nobody has failed
+        int all_ok;
+        asm volatile(
+            "{\n\t.reg .pred q, r;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+            "bar.red.and.pred r, 1, 128, q;\n\tselp.u32 %0, 1, 0, r;\n\t}"
+            : "=r"(all_ok)
+            : "r"(fail ? 0 : 1)
+            : "memory");
+        if (!all_ok) {
+          err |= LSF_ERR_TIMEOUT;
+          break;
+        }
 #pragma unroll
         for (int p = 0; p < KP; ++p) {
-          const float s = d[p] + d[KP + p];
           u[p] = 0.f;
           if (p < a.k && valid) {
+            const float sp = d[p] + d[KP + p] + xb[p * kTileRows + rloc];
             if (a.mode == kMultiUpdate) {
-              const float v = w[p] / s;
+              const float v = w[p] / sp;
               if (!(v > 0.f && v < INFINITY)) bad |= 1u << p;
-              a.out[p * n + row] = v;
               u[p] = v;
             } else {
-              resid[p] += fabs(static_cast<double>(o[p]) * static_cast<double>(s) - static_cast<double>(w[p]));
+              resid[p] += fabs(static_cast<double>(o[p]) * static_cast<double>(sp) - static_cast<double>(w[p]));
             }
           }
         }
@@ -524,20 +573,29 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         for (int p = 0; p < KP; ++p) u[p] = o[p];
       }
       if (cols) {
-        if (j > 0 && !warp_wait(sm.u_empty, static_cast<uint32_t>(j - 1) & 1u, lane)) {
+        if (owner && !fail && j >= 2 &&
+            !warp_wait(&sm.u_empty[j & 1], static_cast<uint32_t>((j - 2) >> 1) & 1u, lane)) {
+          fail = true;
           err = LSF_ERR_TIMEOUT;
-          break;
         }
-        uint16_t* region = sm.sU + (rloc >> 6) * (2 * KP * 64);
+        uint16_t* sUb = sm.sU + (j & 1) * (2 * KP * kTileRows);
+        if (owner && !fail) {
 #pragma unroll
-        for (int p = 0; p < KP; ++p) {
-          uint16_t hi, lo;
-          split_bf16(u[p], hi, lo);
-          region[sw128(p, rloc & 63)] = hi;
-          region[sw128(KP + p, rloc & 63)] = lo;
+          for (int p = 0; p < KP; ++p) {
+            uint16_t hi, lo;
+            split_bf16(u[p], hi, lo);
+            sUb[sw128(p, rloc)] = hi;
+            sUb[sw128(KP + p, rloc)] = lo;
+          }
+          fence_async_smem();
+          mbar_arrive(&sm.u_full[j & 1]);
         }
-        fence_async_smem();
-        mbar_arrive(sm.u_full);
+      }
+      // the new scalings to global memory, off the MMA issuer's critical path
+      if (a.mode == kMultiUpdate) {
+#pragma unroll
+        for (int p = 0; p < KP; ++p)
+          if (p < a.k && valid) a.out[p * n + row] = u[p];
       }
     }
     // the launch's partial T' (this CTA's points) out of TMEM
@@ -556,7 +614,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 #pragma unroll
             for (int i = 0; i < 32; ++i) d[32 * h + i] = v[i];
           }
-          const int f = c * kChunkCols + rloc;
+          const int f = c * kChunkCols + quarter * 32 + lane;  // M = 128: lane = feature
 #pragma unroll
           for (int p = 0; p < KP; ++p) dst[static_cast<size_t>(p) * a.ldr2 + f] = d[p] + d[KP + p];
         }
