@@ -54,6 +54,9 @@ constexpr int kBoxBytes = kTileRows * kBoxCols * 2;   // 8 KB
 constexpr int kStageBytes = 4 * kBoxBytes;     // two boxes of each plane: 32 KB
 constexpr int kMultiThreads = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kMaxStages = 6;
+// Row chunks of a phase issued before its first transposed chunk: the slack the
+// epilogue has to form the previous tile's scalings (measured best of 1..8).
+constexpr int kSkew = 3;
 
 enum MultiMode : int { kMultiUpdate = 0, kMultiAxpy = 1, kMultiDot = 2 };
 
@@ -252,10 +255,29 @@ __device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, in
   return s;
 }
 
+// Bounded wait that suspends the thread in hardware (try_wait with a suspend-time
+// hint) instead of spinning, so that waiting warps leave the issue slots to the
+// MMA and TMA warps; false if kWaitLimitNs ran out.
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(200000u)
+        : "memory");
+    if (ok) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 // Bounded wait by one lane, result broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int lane) {
   int ok = 1;
-  if (lane == 0) ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
+  if (lane == 0) ok = mbar_wait_suspend(bar, parity) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -301,7 +323,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   sch.rows = rows;
   sch.cols = cols;
   sch.lag = (rows && cols) ? 1 : 0;
-  sch.skew = (rows && cols) ? min(3, nchunks) : 0;
+  sch.skew = (rows && cols) ? min(kSkew, nchunks) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.nstages; ++s) {
@@ -414,8 +436,9 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       const int s = it % a.nstages;
       const uint32_t ph = static_cast<uint32_t>(it / a.nstages) & 1u;
       ++it;
+      // the TMA copy completed on this mbarrier: its bytes are visible to the
+      // tensor core (both async proxy) without a tcgen05 fence
       if (!warp_wait(&sm.full[s], ph, lane)) return false;
-      tc_fence_after();
       st = st_base + s * stage_bytes;
       return true;
     };
