@@ -647,9 +647,11 @@ def run_accel(args):
 def run_multi(args):
     """Many weight vectors on one support (the tensor-core pass): k = 16 pairs of
     Dirichlet(1) weights on the large two-cloud shape (n = m = 2^20 in R^3, eps = 0.1,
-    r = 1024), 200 iterations of Alg. 1 for each pair and Eq. (6). A step = features,
-    their bf16 pair split, the multi-right-hand-side solve. Compared with the same 16
-    pairs solved one after another by the stored-feature single solve."""
+    r = 1024), 200 iterations of Alg. 1 for each of the three terms of Eq. (2) per
+    pair. A step = features, their bf16 pair split, three multi-right-hand-side
+    solves ((X, Y), (X, X), (Y, Y)) and Eq. (6)/(2). Compared with the same 16 pairs'
+    debiased divergences computed one after another by the stored-feature single
+    solve (its lock-step schedule)."""
     import torch
     import paper_2006_07057_gb300 as lsf
     torch.cuda.set_device(0)
@@ -670,7 +672,7 @@ def run_multi(args):
 
     def step():
         prob = lsf.MultiSinkhornProblem(t["X"], t["Y"], tA, tB, t["Z"], p.eps)
-        prob.run(args.iters)
+        prob.run(args.iters, debiased=True)
         holder["prob"] = prob
 
     for _ in range(args.warmup):
@@ -701,8 +703,8 @@ def run_multi(args):
         for q in range(k):
             single.x.w = tA[q].contiguous()
             single.y.w = tB[q].contiguous()
-            single.run(args.iters, debiased=False)
-            out.append(single.values()["W_xy"])
+            single.run(args.iters, debiased=True)
+            out.append(single.values()["W_bar"])
         return out
 
     torch.cuda.synchronize()
@@ -710,22 +712,25 @@ def run_multi(args):
     seq_W = sequential()
     torch.cuda.synchronize()
     ms_seq = (time.perf_counter() - t0) * 1e3
-    worst = max(abs(v["W"] - w) / abs(w) for v, w in zip(vals, seq_W))
-    updates = k * args.iters * (p.n + p.m) * p.r
+    worst = max(abs(v["W_bar"] - w) / (abs(v["W"]) + 0.5 * abs(v["W_xx"]) + 0.5 * abs(v["W_yy"]))
+                for v, w in zip(vals, seq_W))
+    updates = 3 * k * args.iters * (p.n + p.m) * p.r
     line = {
         "metric": METRIC, "value": updates / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2/f32", "data": "synthetic",
         "config": {"workload": f"{k} weight pairs (Dirichlet(1)) on one support: the large two-cloud "
                                f"shape n=m={p.n}, d=3, eps={p.eps}, r={p.r}, {args.iters} iterations "
-                               f"per pair, Eq. (6) per pair; tensor-core multi-right-hand-side passes",
+                               f"per term, debiased divergence (Eq. 2) per pair; tensor-core "
+                               f"multi-right-hand-side passes",
                    "l2": "inputs larger than L2 (two 4 GiB bf16-pair feature matrices per pass)"},
         "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
         "features_ms_per_step": feat_ms / args.steps,
         "sequential_single_solves_ms": ms_seq,
         "speedup_vs_sequential": ms_seq / ms,
-        "max_rel_W_diff_vs_single": worst,
-        "result": {"W": [v["W"] for v in vals[:4]], "residual": [v["residual"] for v in vals[:4]]},
+        "max_rel_W_bar_diff_vs_single": worst,
+        "result": {"W_bar": [v["W_bar"] for v in vals[:4]], "W": [v["W"] for v in vals[:4]],
+                   "residual": [v["residual"] for v in vals[:4]]},
     }
     print(json.dumps(line))
     return 0

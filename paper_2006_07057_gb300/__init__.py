@@ -869,10 +869,13 @@ class MultiSinkhornProblem:
     """k pairs of weights (rows of A: k x n, B: k x m) on the same two clouds.
 
     One theta, one set of features (split into the bf16 pair planes of the
-    tensor-core pass), and one multi-right-hand-side solve per ``run``: every
-    half iteration of Alg. 1 for all k pairs is two n x r x k contractions on
-    the tensor cores. ``values`` returns, per pair, Eq. (6), the residual and
-    the status, as a single solve of that pair reports them.
+    tensor-core pass), and one multi-right-hand-side solve per term: every half
+    iteration of Alg. 1 for all k pairs is two n x r x k contractions on the
+    tensor cores. ``run(iters, debiased=True)`` also solves the self terms
+    W(a_p, a_p) on (X, X) and W(b_p, b_p) on (Y, Y) with the same theta and
+    combines Eq. (2) per pair. ``values`` returns, per pair, Eq. (6) (and
+    Eq. (2)), the residual and the status, as a single solve of that pair
+    reports them.
     """
 
     def __init__(self, X, Y, A, B, Z, eps: float, stream=None):
@@ -899,24 +902,58 @@ class MultiSinkhornProblem:
         self.F2y = lsf_split_features(Fy, r, self.ldr2, stream=stream)
         del Fx, Fy
         self.A, self.B = A, B
+        self.n, self.m = n, m
+        self.debiased = False
         kp = multi_kp(self.k)
-        self.U = torch.zeros((self.k, n), dtype=torch.float32, device=dev)
-        self.V = torch.zeros((self.k, m), dtype=torch.float32, device=dev)
-        self.Tu = torch.zeros((kp, self.ldr2), dtype=torch.float32, device=dev)
-        self.Tv = torch.zeros((kp, self.ldr2), dtype=torch.float32, device=dev)
+
+        def scal(a, b):
+            z = lambda *s_: torch.zeros(s_, dtype=torch.float32, device=dev)  # noqa: E731
+            return {"U": z(self.k, a), "V": z(self.k, b), "Tu": z(kp, self.ldr2), "Tv": z(kp, self.ldr2)}
+
+        self._scal = scal
+        self.s = {"xy": scal(n, m)}
+        self.U, self.V = self.s["xy"]["U"], self.s["xy"]["V"]
+        self.Tu, self.Tv = self.s["xy"]["Tu"], self.s["xy"]["Tv"]
         self.results = alloc_results(self.k, dev)
+        self.res = {"xy": self.results}
         nbytes = lsf_multi_workspace_bytes(self.ldr2, self.k)
         ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
         off = (-ws.data_ptr()) % 256
         self.workspace = ws[off:off + nbytes]
 
-    def run(self, iters: int) -> None:
-        """Launch the k solves and their Eq. (6) reductions on the stream (asynchronous)."""
-        lsf_solve_multi(self.theta, self.ldr2, self.F2x, self.shift_x, self.A, self.F2y,
-                        self.shift_y, self.B, iters, self.U, self.V, self.Tu, self.Tv,
-                        self.results, self.workspace, self.stream)
+    def _term(self, which: str):
+        x = (self.F2x, self.shift_x, self.A) if which in ("xy", "xx") else (self.F2y, self.shift_y, self.B)
+        y = (self.F2y, self.shift_y, self.B) if which in ("xy", "yy") else (self.F2x, self.shift_x, self.A)
+        return x, y
+
+    def run(self, iters: int, debiased: bool = False) -> None:
+        """Launch the k solves of each term and their Eq. (6) reductions on the
+        stream (asynchronous)."""
+        self.debiased = bool(debiased)
+        terms = ("xy", "xx", "yy") if self.debiased else ("xy",)
+        dev = self.A.device
+        for t in terms:
+            if t not in self.s:
+                x, y = self._term(t)
+                self.s[t] = self._scal(x[2].shape[1], y[2].shape[1])
+                self.res[t] = alloc_results(self.k, dev)
+            x, y = self._term(t)
+            s = self.s[t]
+            lsf_solve_multi(self.theta, self.ldr2, x[0], x[1], x[2], y[0], y[1], y[2], iters,
+                            s["U"], s["V"], s["Tu"], s["Tv"], self.res[t], self.workspace,
+                            self.stream)
 
     def values(self) -> list[dict]:
-        """Per pair: W (Eq. (6)), residual, status, iters (synchronises)."""
-        return [{"W": r["W"], "residual": r["residual"], "status": r["status"], "iters": r["iters"],
-                 "log_scale": r["log_scale"]} for r in read_results(self.results)]
+        """Per pair: W (Eq. (6)), residual, status, iters, and with ``debiased``
+        W_xx, W_yy and W_bar (Eq. (2)) (synchronises)."""
+        xy = read_results(self.res["xy"])
+        out = [{"W": r["W"], "residual": r["residual"], "status": r["status"], "iters": r["iters"],
+                "log_scale": r["log_scale"]} for r in xy]
+        if self.debiased:
+            xx = read_results(self.res["xx"])
+            yy = read_results(self.res["yy"])
+            for o_, a_, b_ in zip(out, xx, yy):
+                o_.update(W_xx=a_["W"], W_yy=b_["W"], res_xx=a_["residual"], res_yy=b_["residual"],
+                          W_bar=o_["W"] - 0.5 * (a_["W"] + b_["W"]),
+                          status=o_["status"] | a_["status"] | b_["status"])
+        return out

@@ -5,7 +5,7 @@ oracle on its own (Alg. 1 in the log domain from v = 1, Eq. (6)); the GPU solves
 all k at once with the multi-right-hand-side pass. Tolerances: |W_gpu - W_orc|
 <= 1e-4 |W_orc| and |res_gpu - res_orc| <= 1e-5, per pair.
 
-The cases span ragged n and m (partial tiles of 128 points), r below and at a
+The cases span ragged n and m (partial tiles of 64 points), r below and at a
 multiple of 128 (zero feature padding), one to 20 right-hand sides (16 and 32
 computed), and the single-point problem, whose divergence has the closed form
 -eps log k_theta(x, y) (Eq. (7)) after any number of iterations.
@@ -79,6 +79,39 @@ def test_multi_matches_oracle(lsf, seed, n, m, d, r, eps, iters, k):
         assert abs(g["residual"] - e["res"]) <= 1e-5, (q, g["residual"], e["res"])
 
 
+@pytest.mark.parametrize("seed,n,m,d,r,eps,iters,k", [
+    (41, 900, 700, 2, 100, 0.3, 25, 6),
+    (42, 1300, 1300, 3, 256, 0.5, 15, 17),
+])
+def test_multi_debiased_matches_oracle(lsf, seed, n, m, d, r, eps, iters, k):
+    # Eq. (2) per pair: the self terms run on (X, X) with a_p and (Y, Y) with b_p,
+    # all with the one theta of (X, Y)
+    p, A, B = _problem(seed, n, m, d, r, eps, k)
+    th = o.make_theta(p.X, p.Y, p.Z, p.eps)
+    Lx = o.log_features(p.X, th.U, p.eps, th.q)
+    Ly = o.log_features(p.Y, th.U, p.eps, th.q)
+    dev = torch.device("cuda", 0)
+    t = {q: torch.from_numpy(np.ascontiguousarray(getattr(p, q))).to(dev) for q in "XYZ"}
+    prob = lsf.MultiSinkhornProblem(t["X"], t["Y"], torch.from_numpy(A).to(dev),
+                                    torch.from_numpy(B).to(dev), t["Z"], p.eps)
+    prob.run(iters, debiased=True)
+    got = prob.values()
+    for q in range(k):
+        a, b = A[q], B[q]
+        sxy = o.solve(Lx, Ly, a, b, iters)
+        sxx = o.solve(Lx, Lx, a, a, iters)
+        syy = o.solve(Ly, Ly, b, b, iters)
+        Wxy = o.dual_estimate(a, b, sxy["logu"], sxy["logv"], p.eps)
+        Wxx = o.dual_estimate(a, a, sxx["logu"], sxx["logv"], p.eps)
+        Wyy = o.dual_estimate(b, b, syy["logu"], syy["logv"], p.eps)
+        scale = abs(Wxy) + 0.5 * abs(Wxx) + 0.5 * abs(Wyy)
+        g = got[q]
+        assert g["status"] == 0
+        assert abs(g["W_bar"] - (Wxy - 0.5 * (Wxx + Wyy))) <= 1e-4 * scale, (q, g["W_bar"])
+        assert abs(g["W_xx"] - Wxx) <= 1e-4 * abs(Wxx) and abs(g["W_yy"] - Wyy) <= 1e-4 * abs(Wyy)
+        assert abs(g["res_xx"] - sxx["residual"]) <= 1e-5 and abs(g["res_yy"] - syy["residual"]) <= 1e-5
+
+
 def test_multi_single_point_closed_form(lsf):
     # n = m = 1: P = a b^T after the first half steps and W = -eps log k_theta(x, y)
     p, A, B = _problem(36, 1, 1, 3, 50, 0.7, 3)
@@ -137,7 +170,7 @@ def test_multi_rejects_unsupported_shapes(lsf):
         lsf.lsf_multi_workspace_bytes(100, 4)
     assert e.value.status == lsf.LSF_ERR_UNSUPPORTED
     with pytest.raises(lsf.LsfError) as e:
-        lsf.lsf_multi_workspace_bytes(1024, 20)   # 32 accumulators x 9 blocks > 512 TMEM columns
+        lsf.lsf_multi_workspace_bytes(1024, 20)   # 2 x 32 x (2 + 8) = 640 > 512 TMEM columns
     assert e.value.status == lsf.LSF_ERR_UNSUPPORTED
     p, A, B = _problem(38, 300, 200, 2, 64, 0.5, 3)
     prob, _ = _run(lsf, p, A, B, 2)
