@@ -537,15 +537,19 @@ int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
 
 /*
  * Tuning of lsf_solve_multi (process-wide, not thread-safe against concurrent
- * solves). The pass reads each 128 x 128 feature chunk twice: from HBM for the
- * row products and again, a tile later, for the transposed products, which
- * must find it in L2. chunks: how many row chunks ahead of its shared-memory
- * ring the pass requests into L2 (0 to 16; default 0). l2_hints: the L2
- * eviction priority of the chunk reads: 0 default for both, 1 (default) evict
- * first on the second read (the chunk's last use), 2 additionally evict last
- * on the first read. Errors: LSF_ERR_ARG outside those ranges.
+ * solves). The pass reads each 64-point x 128-feature chunk twice: from HBM for
+ * the row products and again, a tile later, for the transposed products, which
+ * must find it in L2. prefetch_chunks: how many row chunks ahead of its
+ * shared-memory ring the pass requests into L2 (0 to 16; default 0).
+ * l2_hints: the L2 eviction priority of the chunk reads: 0 default for both, 1
+ * (default) evict first on the second read (the chunk's last use), 2
+ * additionally evict last on the first read. r_vectors_resident: 1 keeps the
+ * split r-vectors of the row products in shared memory for the whole launch
+ * when that leaves room for at least four ring stages, 0 (default) loads their
+ * 128-feature block with every row chunk (one more ring stage; faster at
+ * r = 1024). Errors: LSF_ERR_ARG outside those ranges.
  */
-int lsf_set_multi_prefetch(int chunks, int l2_hints);
+int lsf_set_multi_tuning(int prefetch_chunks, int l2_hints, int r_vectors_resident);
 
 /* Kernel classes timed by the optional event recorder. */
 typedef enum {

@@ -336,10 +336,13 @@ def lsf_split_features(F: torch.Tensor, r: int, ldr2: int | None = None, F2=None
     return F2
 
 
-def lsf_set_multi_prefetch(chunks: int, l2_hints: int = 1) -> None:
-    """Feature chunks the multi-right-hand-side pass requests into L2 ahead of its
-    ring, and the L2 eviction hints of its two reads of each chunk (0, 1, 2)."""
-    check(lib().lsf_set_multi_prefetch(int(chunks), int(l2_hints)), "lsf_set_multi_prefetch")
+def lsf_set_multi_tuning(prefetch_chunks: int = 0, l2_hints: int = 1,
+                         r_vectors_resident: int = 0) -> None:
+    """Tuning of the multi-right-hand-side pass: row chunks requested into L2 ahead
+    of its ring, the L2 eviction hints of its two reads of each chunk (0, 1, 2),
+    and whether the split r-vectors stay in shared memory for the launch."""
+    check(lib().lsf_set_multi_tuning(int(prefetch_chunks), int(l2_hints), int(r_vectors_resident)),
+          "lsf_set_multi_tuning")
 
 
 def lsf_multi_workspace_bytes(ldr2: int, k: int) -> int:

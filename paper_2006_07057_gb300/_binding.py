@@ -120,7 +120,7 @@ _SIGNATURES = {
                                       c_size_t, c_void_p]),
     "lsf_split_features": (c_int, [c_void_p, c_int64, c_int, c_int, c_void_p, c_int, c_void_p]),
     "lsf_multi_workspace_bytes": (c_int, [c_int, c_int, _P(c_size_t)]),
-    "lsf_set_multi_prefetch": (c_int, [c_int, c_int]),
+    "lsf_set_multi_tuning": (c_int, [c_int, c_int, c_int]),
     "lsf_solve_multi": (c_int, [_P(LsfTheta), c_int, _P(LsfMultiCloud), _P(LsfMultiCloud), c_int,
                                 c_int, _P(LsfMultiScalings), c_void_p, c_void_p, c_size_t,
                                 c_void_p]),

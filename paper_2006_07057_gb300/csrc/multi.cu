@@ -69,6 +69,7 @@ struct MultiArgs {
   int nstages;
   int prefetch;        // row chunks requested into L2 ahead of the ring
   int l2_hints;        // 0 none, 1 evict-first on the re-read, 2 also evict-last on the first read
+  int t_resident;      // the split r-vectors stay in shared memory for the launch (else a box per row chunk)
   uint32_t tmem_cols;
   const float* w;      // k x n weights (Update, Dot)
   const float* old;    // k x n previous scalings (Dot) or the given scalings (Axpy)
@@ -206,6 +207,7 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
 // wrote).
 struct MultiSmem {
   unsigned char* stages;  // [S][32 KB features | 2 x (2 kp x 128 B) r-vector boxes]
+  uint16_t* sT;           // [ldr2 / 64][2 kp][64]: resident split r-vectors (t_resident)
   uint16_t* sU;           // [2][2 kp][64]: the split scalings of a tile, double-buffered
   float* xbuf;            // [2][64][kp]: lo-plane row products handed between epilogue warps
   uint64_t* full;         // [S]
@@ -215,28 +217,38 @@ struct MultiSmem {
   uint64_t* u_full;       // [2] sU[b] written
   uint64_t* u_empty;      // [2] sU[b] read by the transposed products
   uint64_t* t_done;       // every MMA of the launch completed
+  uint64_t* t_full;       // resident r-vectors loaded
   uint32_t* tmem_slot;
   double* red;            // [4][kp]
 };
 
 __host__ __device__ inline int multi_tbox_bytes(int kp) { return 2 * kp * 128; }
-__host__ __device__ inline int multi_stage_bytes(int kp) { return kStageBytes + 2 * multi_tbox_bytes(kp); }
+__host__ __device__ inline int multi_stage_bytes(int kp, bool tres) {
+  return kStageBytes + (tres ? 0 : 2 * multi_tbox_bytes(kp));
+}
+__host__ __device__ inline size_t multi_t_bytes(int kp, int ldr2, bool tres) {
+  return tres ? static_cast<size_t>(ldr2 / kBoxCols) * multi_tbox_bytes(kp) : 0;
+}
 
 __host__ __device__ inline size_t multi_u_bytes(int kp) { return static_cast<size_t>(2 * kp) * kTileRows * 2; }
 
 __host__ __device__ inline size_t multi_x_bytes(int kp) { return static_cast<size_t>(kTileRows) * kp * 4; }
 
-__host__ __device__ inline size_t multi_smem_bytes(int kp, int stages) {
-  return 1024 + static_cast<size_t>(stages) * multi_stage_bytes(kp) + 2 * multi_u_bytes(kp) +
+__host__ __device__ inline size_t multi_smem_bytes(int kp, int stages, int ldr2, bool tres) {
+  return 1024 + static_cast<size_t>(stages) * multi_stage_bytes(kp, tres) +
+         multi_t_bytes(kp, ldr2, tres) + 2 * multi_u_bytes(kp) +
          2 * multi_x_bytes(kp) + 256 + static_cast<size_t>(4) * kp * 8;
 }
 
-__device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int stages) {
+__device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, int stages, int ldr2,
+                                                  bool tres) {
   MultiSmem s;
   unsigned char* p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
                                                       ~static_cast<uintptr_t>(1023));
   s.stages = p;
-  p += static_cast<size_t>(stages) * multi_stage_bytes(kp);
+  p += static_cast<size_t>(stages) * multi_stage_bytes(kp, tres);
+  s.sT = reinterpret_cast<uint16_t*>(p);
+  p += multi_t_bytes(kp, ldr2, tres);
   s.sU = reinterpret_cast<uint16_t*>(p);
   p += 2 * multi_u_bytes(kp);
   s.xbuf = reinterpret_cast<float*>(p);
@@ -249,7 +261,8 @@ __device__ __forceinline__ MultiSmem multi_layout(unsigned char* raw, int kp, in
   s.u_full = s.s_full + 4;
   s.u_empty = s.s_full + 6;
   s.t_done = s.s_full + 8;
-  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 9);
+  s.t_full = s.s_full + 9;
+  s.tmem_slot = reinterpret_cast<uint32_t*>(s.s_full + 10);
   p += 256;
   s.red = reinterpret_cast<double*>(p);
   return s;
@@ -311,11 +324,12 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   const bool rows = a.mode != kMultiAxpy;
   const bool cols = a.mode != kMultiDot;
-  const MultiSmem sm = multi_layout(smem_raw, KP, a.nstages);
+  const bool tres = a.t_resident && rows;
+  const MultiSmem sm = multi_layout(smem_raw, KP, a.nstages, a.ldr2, tres);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = a.ldr2 / kChunkCols;
   const int64_t n = a.n;
-  const int stage_bytes = multi_stage_bytes(KP);
+  const int stage_bytes = multi_stage_bytes(KP, tres);
   const int tbox = multi_tbox_bytes(KP);
   Schedule sch;
   sch.nt = static_cast<int>((a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
@@ -337,6 +351,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       mbar_init(&sm.u_empty[b], 1);
     }
     mbar_init(sm.t_done, 1);
+    mbar_init(sm.t_full, 1);
     fence_mbarrier_init();
   }
   if (warp == 1) {
@@ -397,6 +412,14 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       tma_prefetch(&fmap, x, y, 1);
       tma_prefetch(&fmap, x + kBoxCols, y, 1);
     };
+    if (tres && lane == 0) {
+      // the launch's r-vectors, once: one box per 64 features
+      const int nb = a.ldr2 / kBoxCols;
+      mbar_arrive_expect_tx(sm.t_full, static_cast<uint32_t>(nb * tbox));
+      for (int b = 0; b < nb; ++b)
+        tma_box2d(reinterpret_cast<unsigned char*>(sm.sT) + b * tbox, &tmap, b * kBoxCols, 0, sm.t_full);
+    }
+    __syncwarp();
     for (int q = 0; q < a.prefetch; ++q) prefetch(q);
     int rq = 0;
     for (int ph = 0; ph < sch.phases() && !err; ++ph) {
@@ -406,12 +429,13 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         if (sch.r_on(ph) && i < nchunks) {
           prefetch(rq + a.prefetch);
           ++rq;
-          if (!issue(tr, i, true)) err = LSF_ERR_TIMEOUT;
+          if (!issue(tr, i, !tres)) err = LSF_ERR_TIMEOUT;
         }
         if (!err && sch.c_on(ph) && i >= sch.skew && !issue(tc, i - sch.skew, false)) err = LSF_ERR_TIMEOUT;
       }
     }
     // drain: every issued copy has landed before the CTA may exit
+    if (tres && !warp_wait(sm.t_full, 0u, lane)) err = LSF_ERR_TIMEOUT;
     const int used = min(it, a.nstages);
     for (int j = 0; j < used; ++j) {
       const int itj = it - 1 - j;
@@ -431,6 +455,8 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     const uint32_t sU_base = smem_u32(sm.sU);
     const uint64_t dK0 = smem_desc(st_base, 16, 1024);         // K-major, 128-byte swizzle
     const uint64_t dM0 = smem_desc(st_base, 2 * kBoxBytes, 1024);  // MN-major A^T: halves 16 KB apart
+    const uint32_t sT_off = smem_u32(sm.sT) - st_base;
+    if (tres && !warp_wait(sm.t_full, 0u, lane)) err = LSF_ERR_TIMEOUT;
     int it = 0;
     auto take = [&](uint32_t& st) -> bool {
       const int s = it % a.nstages;
@@ -471,7 +497,8 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
               for (int ks = 0; ks < 4; ++ks) {
                 // A: the hi and lo boxes of half h (128 rows), B: [T_hi; T_lo] of half h
                 const uint64_t ad = ds + ((h * 2 * kBoxBytes + ks * 32) >> 4);
-                const uint64_t bd = ds + ((kStageBytes + h * tbox + ks * 32) >> 4);
+                const uint64_t bd = tres ? dK0 + ((sT_off + (2 * c + h) * tbox + ks * 32) >> 4)
+                                         : ds + ((kStageBytes + h * tbox + ks * 32) >> 4);
                 mma_bf16(dS, ad, bd, kRow, (c | h | ks) != 0);
               }
             }
@@ -809,8 +836,9 @@ int make_t_map(const uint16_t* t_pair, int kp, int ldr2, CUtensorMap* map) {
 
 int multi_kp(int k) { return k <= 16 ? 16 : 32; }
 
-int g_multi_prefetch = 0;  // row chunks prefetched into L2 (lsf_set_multi_prefetch)
-int g_multi_l2_hints = 1;  // L2 eviction hints of the chunk reads (lsf_set_multi_prefetch)
+int g_multi_prefetch = 0;  // row chunks prefetched into L2 (lsf_set_multi_tuning)
+int g_multi_l2_hints = 1;  // L2 eviction hints of the chunk reads (lsf_set_multi_tuning)
+int g_multi_t_resident = 0;  // split r-vectors resident in shared memory (lsf_set_multi_tuning)
 
 // TMEM columns: D_S double-buffered (2 x 2 kp) and one 2 kp block per feature chunk.
 int tmem_need(int kp, int ldr2) { return 2 * kp * (2 + ldr2 / kChunkCols); }
@@ -830,7 +858,7 @@ int check_multi_shape(int ldr2, int k) {
   const int kp = multi_kp(k);
   if (tmem_need(kp, ldr2) > 512)
     return fail(LSF_ERR_UNSUPPORTED, "multi solve: %d right-hand sides at ldr2 = %d exceed TMEM", k, ldr2);
-  if (multi_smem_bytes(kp, 2) > static_cast<size_t>(device_info().smem_optin))
+  if (multi_smem_bytes(kp, 2, ldr2, false) > static_cast<size_t>(device_info().smem_optin))
     return fail(LSF_ERR_UNSUPPORTED, "multi solve: shared memory too small");
   return LSF_OK;
 }
@@ -857,9 +885,13 @@ int launch_multi_kp(const MultiArgs& a0, const CUtensorMap& fmap, const CUtensor
                     cudaStream_t st, int* grid_out) {
   MultiArgs a = a0;
   const size_t optin = static_cast<size_t>(device_info().smem_optin);
+  // resident r-vectors when they leave room for at least 4 ring stages
+  const bool tres = g_multi_t_resident && a.mode != kMultiAxpy &&
+                    multi_smem_bytes(KP, 4, a.ldr2, true) <= optin;
   int stages = kMaxStages;
-  while (stages > 2 && multi_smem_bytes(KP, stages) > optin) --stages;
-  const size_t smem = multi_smem_bytes(KP, stages);
+  while (stages > 2 && multi_smem_bytes(KP, stages, a.ldr2, tres) > optin) --stages;
+  const size_t smem = multi_smem_bytes(KP, stages, a.ldr2, tres);
+  a.t_resident = tres ? 1 : 0;
   if (smem > optin) return fail(LSF_ERR_UNSUPPORTED, "multi pass: %zu bytes of shared memory", smem);
   a.nstages = stages;
   a.prefetch = g_multi_prefetch;
@@ -937,11 +969,15 @@ int lsf_split_features(const float* F, int64_t n, int ldr, int r, uint16_t* F2, 
   return check_launch("split_features_kernel");
 }
 
-int lsf_set_multi_prefetch(int chunks, int l2_hints) {
-  if (chunks < 0 || chunks > 16) return fail(LSF_ERR_ARG, "lsf_set_multi_prefetch: chunks must be in [0, 16]");
-  if (l2_hints < 0 || l2_hints > 2) return fail(LSF_ERR_ARG, "lsf_set_multi_prefetch: l2_hints must be 0, 1 or 2");
-  g_multi_prefetch = chunks;
+int lsf_set_multi_tuning(int prefetch_chunks, int l2_hints, int r_vectors_resident) {
+  if (prefetch_chunks < 0 || prefetch_chunks > 16)
+    return fail(LSF_ERR_ARG, "lsf_set_multi_tuning: prefetch_chunks must be in [0, 16]");
+  if (l2_hints < 0 || l2_hints > 2) return fail(LSF_ERR_ARG, "lsf_set_multi_tuning: l2_hints must be 0, 1 or 2");
+  if (r_vectors_resident < 0 || r_vectors_resident > 1)
+    return fail(LSF_ERR_ARG, "lsf_set_multi_tuning: r_vectors_resident must be 0 or 1");
+  g_multi_prefetch = prefetch_chunks;
   g_multi_l2_hints = l2_hints;
+  g_multi_t_resident = r_vectors_resident;
   return LSF_OK;
 }
 
