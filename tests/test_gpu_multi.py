@@ -112,6 +112,21 @@ def test_multi_debiased_matches_oracle(lsf, seed, n, m, d, r, eps, iters, k):
         assert abs(g["res_xx"] - sxx["residual"]) <= 1e-5 and abs(g["res_yy"] - syy["residual"]) <= 1e-5
 
 
+def test_multi_resident_r_vectors_match_oracle(lsf):
+    # the layout that keeps the split r-vectors in shared memory for the launch
+    p, A, B = _problem(43, 1100, 900, 3, 256, 0.3, 9)
+    ref = _oracle(p, A, B, 20)
+    try:
+        lsf.lsf_set_multi_tuning(0, 1, 1)
+        _, got = _run(lsf, p, A, B, 20)
+    finally:
+        lsf.lsf_set_multi_tuning()
+    for q in range(9):
+        assert got[q]["status"] == 0
+        assert abs(got[q]["W"] - ref[q]["W"]) <= 1e-4 * abs(ref[q]["W"])
+        assert abs(got[q]["residual"] - ref[q]["res"]) <= 1e-5
+
+
 def test_multi_single_point_closed_form(lsf):
     # n = m = 1: P = a b^T after the first half steps and W = -eps log k_theta(x, y)
     p, A, B = _problem(36, 1, 1, 3, 50, 0.7, 3)
