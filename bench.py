@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--batch-strategy", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--pairs", type=int, default=16, help="weight pairs of --workload multi (1..32)")
     return ap.parse_args()
 
 
@@ -657,7 +658,7 @@ def run_multi(args):
     torch.cuda.set_device(0)
     lsf.lib()
     n = args.n
-    k = 16
+    k = args.pairs
     p = synth.large_problem(seed=0, n=n, iters=args.iters)
     rng = np.random.default_rng(7)
     A = rng.exponential(size=(k, n))
@@ -689,7 +690,7 @@ def run_multi(args):
     launches = lsf.lsf_launch_count()
     peak, peak_kind = load_peaks()
     roof = _profile_roofline(lsf, lsf.LSF_KERNEL_PASS_MULTI,
-                             "multi_pass_kernel (tcgen05 bf16-pair passes, 16 right-hand sides)",
+                             f"multi_pass_kernel (tcgen05 bf16-pair passes, {k} right-hand sides)",
                              peak, peak_kind, ms * args.steps)
     feat_ms, _, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
     lsf.lsf_profile_enable(False)

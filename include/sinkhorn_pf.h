@@ -524,9 +524,9 @@ int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes);
  * half iteration becomes two n x r x k contractions, which run on the tensor
  * cores (tcgen05, bf16 pair features and bf16 pair splits of the scalings and
  * r-vectors, FP32 accumulation): one read of the features serves all k solves.
- * k in [1, 32]; ldr2 a multiple of 128 with r <= ldr2 <= 1024, and the
- * accumulators 2 kp (2 + ldr2/128) <= 512 TMEM columns (k <= 16: any ldr2; k <= 32:
- * ldr2 <= 768). theta supplies r and eps (its ldr is not used). Iterates start
+ * k in [1, 32]; ldr2 a multiple of 128 with r <= ldr2 <= 1024 (the accumulators,
+ * 4 kp + 2 kp ldr2/128 columns for k <= 16 and 4 kp + kp ldr2/128 for k <= 32,
+ * fit TMEM's 512 columns at every ldr2). theta supplies r and eps (its ldr is not used). Iterates start
  * from v = 1 as in lsf_solve. Errors: LSF_ERR_ARG, LSF_ERR_UNSUPPORTED (shapes
  * above), LSF_ERR_WORKSPACE (below lsf_multi_workspace_bytes), LSF_ERR_CUDA;
  * device status bits per solve in results[p].status.

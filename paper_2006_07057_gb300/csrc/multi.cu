@@ -54,6 +54,12 @@ constexpr int kBoxBytes = kTileRows * kBoxCols * 2;   // 8 KB
 constexpr int kStageBytes = 4 * kBoxBytes;     // two boxes of each plane: 32 KB
 constexpr int kMultiThreads = 192;             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kMaxStages = 6;
+// Columns of the transposed-product accumulator of one feature chunk: with 16
+// right-hand sides the hi and lo parts of the scalings are separate columns (two
+// MMAs per K step, N = 2 kp and kp); with 32 they share kp columns (three MMAs of
+// N = kp: F_hi U_hi, F_hi U_lo, F_lo U_hi), so that r = 1024 fits in TMEM.
+__host__ __device__ constexpr int dt_cols(int kp) { return kp == 32 ? kp : 2 * kp; }
+
 // Row chunks of a phase issued before its first transposed chunk: the slack the
 // epilogue has to form the previous tile's scalings (measured best of 1..8).
 constexpr int kSkew = 3;
@@ -366,7 +372,8 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *sm.tmem_slot;
   const uint32_t tmem_S = tmem;             // D_S[b] at b * 2 kp
-  const uint32_t tmem_T = tmem + 4 * KP;    // D_T[c] at c * 2 kp
+  const uint32_t tmem_T = tmem + 4 * KP;    // D_T[c] at c * dt_cols(kp)
+  constexpr int kDT = dt_cols(KP);
   int err = 0;
 
   if (warp == 0) {
@@ -449,6 +456,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     constexpr uint32_t kRow = idesc_bf16(2 * kTileRows, 2 * KP, 0);
     constexpr uint32_t kColHi = idesc_bf16(kChunkCols, 2 * KP, 1);
     constexpr uint32_t kColLo = idesc_bf16(kChunkCols, KP, 1);
+    constexpr bool kSplit3 = kDT == KP;
     // descriptors are built once; an operand at a byte offset o adds o >> 4 to
     // the start-address field (addresses stay below 256 KB: no carry)
     const uint32_t st_base = smem_u32(sm.stages);
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
           }
           if (!take(st)) { err = LSF_ERR_TIMEOUT; break; }
           if (lane == 0) {
-            const uint32_t dT = tmem_T + c * 2 * KP;
+            const uint32_t dT = tmem_T + c * kDT;
             const uint64_t dm = dM0 + ((st - st_base) >> 4);
             const uint64_t du = dK0 + ((sU_b - st_base) >> 4);
 #pragma unroll
@@ -527,8 +535,16 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
               // A^T: M = the chunk's 128 features (the two halves' boxes of a plane,
               // 16 KB apart), K = 16 points (two 8-point groups of 1024 B)
               const uint64_t bd = du + ((ks * 32) >> 4);
-              mma_bf16(dT, dm + ((ks * 2048) >> 4), bd, kColHi, (jc > 0 || ks > 0) ? 1 : 0);
-              mma_bf16(dT, dm + ((kBoxBytes + ks * 2048) >> 4), bd, kColLo, 1);
+              if (kSplit3) {
+                // U_lo: rows kp .. 2kp - 1 of the B operand, kp x 128 B further
+                const uint64_t bd_lo = bd + ((KP * 128) >> 4);
+                mma_bf16(dT, dm + ((ks * 2048) >> 4), bd, kColLo, (jc > 0 || ks > 0) ? 1 : 0);
+                mma_bf16(dT, dm + ((ks * 2048) >> 4), bd_lo, kColLo, 1);
+                mma_bf16(dT, dm + ((kBoxBytes + ks * 2048) >> 4), bd, kColLo, 1);
+              } else {
+                mma_bf16(dT, dm + ((ks * 2048) >> 4), bd, kColHi, (jc > 0 || ks > 0) ? 1 : 0);
+                mma_bf16(dT, dm + ((kBoxBytes + ks * 2048) >> 4), bd, kColLo, 1);
+              }
             }
             if (c == nchunks - 1) mma_commit(&sm.u_empty[jc & 1]);
           }
@@ -656,17 +672,18 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         tc_fence_after();
         float* dst = a.part + static_cast<size_t>(blockIdx.x) * KP * a.ldr2;
         for (int c = 0; c < nchunks; ++c) {
-          float d[2 * KP];
+          float d[kDT];
 #pragma unroll
-          for (int h = 0; h < 2 * KP / 32; ++h) {
+          for (int h = 0; h < kDT / 32; ++h) {
             float v[32];
-            tmem_ld32(tmem_T + c * 2 * KP + lane_base + 32 * h, v);
+            tmem_ld32(tmem_T + c * kDT + lane_base + 32 * h, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) d[32 * h + i] = v[i];
           }
           const int f = c * kChunkCols + quarter * 32 + lane;  // M = 128: lane = feature
 #pragma unroll
-          for (int p = 0; p < KP; ++p) dst[static_cast<size_t>(p) * a.ldr2 + f] = d[p] + d[KP + p];
+          for (int p = 0; p < KP; ++p)
+            dst[static_cast<size_t>(p) * a.ldr2 + f] = kDT == KP ? d[p] : d[p] + d[(KP + p) % kDT];
         }
       }
     }
@@ -841,7 +858,7 @@ int g_multi_l2_hints = 1;  // L2 eviction hints of the chunk reads (lsf_set_mult
 int g_multi_t_resident = 0;  // split r-vectors resident in shared memory (lsf_set_multi_tuning)
 
 // TMEM columns: D_S double-buffered (2 x 2 kp) and one 2 kp block per feature chunk.
-int tmem_need(int kp, int ldr2) { return 2 * kp * (2 + ldr2 / kChunkCols); }
+int tmem_need(int kp, int ldr2) { return 4 * kp + dt_cols(kp) * (ldr2 / kChunkCols); }
 
 uint32_t tmem_columns(int kp, int ldr2) {
   uint32_t c = 32;
