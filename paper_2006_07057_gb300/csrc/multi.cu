@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm.s_full[b], 1);
       mbar_init(&sm.s_empty[b], 128);
-      mbar_init(&sm.u_full[b], 64);
+      mbar_init(&sm.u_full[b], 128);
       mbar_init(&sm.u_empty[b], 1);
     }
     mbar_init(sm.t_done, 1);
@@ -560,13 +560,17 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     // ------------------------------------------------ epilogue warps 2..5
     // D_S has one TMEM lane per row of the stacked operand: lanes 0-63 hold the hi
     // plane's row products of the tile's 64 points, lanes 64-127 the lo plane's.
-    // The warps on lanes 64-127 hand their partial sums to the owners of the
-    // points (lanes 0-63) through shared memory. Waits that run out are agreed on
-    // by all four warps at the per-tile named barrier, so they leave together.
+    // Warps on lanes 0-63 finish the first half of the right-hand sides of their
+    // points and warps on lanes 64-127 the second half: each hands the other its
+    // partial sums for the other half through shared memory. Waits that run out
+    // are agreed on by all four warps at the per-tile named barrier, so they
+    // leave together.
     const int quarter = warp & 3;               // TMEM lanes this warp may access
-    const bool owner = quarter < 2;
+    const int half = quarter >> 1;              // 0: hi-plane lanes, 1: lo-plane lanes
     const int rloc = (quarter & 1) * 32 + lane;  // point within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    constexpr int kHalf = KP / 2;
+    auto mine = [&](int p) { return (p >= kHalf) == (half == 1); };  // warp-uniform
     double resid[KP];
 #pragma unroll
     for (int p = 0; p < KP; ++p) resid[p] = 0.0;
@@ -577,12 +581,12 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     // collective and a failed warp leaves at once
     for (int j = 0; j < sch.nt && !(fail && !rows); ++j) {
       const int64_t row = (blockIdx.x + static_cast<int64_t>(j) * gridDim.x) * kTileRows + rloc;
-      const bool valid = owner && row < n && !fail;
-      // this tile's weights (and previous scalings) are fetched before the wait
+      const bool valid = row < n && !fail;
+      // this tile's weights (and previous scalings) of my half, fetched before the wait
       float w[KP], o[KP];
 #pragma unroll
       for (int p = 0; p < KP; ++p) {
-        const bool on = p < a.k && valid;
+        const bool on = p < a.k && valid && mine(p);
         w[p] = (on && rows) ? __ldg(a.w + p * n + row) : 0.f;
         o[p] = (on && a.mode != kMultiUpdate) ? __ldg(a.old + p * n + row) : 0.f;
       }
@@ -604,10 +608,9 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         tc_fence_before();
         mbar_arrive(&sm.s_empty[j & 1]);
         float* xb = sm.xbuf + (j & 1) * (KP * kTileRows);
-        if (!owner) {
 #pragma unroll
-          for (int p = 0; p < KP; ++p) xb[p * kTileRows + rloc] = d[p] + d[KP + p];
-        }
+        for (int p = 0; p < KP; ++p)
+          if (!mine(p)) xb[p * kTileRows + rloc] = d[p] + d[KP + p];
         // all four warps: the hand-over is visible, and nobody has failed
         int all_ok;
         asm volatile(
@@ -623,10 +626,11 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 #pragma unroll
         for (int p = 0; p < KP; ++p) {
           u[p] = 0.f;
-          if (p < a.k && valid) {
-            const float sp = d[p] + d[KP + p] + xb[p * kTileRows + rloc];
+          if (mine(p) && p < a.k && valid) {
+            // hi-plane part + lo-plane part (the same sum on either side)
+            const float sp = (d[p] + d[KP + p]) + xb[p * kTileRows + rloc];
             if (a.mode == kMultiUpdate) {
-              const float v = w[p] / sp;
+              const float v = w[p] * __frcp_rn(sp);
               if (!(v > 0.f && v < INFINITY)) bad |= 1u << p;
               u[p] = v;
             } else {
@@ -639,15 +643,16 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         for (int p = 0; p < KP; ++p) u[p] = o[p];
       }
       if (cols) {
-        if (owner && !fail && j >= 2 &&
+        if (!fail && j >= 2 &&
             !warp_wait(&sm.u_empty[j & 1], static_cast<uint32_t>((j - 2) >> 1) & 1u, lane)) {
           fail = true;
           err = LSF_ERR_TIMEOUT;
         }
         uint16_t* sUb = sm.sU + (j & 1) * (2 * KP * kTileRows);
-        if (owner && !fail) {
+        if (!fail) {
 #pragma unroll
           for (int p = 0; p < KP; ++p) {
+            if (!mine(p)) continue;
             uint16_t hi, lo;
             split_bf16(u[p], hi, lo);
             sUb[sw128(p, rloc)] = hi;
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       if (a.mode == kMultiUpdate) {
 #pragma unroll
         for (int p = 0; p < KP; ++p)
-          if (p < a.k && valid) a.out[p * n + row] = u[p];
+          if (mine(p) && p < a.k && valid) a.out[p * n + row] = u[p];
       }
     }
     // the launch's partial T' (this CTA's points) out of TMEM
