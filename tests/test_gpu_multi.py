@@ -129,6 +129,24 @@ def test_multi_resident_r_vectors_match_oracle(lsf):
         assert abs(got[q]["residual"] - ref[q]["res"]) <= 1e-5
 
 
+def test_multi_flags_scalings_outside_fp32(lsf):
+    # clouds 6 apart at eps = 0.01: every row product underflows in the scaling
+    # domain, so each pair must report LSF_ERR_NONFINITE (as the single solve does)
+    # rather than return a value
+    p = synth.small_problem(44, 300, 280, 2, 64, 0.01, 1, shift=6.0)
+    rng = np.random.default_rng(44)
+    A, B = _weights(rng, 3, 300), _weights(rng, 3, 280)
+    _, got = _run(lsf, p, A, B, 5)
+    for g in got:
+        assert g["status"] & lsf.LSF_ERR_NONFINITE, g
+    dev = torch.device("cuda", 0)
+    t = {q: torch.from_numpy(np.ascontiguousarray(getattr(p, q))).to(dev) for q in "XYZ"}
+    single = lsf.SinkhornProblem(t["X"], t["Y"], torch.from_numpy(A[0]).to(dev),
+                                 torch.from_numpy(B[0]).to(dev), t["Z"], p.eps, mode="stored")
+    single.run(5, debiased=False)
+    assert single.values()["status"] & lsf.LSF_ERR_NONFINITE
+
+
 def test_multi_single_point_closed_form(lsf):
     # n = m = 1: P = a b^T after the first half steps and W = -eps log k_theta(x, y)
     p, A, B = _problem(36, 1, 1, 3, 50, 0.7, 3)
