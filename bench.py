@@ -160,7 +160,7 @@ def oracle_sample(n_sample: int, iters: int) -> dict:
             cores = int(max(nt))
     except Exception:
         pass
-    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "ms": dt * 1e3,
             "sample": f"FP64 oracle (scaling-domain mode, numpy BLAS) on n=m={n_sample} points "
                       f"of the same distributions, r={p.r}, eps={p.eps}, {iters} iterations, "
                       f"debiased (3 solves): {dt:.2f} s"}
@@ -208,7 +208,8 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": statistics.median(v["ms"] for v in vals), "higher_is_better": True,
+        "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
         "cpu_baseline": cb,
