@@ -12,25 +12,30 @@
 //
 // Precision. F is stored as a pair of bf16 planes, hi = RN(F) and lo = RN(F - hi),
 // so hi + lo equals F to 2^-16 relative (4 bytes per entry, as FP32). The small
-// operands are split the same way each pass (T and U into hi, lo), and each
-// product takes the three terms hi*hi + hi*lo + lo*hi, accumulated in FP32 in
-// TMEM; the dropped lo*lo term is below 2^-16 relative.
+// operands are split the same way each pass (T and U into hi, lo). The row
+// products take all four terms (the stacked hi/lo operand makes lo*lo free), the
+// transposed products hi*hi + hi*lo + lo*hi, accumulated in FP32 in TMEM; the
+// dropped term is below 2^-16 relative.
 //
 // Kernel. One CTA per SM, persistent over tiles of 64 points. Per tile the
 // producer warp streams the tile's feature chunks (64 points x 128 features,
-// both planes, 32 KB) into a shared-memory ring with TMA (128-byte swizzle), twice:
-// first for the row products, then again (from L2, a tile later) for the
-// transposed products. One elected thread issues the MMAs:
-//   row sweep:  D_S (64 x 2kp)    += A . [T_hi; T_lo]^T   A = F chunk, K-major (K = features)
-//               D_S (64 x kp)     += A_lo . T_hi^T
-//   col sweep:  D_T[c] (128 x 2kp) += A^T . [U_hi; U_lo]  A^T = the same smem chunk read
-//               MN-major (M = features, K = points), no transposed copy
-// Four epilogue warps read D_S from TMEM (one point per thread, lanes 0-15 of
-// each warp), form u = a / s, write it, split it into bf16 hi/lo and store it as
-// the B operand of the col sweep. D_T holds this CTA's partial T' for the whole
-// launch; at the end it is read out to a per-CTA slot and summed over the CTAs
-// in a fixed order by a second kernel. 64-point tiles keep the data between a
-// chunk's two reads at 256 KB per SM, which L2 holds for all SMs at once.
+// both planes, 32 KB, plus the chunk's block of [T_hi; T_lo]) into a shared-memory
+// ring with TMA (128-byte swizzle), twice: first for the row products, then again
+// (from L2, a tile later, evict-first) for the transposed products. One elected
+// thread issues the MMAs:
+//   row sweep:  D_S (128 x 2kp)   += [A_hi; A_lo] . [T_hi; T_lo]^T   A = F chunk, K-major,
+//               the hi and lo boxes of a 64-feature half stacked as 128 rows
+//   col sweep:  D_T[c] (128 x 2kp) += A_hi^T . [U_hi; U_lo],  (128 x kp) += A_lo^T . U_hi
+//               A^T = the same smem chunk read MN-major (M = features, K = points),
+//               no transposed copy (with 32 right-hand sides: three MMAs into kp columns)
+// Four epilogue warps read D_S from TMEM (lanes 0-63: the hi plane's sums of the
+// tile's points, lanes 64-127: the lo plane's); each warp pair hands the other its
+// partial sums for the other half of the right-hand sides through shared memory,
+// forms u = a / s for its half, writes it, splits it into bf16 hi/lo and stores it
+// as the B operand of the col sweep. D_T holds this CTA's partial T' for the whole
+// launch; at the end it is read out to a per-CTA slot and summed over the CTAs in
+// a fixed order by a second kernel. 64-point tiles keep the data between a chunk's
+// two reads at 256 KB per SM, which L2 holds for all SMs at once.
 // Every wait is bounded; a wait that runs out sets LSF_ERR_TIMEOUT and the CTA
 // still drains its copies and frees its TMEM.
 #include <cuda.h>
