@@ -147,6 +147,27 @@ def test_multi_flags_scalings_outside_fp32(lsf):
     assert single.values()["status"] & lsf.LSF_ERR_NONFINITE
 
 
+def test_split_features_bit_exact(lsf):
+    # lsf_split_features against round-to-nearest-even done on the integer bits:
+    # the same bf16 bit patterns for every entry, zeros in the padding columns
+    from tests.bf16_split import split_pair
+    p = synth.small_problem(45, 777, 10, 3, 200, 0.2, 1)
+    dev = torch.device("cuda", 0)
+    t = {q: torch.from_numpy(np.ascontiguousarray(getattr(p, q))).to(dev) for q in "XYZ"}
+    R = float(lsf.lsf_radius(t["X"], t["Y"]).item())
+    q_, sig = lsf.lsf_gaussian_params(R, p.eps, 3)
+    U, c = lsf.lsf_anchors(t["Z"], q_, sig, p.eps)
+    th = lsf.Theta(U, c, 200, lsf.ldr_for(200), 3, p.eps, R, q_, sig)
+    F, _ = lsf.lsf_features(t["X"], th)
+    F2 = lsf.lsf_split_features(F, 200, 256)
+    torch.cuda.synchronize()
+    got = F2.view(torch.int16).cpu().numpy().view(np.uint16)
+    Fh = F.cpu().numpy()[:, :200]
+    hi, lo = split_pair(Fh)
+    assert np.array_equal(got[0, :, :200], hi) and np.array_equal(got[1, :, :200], lo)
+    assert not got[:, :, 200:].any()
+
+
 def test_multi_single_point_closed_form(lsf):
     # n = m = 1: P = a b^T after the first half steps and W = -eps log k_theta(x, y)
     p, A, B = _problem(36, 1, 1, 3, 50, 0.7, 3)

@@ -515,3 +515,22 @@ def test_accelerated_single_point_is_the_closed_form():
     acc = o.sinkhorn_accelerated(Lx, Ly, p.a, p.b, 5)
     W = o.dual_estimate(p.a, p.b, acc["logu"], acc["logv"], 0.3)
     assert abs(W - (-0.3 * logK)) <= 1e-12 * abs(logK)
+
+
+def test_bf16_pair_split_precision():
+    # the pair features of the tensor-core pass: hi + lo equals F to 2^-16
+    # relative (a rounding to nearest bf16 is within 2^-8 of its argument,
+    # relatively), and the rounding helper agrees with known bf16 values, ties
+    # included
+    from tests.bf16_split import bf16_value, rn_bf16_bits, split_pair
+    assert rn_bf16_bits(np.array([1.0], np.float32))[0] == 0x3F80
+    assert rn_bf16_bits(np.array([1.0 + 2.0 ** -8], np.float32))[0] == 0x3F80   # tie, to even
+    assert rn_bf16_bits(np.array([1.0 + 3 * 2.0 ** -8], np.float32))[0] == 0x3F82  # tie, to even
+    assert rn_bf16_bits(np.array([1.0 + 2.0 ** -8 + 2.0 ** -20], np.float32))[0] == 0x3F81
+    rng = np.random.default_rng(3)
+    F = np.exp(-rng.uniform(0.0, 80.0, size=200000)).astype(np.float32)
+    hi, lo = split_pair(F)
+    approx = bf16_value(hi).astype(np.float64) + bf16_value(lo).astype(np.float64)
+    rel = np.abs(approx - F.astype(np.float64)) / F.astype(np.float64)
+    assert rel.max() <= 2.0 ** -16
+    assert (np.abs(bf16_value(hi).astype(np.float64) - F) / F).max() <= 2.0 ** -8
