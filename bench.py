@@ -583,7 +583,8 @@ def run_accel(args):
     measured as time to the same residual: the accelerated solver runs K iterations
     (three log-domain passes and a host decision per line-search attempt); the
     plain solver is run for 100, 200, 400, ... iterations until its residual
-    ||P 1 - a||_1 is at most the accelerated one's ||P 1 - a||_1 + ||P^T 1 - b||_1.
+    ||P 1 - a||_1 is at most the accelerated one's ||P 1 - a||_1 + ||P^T 1 - b||_1,
+    then bisected to the fewest iterations that reach it.
     Workload: the tiny workload's mixtures at n = m = 2^16, r = 512, eps = 0.01."""
     import torch
     import paper_2006_07057_gb300 as lsf
@@ -614,19 +615,36 @@ def run_accel(args):
     va = prob.values()
     target = va["res_xy"]
     plain = []
-    it = 100
-    while it <= 12800:
-        ms_p, _ = wall(lambda: prob.run(it, debiased=False))
+
+    def plain_run(its):
+        ms_p, _ = wall(lambda: prob.run(its, debiased=False))
         vp = prob.values()
-        plain.append({"iters": it, "ms": ms_p, "residual": vp["res_xy"], "W": vp["W_xy"]})
-        if vp["res_xy"] <= target:
+        rec = {"iters": its, "ms": ms_p, "residual": vp["res_xy"], "W": vp["W_xy"]}
+        plain.append(rec)
+        return rec
+
+    # doubling until the target residual is reached, then bisection between the
+    # last two counts for the fewest iterations that reach it
+    it, lo_it, reached = 100, 0, None
+    while it <= 12800:
+        rec = plain_run(it)
+        if rec["residual"] <= target:
+            reached = rec
             break
-        it *= 2
+        lo_it, it = it, it * 2
+    if reached is not None:
+        hi_it = reached["iters"]
+        while hi_it - lo_it > max(2, hi_it // 64):
+            mid = (lo_it + hi_it) // 2
+            rec = plain_run(mid)
+            if rec["residual"] <= target:
+                hi_it, reached = mid, rec
+            else:
+                lo_it = mid
     clocks = sampler.stop()
     attempts = stats[0]["attempts"]
     # entry updates: per attempt an X column pass, a Y row+column pass and an X row pass
     acc_updates = attempts * (2 * n + n) * p.r
-    reached = plain[-1] if plain[-1]["residual"] <= target else None
     line = {
         "metric": METRIC, "value": acc_updates / (ms_acc / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": 1, "warmup": args.warmup, "ms_per_step": ms_acc, "higher_is_better": True,
