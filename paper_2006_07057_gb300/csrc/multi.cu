@@ -66,8 +66,9 @@ constexpr int kMaxStages = 6;
 __host__ __device__ constexpr int dt_cols(int kp) { return kp == 32 ? kp : 2 * kp; }
 
 // Row chunks of a phase issued before its first transposed chunk: the slack the
-// epilogue has to form the previous tile's scalings (measured best of 1..8).
-constexpr int kSkew = 3;
+// epilogue has to form the previous tile's scalings (measured best of 1..8: 2
+// with 16 right-hand sides, 4 with 32, whose epilogue does twice the work).
+__host__ __device__ constexpr int skew_chunks(int kp) { return kp == 32 ? 4 : 2; }
 
 enum MultiMode : int { kMultiUpdate = 0, kMultiAxpy = 1, kMultiDot = 2 };
 
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
   sch.rows = rows;
   sch.cols = cols;
   sch.lag = (rows && cols) ? 1 : 0;
-  sch.skew = (rows && cols) ? min(kSkew, nchunks) : 0;
+  sch.skew = (rows && cols) ? min(skew_chunks(KP), nchunks) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.nstages; ++s) {
