@@ -188,12 +188,13 @@ __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, int x, int 
                : "memory");
 }
 
-// TMA: one box of a 2-D tensor map at (x, y).
-__device__ __forceinline__ void tma_box2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+// TMA: the r-vector map viewed as (64 features, 2 kp rows, ldr2 / 64 halves):
+// two consecutive halves starting at half h.
+__device__ __forceinline__ void tma_box3d_t(void* dst, const CUtensorMap* map, int h, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(0), "r"(0), "r"(h), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -399,14 +400,11 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         mbar_arrive_expect_tx(&sm.full[s], kStageBytes + (with_t ? 2 * tbox : 0));
         const int y = static_cast<int>(tile * kTileRows);
         const int x = c * kChunkCols;
+        // a box spans both planes of a 64-feature half: [hi | lo], 16 KB
         tma_box(dst, &fmap, x, y, 0, &sm.full[s], pol);
-        tma_box(dst + kBoxBytes, &fmap, x, y, 1, &sm.full[s], pol);
         tma_box(dst + 2 * kBoxBytes, &fmap, x + kBoxCols, y, 0, &sm.full[s], pol);
-        tma_box(dst + 3 * kBoxBytes, &fmap, x + kBoxCols, y, 1, &sm.full[s], pol);
-        if (with_t) {
-          tma_box2d(dst + kStageBytes, &tmap, x, 0, &sm.full[s]);
-          tma_box2d(dst + kStageBytes + tbox, &tmap, x + kBoxCols, 0, &sm.full[s]);
-        }
+        // the chunk's two 64-feature blocks of [T_hi; T_lo] in one box
+        if (with_t) tma_box3d_t(dst + kStageBytes, &tmap, x / kBoxCols, &sm.full[s]);
       }
       __syncwarp();
       return true;
@@ -429,8 +427,8 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
       // the launch's r-vectors, once: one box per 64 features
       const int nb = a.ldr2 / kBoxCols;
       mbar_arrive_expect_tx(sm.t_full, static_cast<uint32_t>(nb * tbox));
-      for (int b = 0; b < nb; ++b)
-        tma_box2d(reinterpret_cast<unsigned char*>(sm.sT) + b * tbox, &tmap, b * kBoxCols, 0, sm.t_full);
+      for (int b = 0; b < nb; b += 2)
+        tma_box3d_t(reinterpret_cast<unsigned char*>(sm.sT) + b * tbox, &tmap, b, sm.t_full);
     }
     __syncwarp();
     for (int q = 0; q < a.prefetch; ++q) prefetch(q);
@@ -828,8 +826,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of the two bf16 planes: dims (ldr2, n, 2), boxes of 64 x 128 x 1,
-// 128-byte swizzle; rows past n read as zeros.
+// Tensor map of the two bf16 planes: dims (ldr2, n, 2), boxes of 64 features x
+// 64 points x both planes ([hi | lo], 16 KB), 128-byte swizzle; rows past n read
+// as zeros.
 int make_pair_map(const uint16_t* F2, int64_t n, int ldr2, CUtensorMap* map) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
@@ -837,7 +836,7 @@ int make_pair_map(const uint16_t* F2, int64_t n, int ldr2, CUtensorMap* map) {
     return fail(LSF_ERR_ARG, "F2 must be 256-byte aligned");
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(ldr2), static_cast<cuuint64_t>(n), 2};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldr2) * 2, static_cast<cuuint64_t>(n) * ldr2 * 2};
-  cuuint32_t box[3] = {kBoxCols, kTileRows, 1};
+  cuuint32_t box[3] = {kBoxCols, kTileRows, 2};
   cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(F2), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -846,16 +845,18 @@ int make_pair_map(const uint16_t* F2, int64_t n, int ldr2, CUtensorMap* map) {
   return LSF_OK;
 }
 
-// Tensor map of a split r-vector block [T_hi; T_lo] (2 kp rows x ldr2 bf16):
-// boxes of 64 features x 2 kp rows, 128-byte swizzle (the K-major B layout).
+// Tensor map of a split r-vector block [T_hi; T_lo] (2 kp rows x ldr2 bf16),
+// viewed as (64 features, 2 kp rows, ldr2 / 64 halves): a box of two halves
+// lands as two K-major B operands of 2 kp rows x 128 B (128-byte swizzle).
 int make_t_map(const uint16_t* t_pair, int kp, int ldr2, CUtensorMap* map) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(ldr2), static_cast<cuuint64_t>(2 * kp)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldr2) * 2};
-  cuuint32_t box[2] = {kBoxCols, static_cast<cuuint32_t>(2 * kp)};
-  cuuint32_t es[2] = {1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(t_pair), dims,
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(kBoxCols), static_cast<cuuint64_t>(2 * kp),
+                        static_cast<cuuint64_t>(ldr2 / kBoxCols)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldr2) * 2, static_cast<cuuint64_t>(kBoxCols) * 2};
+  cuuint32_t box[3] = {kBoxCols, static_cast<cuuint32_t>(2 * kp), 2};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(t_pair), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(LSF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
