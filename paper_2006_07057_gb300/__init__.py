@@ -7,7 +7,9 @@ step runs in the CUDA kernels). PyTorch provides device memory and streams.
 Above them, :class:`SinkhornProblem` keeps one problem resident on the device
 (theta, features, scalings, results, workspace), :func:`sinkhorn_divergence`
 runs it once, and :class:`SinkhornDivergenceFn` is the autograd wrapper whose
-backward pass calls the adjoint kernels.
+backward pass calls the adjoint kernels. :class:`BatchedSolver` runs many
+independent problems in one persistent launch, and :class:`MultiSinkhornProblem`
+solves many weight pairs on one support with the tensor-core passes.
 
 Paper: Scetbon & Cuturi, "Linear Time Sinkhorn Divergences using Positive
 Features", arXiv 2006.07057 (Lemma 1, Alg. 1, Eqs. (2), (6), Prop. 3.3).
