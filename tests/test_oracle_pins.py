@@ -64,6 +64,46 @@ def test_q_limit_small_radius():
     assert q0 == 0.5 and abs(q1 - 0.5) < 1e-10
 
 
+# ---------------------------------------------------------------- Lemma 1 R
+
+def _norm(p):
+    # one point's Euclidean norm by a plain loop over coordinates (brute force)
+    return math.sqrt(math.fsum(float(c) * float(c) for c in p))
+
+
+@pytest.mark.parametrize("far", ["x", "y"])
+def test_radius_is_the_smallest_ball_holding_both_clouds(far):
+    # Lemma 1 (Sec. 3.2) needs every point of both clouds in B(0, R); the
+    # reading taken is the smallest such R centred at 0. So no point lies
+    # outside, and some point of either cloud lies on the sphere. The farthest
+    # point is planted once in X and once in Y, so a radius taken from one
+    # cloud only fails one of the two cases.
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((37, 3)) * 0.5
+    Y = rng.standard_normal((29, 3)) * 0.5 + 0.2
+    target = X if far == "x" else Y
+    target[17] = np.array([3.0, -4.0, 12.0])      # norm exactly 13
+    R = o.radius(X, Y)
+    norms = [_norm(p) for p in X] + [_norm(p) for p in Y]
+    assert all(nv <= R * (1 + 1e-15) for nv in norms)
+    assert abs(R - 13.0) <= 1e-14 * 13.0
+    # symmetric in the two clouds; invariant to a rotation of both
+    assert o.radius(Y, X) == R
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    assert abs(o.radius(X @ Q, Y @ Q) - 13.0) <= 1e-13
+
+
+def test_radius_of_single_points_and_scaling():
+    # one point per cloud: the larger of the two norms; a scaling c of both
+    # clouds scales R by |c|
+    assert o.radius(np.array([[0.6, 0.8]]), np.array([[0.0, 0.5]])) == pytest.approx(1.0, abs=1e-15)
+    assert o.radius(np.array([[0.0, 0.5]]), np.array([[-0.6, -0.8]])) == pytest.approx(1.0, abs=1e-15)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((10, 5))
+    Y = rng.standard_normal((8, 5))
+    assert o.radius(-2.5 * X, -2.5 * Y) == pytest.approx(2.5 * o.radius(X, Y), rel=1e-15)
+
+
 # ---------------------------------------------------------------- feature map
 
 @pytest.mark.parametrize("d,eps", [(2, 0.5), (3, 0.1), (16, 1.0)])
