@@ -43,13 +43,15 @@ import synth  # noqa: E402
 
 METRIC = "Sinkhorn n*r updates/s & %HBM roofline; batched/served solves/s, p99 vs plain"
 UNIT = "updates/s"
-# Peak of the recompute variant: per entry one ex2 (MUFU; 31.5 results per clock
-# per SM measured on this GPU, i.e. 32) and, for d = 3, 4 FP32 operations for the
-# exponent plus 2 per right-hand side (128 FP32 lanes per SM); the FP32 pipe is
-# the tighter bound: 128 / 7 entries per clock per SM (one and two right-hand
-# sides, 4 + 3 on average).
-SMS = 152
-RC_ENTRIES_PER_CLK_SM = 128.0 / 7.0
+# FP32 work per feature entry of a pass at d = 3 (the recompute roofline): 4
+# operations for the exponent A_k + B_i + x.W_k, then per right-hand side one for
+# the row product and one for the transposed product; the debiased lock-step
+# schedule averages 1.5 right-hand sides per pass, so 7 per recomputed entry and
+# 3 per stored entry (which needs no exponent). One ex2 per recomputed entry goes
+# to the special-function unit, whose rate (32 per clock per SM) is above the
+# FP32 pipe's 128 / 7.
+OPS_RC_ENTRY = 7.0
+OPS_ST_ENTRY = 3.0
 
 
 def parse():
@@ -58,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="both", choices=["both", "stored", "recompute", "log"])
+    ap.add_argument("--mode", default="all", choices=["all", "both", "stored", "recompute", "hybrid",
+                                                      "log"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
@@ -144,26 +147,76 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle timing
 
-def oracle_sample(n_sample: int, iters: int) -> dict:
-    """Time the FP64 oracle on a bounded sample of the workload (host cores)."""
-    from oracle import oracle as o
-    p = synth.large_problem(seed=0, n=n_sample, iters=iters)
+ORACLE_SNIPPET = """
+import json, os, sys, time
+sys.path.insert(0, os.environ["LSF_ROOT"])
+import synth
+from oracle import oracle as o
+n, iters, reps = int(sys.argv[1]), int(sys.argv[2]), int(sys.argv[3])
+p = synth.large_problem(seed=0, n=n, iters=iters)
+ts = []
+for _ in range(reps):
     t0 = time.perf_counter()
     o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, p.iters, debiased=True, mode="scaled")
-    dt = time.perf_counter() - t0
-    updates = iters * 3 * (p.n + p.m) * p.r
-    cores = os.cpu_count()
+    ts.append(time.perf_counter() - t0)
+threads = None
+try:
+    from threadpoolctl import threadpool_info
+    nt = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+    threads = int(max(nt)) if nt else None
+except Exception:
+    pass
+print(json.dumps({"times": ts, "r": p.r, "eps": p.eps, "blas_threads": threads}))
+"""
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
     try:
-        from threadpoolctl import threadpool_info
-        nt = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
-        if nt:
-            cores = int(max(nt))
-    except Exception:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
         pass
-    return {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "ms": dt * 1e3,
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_times(n_sample: int, iters: int, reps: int, threads: int | None) -> dict:
+    """Run the oracle in a child process (so that the BLAS thread count is set
+    before numpy loads) and return its per-run times."""
+    env = dict(os.environ, LSF_ROOT=ROOT)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET, str(n_sample), str(iters), str(reps)],
+                         capture_output=True, text=True, env=env, timeout=600, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample(n_sample: int, iters: int, reps: int = 3) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload on the host cores:
+    median of `reps` runs at all cores and at one thread, CPU model recorded."""
+    updates = iters * 3 * (2 * n_sample) * 1024
+    allc = _oracle_times(n_sample, iters, reps, None)
+    one = _oracle_times(n_sample, iters, reps, 1)
+    t_all = statistics.median(allc["times"])
+    t_one = statistics.median(one["times"])
+    cores = allc["blas_threads"] or os.cpu_count()
+    return {"value": updates / t_all, "unit": UNIT, "cores": cores, "kind": "oracle", "ms": t_all * 1e3,
+            "one_thread": {"value": updates / t_one, "ms": t_one * 1e3, "cores": 1},
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "runs": reps,
             "sample": f"FP64 oracle (scaling-domain mode, numpy BLAS) on n=m={n_sample} points "
-                      f"of the same distributions, r={p.r}, eps={p.eps}, {iters} iterations, "
-                      f"debiased (3 solves): {dt:.2f} s"}
+                      f"of the same distributions, r={allc['r']}, eps={allc['eps']}, {iters} "
+                      f"iterations, debiased (3 solves); median of {reps} runs: {t_all:.2f} s at "
+                      f"{cores} threads, {t_one:.2f} s at 1 thread"}
 
 
 # ---------------------------------------------------------------- distributed helpers
@@ -197,14 +250,20 @@ def run_reference(args):
         return 0
     iters = 20
     n_sample = 1 << 13
-    vals = []
-    for _ in range(args.warmup):
-        oracle_sample(n_sample, iters)
-    for _ in range(args.steps):
-        vals.append(oracle_sample(n_sample, iters))
+    # each step: one oracle run on the sample at all host cores (warm-up and timed
+    # runs in one child process, the warm-up runs discarded), plus a 1-thread record
+    allc = _oracle_times(n_sample, iters, args.warmup + args.steps, None)
+    updates = iters * 3 * (2 * n_sample) * 1024
+    vals = [{"value": updates / t, "ms": t * 1e3} for t in allc["times"][args.warmup:]]
     value = statistics.median(v["value"] for v in vals)
-    cb = dict(vals[-1])
-    cb["value"] = value
+    one = _oracle_times(n_sample, iters, 1, 1)
+    cores = allc["blas_threads"] or os.cpu_count()
+    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "one_thread": {"value": updates / one["times"][0], "cores": 1},
+          "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+          "sample": f"FP64 oracle (scaling-domain mode, numpy BLAS) on n=m={n_sample} points of "
+                    f"the same distributions, r=1024, eps=0.1, {iters} iterations, debiased "
+                    f"(3 solves), one run per step at {cores} threads"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -220,7 +279,7 @@ def run_reference(args):
 
 
 def workload_config(args, mode=None):
-    mode = mode or (args.mode if args.mode != "both" else "stored")
+    mode = mode or (args.mode if args.mode not in ("both", "all") else "stored")
     return {"workload": f"large two-cloud: n=m={args.n}, d=3, X~U[0,1]^3 vs Y~N(0.5,0.1^2 I), "
                         f"uniform weights, eps=0.1, r=1024 Gaussian features, {args.iters} "
                         f"iterations, debiased (Eq. 2), {mode} features",
@@ -228,6 +287,9 @@ def workload_config(args, mode=None):
             "debiased": True, "mode": mode,
             "l2": ("inputs larger than L2 (two 4 GiB feature matrices streamed every pass)"
                    if mode in ("stored", "log") else
+                   "inputs larger than L2 (two 2 GiB stored half-feature blocks streamed every "
+                   "pass); a 256 MiB buffer is also written before every timed step"
+                   if mode == "hybrid" else
                    "points and vectors (about 50 MB) fit in L2: a 256 MiB buffer is written "
                    "before every timed step to flush it (its time counted in the step)"),
             "parallelism": f"replicas x{args.gpus} (independent problems, no collective)"}
@@ -791,6 +853,7 @@ def main():
     devt = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
     stream = torch.cuda.current_stream()
     peak, peak_kind = load_peaks()
+    peak_kind_hbm = peak_kind
 
     def barrier():
         if world > 1:
@@ -802,6 +865,8 @@ def main():
 
     # the recompute variant's inputs fit in L2: flush it between timed steps
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    rates = lsf.lsf_probe_pipe_rates()
 
     def measure(mode):
         """Warm-up, then K timed steps of one variant with inputs resident."""
@@ -826,7 +891,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            if mode == "recompute":
+            if mode in ("recompute", "hybrid"):
                 l2_flush.zero_()
             prob = step_resident()
         e1.record(stream)
@@ -835,7 +900,7 @@ def main():
         clocks = sampler.stop()
         ms = slowest(e0.elapsed_time(e1) / args.steps)
         cls = {"stored": lsf.LSF_KERNEL_PASS, "recompute": lsf.LSF_KERNEL_PASS_RECOMPUTE,
-               "log": lsf.LSF_KERNEL_PASS_LOG}[mode]
+               "log": lsf.LSF_KERNEL_PASS_LOG, "hybrid": lsf.LSF_KERNEL_PASS_HYBRID}[mode]
         k_ms, k_n, k_bytes = lsf.lsf_profile_read(cls)
         feat_ms, _, _ = lsf.lsf_profile_read(lsf.LSF_KERNEL_FEATURES)
         lsf.lsf_profile_enable(False)
@@ -851,25 +916,57 @@ def main():
                     "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / max(k_n, 1),
                     "bytes_per_launch": k_bytes / max(k_n, 1), "share_of_step": share}
         else:
-            # one ex2 per entry update: the MUFU rate bounds the pass (FP32 ops per entry:
-            # d + 1 for the exponent, 2 per right-hand side)
             # passes per step: 2 per iteration over each cloud, plus the start and residual
-            # passes (one each per cloud); every pass rebuilds each entry of its cloud once
+            # passes (one each per cloud); every pass uses each entry of its cloud once.
+            # FP32 pipe peak: lanes per clock per SM measured by the packed-FMA probe,
+            # times the SMs and the SM clock sampled during the timed region.
             entries = (2 * args.iters + 2) * (p.n + p.m) * p.r * args.steps
+            launches_n = max(k_n, 1)
             sm_mhz = clocks.get("sm_mhz") or 2070.0
-            alu_peak = RC_ENTRIES_PER_CLK_SM * SMS * sm_mhz * 1e6 / 1e12
-            achieved = entries / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-            roof = {"bound": "alu", "kernel": "recompute_kernel (fused pass, features rebuilt with ex2)",
-                    "achieved": achieved, "peak": alu_peak, "unit": "T entries/s",
-                    "frac": (achieved / alu_peak) if achieved else None,
-                    "peak_kind": f"derived: 128/7 entries/clk/SM (FP32 pipe) x {SMS} SMs x {sm_mhz:.0f} MHz",
-                    "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / max(k_n, 1),
-                    "share_of_step": share}
+            lanes = rates["ffma2_lane_ops_per_clk_sm"]
+            alu_peak = lanes * sms * sm_mhz * 1e6 / 1e12            # T FP32 ops/s
+            alu_kind = (f"measured: {lanes:.1f} FP32 lane-ops/clk/SM (packed FMA probe) x {sms} "
+                        f"SMs x {sm_mhz:.0f} MHz")
+            if mode == "recompute":
+                ops = entries * OPS_RC_ENTRY
+                achieved = ops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+                roof = {"bound": "alu", "kernel": "recompute_kernel (fused pass, features rebuilt with ex2)",
+                        "achieved": achieved, "peak": alu_peak, "unit": "T FP32 ops/s",
+                        "frac": (achieved / alu_peak) if achieved else None, "peak_kind": alu_kind,
+                        "ops_per_entry": OPS_RC_ENTRY, "entries_per_launch": entries / launches_n,
+                        "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / launches_n,
+                        "share_of_step": share}
+            else:
+                # half the columns recomputed (ALU), half streamed (HBM): the kernel's
+                # bound is the larger of the two times; both fractions are reported
+                c0 = lsf.lsf_hybrid_columns(1024)
+                frac_rc = min(c0, p.r) / p.r
+                ops = entries * (frac_rc * OPS_RC_ENTRY + (1 - frac_rc) * OPS_ST_ENTRY)
+                t_alu = ops / (alu_peak * 1e12)
+                t_hbm = (k_bytes / 1e9) / peak
+                t_meas = k_ms / 1e3
+                hbm_ach = (k_bytes / 1e9) / t_meas if k_ms > 0 else None
+                alu_ach = ops / t_meas / 1e12 if k_ms > 0 else None
+                hbm_bound = t_hbm >= t_alu
+                roof = {"bound": "hbm" if hbm_bound else "alu",
+                        "kernel": "hybrid_kernel (fused pass: half the feature columns rebuilt, half streamed)",
+                        "achieved": hbm_ach if hbm_bound else alu_ach,
+                        "peak": peak if hbm_bound else alu_peak,
+                        "unit": "GB/s" if hbm_bound else "T FP32 ops/s",
+                        "frac": (max(t_hbm, t_alu) / t_meas) if k_ms > 0 else None,
+                        "peak_kind": peak_kind_hbm if hbm_bound else alu_kind,
+                        "hbm": {"achieved": hbm_ach, "peak": peak, "unit": "GB/s",
+                                "frac": hbm_ach / peak if hbm_ach else None, "peak_kind": peak_kind_hbm},
+                        "alu": {"achieved": alu_ach, "peak": alu_peak, "unit": "T FP32 ops/s",
+                                "frac": alu_ach / alu_peak if alu_ach else None, "peak_kind": alu_kind},
+                        "traffic": None, "launches": k_n, "avg_launch_ms": k_ms / launches_n,
+                        "bytes_per_launch": k_bytes / launches_n, "share_of_step": share}
         return {"mode": mode, "ms": ms, "value": whole_job_value(updates, world, ms), "launches": launches,
                 "clocks": clocks, "roofline": roof, "vals": vals,
                 "features_ms_per_step": feat_ms / args.steps}
 
-    modes = ["stored", "recompute"] if args.mode == "both" else [args.mode]
+    modes = (["stored", "recompute", "hybrid"] if args.mode == "all" else
+             ["stored", "recompute"] if args.mode == "both" else [args.mode])
     runs = [measure(m) for m in modes]
     best = max(runs, key=lambda r: r["value"])
 
@@ -880,6 +977,8 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in host.values())
 
         def step_e2e():
+            if best["mode"] in ("recompute", "hybrid"):
+                l2_flush.zero_()
             d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
             pr = lsf.SinkhornProblem(d["X"], d["Y"], d["a"], d["b"], d["Z"], p.eps, mode=best["mode"])
             pr.run(args.iters, debiased=True)
@@ -902,6 +1001,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(1 << 13, 20)
+    rates["sms"] = sms
 
     if rank == 0:
         vals = best["vals"]
@@ -920,6 +1020,7 @@ def main():
             "result": {"W_bar": vals["W_bar"], "W_xy": vals["W_xy"], "res_xy": vals["res_xy"],
                        "status": vals["status"]},
             "features_ms_per_step": best["features_ms_per_step"],
+            "pipe_rates": rates,
         }
         print(json.dumps(line))
     if world > 1:

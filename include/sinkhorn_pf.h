@@ -51,10 +51,16 @@ typedef enum {
 typedef enum {
   LSF_MODE_STORED = 0,     /* stream stored shifted features F (HBM-bound)            */
   LSF_MODE_RECOMPUTE = 1,  /* recompute features from X, U in registers (ALU-bound)   */
-  LSF_MODE_LOG = 2         /* stored LOG features, log-domain iterates (stabilised):
+  LSF_MODE_LOG = 2,        /* stored LOG features, log-domain iterates (stabilised):
                               F holds log features (lsf_log_features), the scalings
                               u, v hold log u~, log v~, t_u, t_v hold log t, and the
                               global factor M is 0                                    */
+  LSF_MODE_HYBRID = 3      /* the first c0 feature columns recomputed in registers (as
+                              RECOMPUTE), the other ldr - c0 streamed from a stored
+                              block (as STORED), in the same pass, so HBM and the
+                              FP32 pipe work at once. F holds the stored block
+                              (lsf_hybrid_features, n x (ldr - c0)); X is needed too.
+                              c0 = lsf_hybrid_columns(ldr). Scalings as STORED.       */
 } lsf_mode;
 
 /* Feature parameters theta = (U, c), shared by every term of Eq. (2). Device pointers. */
@@ -161,6 +167,25 @@ int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta,
                   float* shift, float* spread, void* stream);
 
 /*
+ * Column split of LSF_MODE_HYBRID for row stride ldr (multiple of 4 in
+ * [8, 1024]): *c0 receives the first stored column. Columns [0, c0) are rebuilt
+ * in the pass, columns [c0, ldr) are read from the stored block (half of the
+ * float4 column groups, rounded down, are stored). Host only.
+ * Errors: LSF_ERR_ARG (NULL), LSF_ERR_UNSUPPORTED (ldr).
+ */
+int lsf_hybrid_columns(int ldr, int* c0);
+
+/*
+ * Features of LSF_MODE_HYBRID (Lemma 1 map, as lsf_features): the row shifts
+ * over all r features, shift[i] = max_{k<r} L_ik, and the stored block
+ *   Fs[i*(ldr - c0) + (k - c0)] = exp(L_ik - shift[i]) for c0 <= k < r, 0 for k >= r,
+ * with c0 = lsf_hybrid_columns(theta->ldr). X: n x d device; Fs: n x (ldr - c0)
+ * device (16-byte aligned); shift: n device; spread as lsf_features.
+ */
+int lsf_hybrid_features(const float* X, int64_t n, const lsf_theta* theta,
+                        float* Fs, float* shift, float* spread, void* stream);
+
+/*
  * Arc-cosine positive features (Sec. 3.2, "Arc-cosine kernels", and the lemma
  * in the appendix): the perturbed kernel k_s(x,y) + kappa, where
  *   k_s(x,y) = int Theta_s(u.x) Theta_s(u.y) dN(0,I)(u),  Theta_s(w) = sqrt(2) max(0,w)^s,
@@ -264,10 +289,14 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
  * Scratch: a fixed 8 MiB array in the library's device image (kept by every GPU
  * that loads the library until the process exits). Problems whose
  * lsf_workspace_bytes(theta->ldr) exceeds 8 MiB are rejected with
- * LSF_ERR_UNSUPPORTED and a message; nothing is allocated, ever.
+ * LSF_ERR_UNSUPPORTED and a message; nothing is allocated, ever. (The scratch
+ * grows with the SM count: at ldr = 1024 it is about 5.3 MB on 152 SMs, so the
+ * rejection is only reached on parts with about 256 SMs or more.)
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture. Every call shares the one array: the solve clears
+ * before any stream capture. The address is kept for the life of the process:
+ * after cudaDeviceReset on a device, do not call this entry point on that device
+ * again in the same process. Every call shares the one array: the solve clears
  * the parts that must start at zero, and two calls that can overlap on the GPU
  * (different streams, or different host threads) race on it and give wrong
  * results. Results, errors and device status are those of lsf_solve.
@@ -358,6 +387,23 @@ int lsf_solve_batched(const lsf_batch_info* info, void* plan, int iters, void* s
  * Errors: LSF_ERR_ARG for a value outside 0..2.
  */
 int lsf_set_batch_strategy(int strategy);
+
+/*
+ * Failure-detection hook of the batched solver, for tests (not a paper
+ * quantity). Every wait of the persistent kernel is bounded; this makes one run
+ * out on purpose, without a GPU fault.
+ * wait_limit_ns: the limit of the kernel's waits on round flags and on its
+ * shared-memory ring (default 4e9 ns; range [1e4, 6e10]). The drain of the
+ * copies still in flight at exit keeps the default limit.
+ * stall_rounds: 0 (default) or 1. With 1, each consumer waits for a problem's
+ * round flag to pass one round beyond the round the kernel will ever publish (a
+ * flag nothing sets): from the second round on every such wait runs out, the
+ * kernel stops streaming, drains its copies and returns, and every problem's
+ * lsf_result.status gets LSF_ERR_TIMEOUT. The device stays usable.
+ * Process-wide; reset with lsf_set_batch_fault(4000000000, 0).
+ * Errors: LSF_ERR_ARG for values outside those ranges.
+ */
+int lsf_set_batch_fault(unsigned long long wait_limit_ns, int stall_rounds);
 
 /* ---------------------------------------------------------------- adjoint */
 
@@ -562,6 +608,7 @@ typedef enum {
   LSF_KERNEL_ADJOINT,        /* gradient kernels (points, weights, anchors) */
   LSF_KERNEL_SMALL,          /* cluster-persistent small-problem solver   */
   LSF_KERNEL_PASS_MULTI,     /* tensor-core passes, many right-hand sides */
+  LSF_KERNEL_PASS_HYBRID,    /* fused passes, stored and recomputed columns */
   LSF_KERNEL_NCLASSES
 } lsf_kernel_class;
 
@@ -575,6 +622,17 @@ typedef enum {
  */
 int lsf_profile_enable(int on);
 int lsf_profile_read(int kernel_class, double* total_ms, int64_t* launches, double* bytes);
+
+/*
+ * Measured issue rates of the pipes the recompute and hybrid passes are bound by,
+ * per SM clock per SM (not a paper quantity: the denominators of their ALU
+ * roofline). One CTA of 1024 threads per SM runs independent chains of one
+ * instruction kind; the SM cycle counter around the loop gives, per clock and
+ * SM, the FP32 lane operations of the packed two-lane FMA (*ffma2_lane_ops) and
+ * of the scalar FMA (*ffma_lane_ops), and the ex2 results of the special-function
+ * unit (*ex2_ops). Host outputs; synchronises the stream.
+ */
+int lsf_probe_pipe_rates(double* ffma2_lane_ops, double* ffma_lane_ops, double* ex2_ops, void* stream);
 
 /* Number of kernel launches the library issued since the last lsf_launch_count_reset(). */
 int64_t lsf_launch_count(void);

@@ -28,11 +28,13 @@ from ._binding import (LSF_ERR_ARG, LSF_ERR_UNSUPPORTED, LSF_ERR_WORKSPACE,  # n
                        LSF_KERNEL_FEATURES, LSF_KERNEL_OTHER, LSF_KERNEL_PASS, LSF_KERNEL_PASS_LOG,
                        LsfAccelInfo, LsfBatchInfo, LsfBatchProblem, LsfMultiCloud,
                        LsfMultiScalings, LSF_KERNEL_PASS_MULTI,
-                       LSF_KERNEL_PASS_RECOMPUTE, LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
+                       LSF_KERNEL_PASS_RECOMPUTE, LSF_KERNEL_PASS_HYBRID, LSF_MODE_HYBRID,
+                       LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
                        LsfArccos, LsfTheta, check, header_symbols, lib)
 
-MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG}
+MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG,
+         "hybrid": LSF_MODE_HYBRID}
 
 # "auto" routes a problem straight to the log domain when the within-row
 # log-feature spread exceeds this many nats. Shifted features only underflow
@@ -210,6 +212,28 @@ def lsf_row_shift(X, theta: Theta, shift=None, spread=None, stream=None):
     check(lib().lsf_row_shift(_p(X), n, ctypes.byref(th), _p(shift), _p(spread),
                               _stream(stream)), "lsf_row_shift")
     return shift
+
+
+def lsf_hybrid_columns(ldr: int) -> int:
+    """First stored column c0 of the hybrid pass for row stride ldr."""
+    c0 = ctypes.c_int()
+    check(lib().lsf_hybrid_columns(int(ldr), ctypes.byref(c0)), "lsf_hybrid_columns")
+    return c0.value
+
+
+def lsf_hybrid_features(X, theta: Theta, Fs=None, shift=None, spread=None, stream=None):
+    """Row shifts and the stored block (columns c0..ldr-1) of the hybrid pass."""
+    _f32(X)
+    n = X.shape[0]
+    c0 = lsf_hybrid_columns(theta.ldr)
+    if Fs is None:
+        Fs = torch.empty(n, theta.ldr - c0, dtype=torch.float32, device=X.device)
+    if shift is None:
+        shift = torch.empty(n, dtype=torch.float32, device=X.device)
+    th = theta.as_c()
+    check(lib().lsf_hybrid_features(_p(X), n, ctypes.byref(th), _p(Fs), _p(shift), _p(spread),
+                                    _stream(stream)), "lsf_hybrid_features")
+    return Fs, shift
 
 
 def lsf_arccos_anchors(Z, sigma: float, U=None, c=None, stream=None):
@@ -428,6 +452,12 @@ def lsf_set_batch_strategy(strategy: int) -> None:
     check(lib().lsf_set_batch_strategy(int(strategy)), "lsf_set_batch_strategy")
 
 
+def lsf_set_batch_fault(wait_limit_ns: int = 4_000_000_000, stall_rounds: int = 0) -> None:
+    """Failure-detection hook of the batched solver (tests): the limit of its
+    bounded waits, and whether its round flags are made unreachable."""
+    check(lib().lsf_set_batch_fault(int(wait_limit_ns), int(stall_rounds)), "lsf_set_batch_fault")
+
+
 def lsf_set_small_solver(policy: int, max_entries: int = 1 << 24) -> None:
     """0: never use the cluster small-problem solver, 1: by size (default), 2: always."""
     check(lib().lsf_set_small_solver(int(policy), int(max_entries)), "lsf_set_small_solver")
@@ -455,6 +485,16 @@ def lsf_profile_read(kernel_class: int) -> tuple[float, int, float]:
     check(lib().lsf_profile_read(int(kernel_class), ctypes.byref(ms), ctypes.byref(n),
                                  ctypes.byref(by)), "lsf_profile_read")
     return ms.value, n.value, by.value
+
+
+def lsf_probe_pipe_rates(stream=None) -> dict:
+    """Measured results per clock per SM: packed and scalar FP32 FMA lane operations
+    and ex2 (the recompute and hybrid passes' ALU roofline). Synchronises."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib().lsf_probe_pipe_rates(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                     _stream(stream)), "lsf_probe_pipe_rates")
+    return {"ffma2_lane_ops_per_clk_sm": a.value, "ffma_lane_ops_per_clk_sm": b.value,
+            "ex2_per_clk_sm": c.value}
 
 
 def lsf_launch_count() -> int:
@@ -496,8 +536,8 @@ class SinkhornProblem:
             raise ValueError(f"mode must be one of {sorted(MODES) + ['auto']}")
         if kernel not in ("gaussian", "arccos"):
             raise ValueError("kernel must be 'gaussian' or 'arccos'")
-        if kernel == "arccos" and mode == "recompute":
-            raise ValueError("the recompute mode evaluates the Gaussian map only")
+        if kernel == "arccos" and mode in ("recompute", "hybrid"):
+            raise ValueError("the recompute and hybrid modes evaluate the Gaussian map only")
         self.kernel = kernel
         self.arccos = None
         for t in (X, Y, a, b, Z):
@@ -556,6 +596,9 @@ class SinkhornProblem:
         elif self.mode == "log":
             Fx, sx = lsf_log_features(X, th, spread=self.spread, stream=st)
             Fy, sy = lsf_log_features(Y, th, spread=self.spread, stream=st)
+        elif self.mode == "hybrid":
+            Fx, sx = lsf_hybrid_features(X, th, spread=self.spread, stream=st)
+            Fy, sy = lsf_hybrid_features(Y, th, spread=self.spread, stream=st)
         else:
             Fx = Fy = None
             sx = lsf_row_shift(X, th, spread=self.spread, stream=st)
@@ -652,8 +695,8 @@ class SinkhornProblem:
         deb = self.debiased if debiased is None else bool(debiased)
         if deb and not self.debiased:
             raise ValueError("the debiased gradient needs a debiased run")
-        if self.mode == "recompute":
-            raise NotImplementedError("the adjoint reads stored features")
+        if self.mode in ("recompute", "hybrid"):
+            raise NotImplementedError("the adjoint reads the full stored features")
         if self.arccos is not None:
             raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
         dev = self.X.device
@@ -676,8 +719,8 @@ class SinkhornProblem:
         deb = self.debiased if debiased is None else bool(debiased)
         if deb and not self.debiased:
             raise ValueError("the debiased gradient needs a debiased run")
-        if self.mode == "recompute":
-            raise NotImplementedError("the adjoint reads stored features")
+        if self.mode in ("recompute", "hybrid"):
+            raise NotImplementedError("the adjoint reads the full stored features")
         if self.arccos is not None:
             raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
         if wrt not in ("U", "Z"):

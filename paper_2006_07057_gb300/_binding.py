@@ -30,6 +30,7 @@ LSF_ERR_UNSUPPORTED = 32
 LSF_MODE_STORED = 0
 LSF_MODE_RECOMPUTE = 1
 LSF_MODE_LOG = 2
+LSF_MODE_HYBRID = 3
 
 LSF_KERNEL_PASS = 0
 LSF_KERNEL_PASS_RECOMPUTE = 1
@@ -40,6 +41,7 @@ LSF_KERNEL_BATCHED = 5
 LSF_KERNEL_ADJOINT = 6
 LSF_KERNEL_SMALL = 7
 LSF_KERNEL_PASS_MULTI = 8
+LSF_KERNEL_PASS_HYBRID = 9
 
 
 class LsfTheta(ctypes.Structure):
@@ -113,6 +115,9 @@ _SIGNATURES = {
     "lsf_row_shift": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p]),
     "lsf_log_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
                                  c_void_p]),
+    "lsf_hybrid_columns": (c_int, [c_int, _P(c_int)]),
+    "lsf_hybrid_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
+                                    c_void_p]),
     "lsf_workspace_bytes": (c_int, [c_int, _P(c_size_t)]),
     "lsf_accel_workspace_bytes": (c_int, [c_int64, c_int64, c_int, _P(c_size_t)]),
     "lsf_solve_accelerated": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double,
@@ -144,11 +149,13 @@ _SIGNATURES = {
                                c_void_p, c_size_t, c_void_p]),
     "lsf_solve_batched": (c_int, [_P(LsfBatchInfo), c_void_p, c_int, c_void_p]),
     "lsf_set_batch_strategy": (c_int, [c_int]),
+    "lsf_set_batch_fault": (c_int, [ctypes.c_ulonglong, c_int]),
     "lsf_set_pass_tiling": (c_int, [c_int, c_int]),
     "lsf_set_small_solver": (c_int, [c_int, ctypes.c_int64]),
     "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),
     "lsf_profile_enable": (c_int, [c_int]),
     "lsf_profile_read": (c_int, [c_int, _P(c_double), _P(c_int64), _P(c_double)]),
+    "lsf_probe_pipe_rates": (c_int, [_P(c_double), _P(c_double), _P(c_double), c_void_p]),
     "lsf_launch_count": (c_int64, []),
     "lsf_launch_count_reset": (None, []),
 }

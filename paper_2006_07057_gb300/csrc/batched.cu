@@ -60,6 +60,8 @@ struct BatchArgs {
   int tile_rows;
   int nstages;
   int rounds;
+  unsigned long long wait_ns;  // limit of the bounded waits on flags and ring slots
+  unsigned stall;              // failure-detection hook: rounds added to every flag target
 };
 
 __device__ __forceinline__ int round_side(int r, int rounds) {
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
         const int s = it % S;
         const uint32_t ph = static_cast<uint32_t>(it / S) & 1u;
         int ok = 1;
-        if (lane == 0) ok = mbar_wait_bounded(&ring.empty[s], ph ^ 1u) ? 1 : 0;
+        if (lane == 0) ok = mbar_wait_bounded(&ring.empty[s], ph ^ 1u, A.wait_ns) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           flag |= LSF_ERR_TIMEOUT;
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
         cp_async_mbar_arrive(&ring.full[s]);
       }
     }
+    // drain: the copies still in flight land in this CTA's shared memory, so wait
+    // for each of them (with the full default limit) before the CTA may exit
     const int used = min(it, S);
     for (int j = 0; j < used; ++j) {
       const int itj = it - 1 - j;
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
 
       for (int64_t ti = lo; ti < hi && !dead; ++ti, ++it) {
         const int s = it % S;
-        if (!ring_wait_full(ring, it, lane)) {
+        if (!ring_wait_full(ring, it, lane, A.wait_ns)) {
           flag |= LSF_ERR_TIMEOUT;
           dead = true;
           break;
@@ -260,10 +264,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           int ok = 1;
           if (lane == 0 && r > 0) {
             const unsigned* fp = A.flag + cur;
-            if (ld_acquire(fp) < static_cast<unsigned>(r)) {
+            const unsigned target = static_cast<unsigned>(r) + A.stall;
+            if (ld_acquire(fp) < target) {
               const uint64_t t0 = globaltimer_ns();
-              while (ld_acquire(fp) < static_cast<unsigned>(r)) {
-                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+              while (ld_acquire(fp) < target) {
+                if (globaltimer_ns() - t0 > A.wait_ns) {
                   ok = 0;
                   break;
                 }
@@ -501,6 +506,8 @@ struct PlanLayout {
 // one launch), 2 by rule (clusters when there are enough problems to occupy
 // every SM with clusters and every problem is small: (n + m) ldr <= 2^18).
 int g_batch_strategy = 0;
+unsigned long long g_batch_wait_ns = kWaitLimitNs;  // lsf_set_batch_fault
+int g_batch_stall = 0;
 
 }  // namespace
 }  // namespace lsf
@@ -695,6 +702,8 @@ extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int ite
   A.tile_rows = info->tile_rows;
   A.nstages = info->stages;
   A.rounds = 2 * iters + 2;
+  A.wait_ns = g_batch_wait_ns;
+  A.stall = static_cast<unsigned>(g_batch_stall);
   if (info->strategy == 1) {
     // one cluster per problem, then the Eq. (6) reduction of every problem
     int rc = small_solve_table(reinterpret_cast<const SProb*>(base + o_sprobs), count, info->ldr, iters, st);
@@ -737,6 +746,16 @@ extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int ite
     batched_divergence_kernel<<<count, 256, 0, st>>>(A.probs, info->mode == LSF_MODE_LOG ? 1 : 0);
   }
   return check_launch("batched_divergence_kernel");
+}
+
+extern "C" int lsf_set_batch_fault(unsigned long long wait_limit_ns, int stall_rounds) {
+  if (wait_limit_ns < 10000ull || wait_limit_ns > 60000000000ull)
+    return fail(LSF_ERR_ARG, "lsf_set_batch_fault: wait_limit_ns outside [1e4, 6e10]");
+  if (stall_rounds != 0 && stall_rounds != 1)
+    return fail(LSF_ERR_ARG, "lsf_set_batch_fault: stall_rounds must be 0 or 1");
+  g_batch_wait_ns = wait_limit_ns;
+  g_batch_stall = stall_rounds;
+  return LSF_OK;
 }
 
 extern "C" int lsf_set_batch_strategy(int strategy) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "recompute.cuh"
 
 namespace lsf {
 namespace {
@@ -84,11 +85,15 @@ __device__ __forceinline__ float map_log(float acc, float ck, int k, const MapAr
 // F = exp(L - shift) (padding 0), KIND 2 stores the log form L - shift
 // (padding -inf) for the log-domain passes. The spread is max - min over the
 // finite log-features of a row (an exact zero feature has no range to lose).
+// The stored kinds write columns [c0, ldr) of every row (c0 a multiple of 4) to
+// F + i * ldf + (k - c0): the whole row for c0 = 0, ldf = ldr, or the stored
+// block of a hybrid pass.
 template <int C, int KIND, int MAP>
 __global__ void __launch_bounds__(kFeatWarps * 32)
     features_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ U,
                     const float* __restrict__ c, int ldr, const MapArgs m,
-                    float* __restrict__ F, float* __restrict__ shift, unsigned* spread_key) {
+                    float* __restrict__ F, float* __restrict__ shift, unsigned* spread_key,
+                    int c0, int ldf) {
   extern __shared__ __align__(16) float sU[];  // [min(d, kFeatDChunk)][ldr] then c[ldr]
   float* sc = sU + static_cast<size_t>(min(d, kFeatDChunk)) * ldr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -172,11 +177,11 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
       if (lane == 0) shift[i] = mx;
       local_spread = fmaxf(local_spread, mx - mn);
       if (KIND == 1) {
-        float* Fi = F + i * ldr;
+        float* Fi = F + i * ldf - c0;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           const int col = 4 * lane + 128 * j;
-          if (col < ldr) {
+          if (col < ldr && col >= c0) {
             float4 o;
             o.x = (col + 0 < m.rf) ? expf(acc[q][j][0] - mx) : 0.f;
             o.y = (col + 1 < m.rf) ? expf(acc[q][j][1] - mx) : 0.f;
@@ -186,11 +191,11 @@ __global__ void __launch_bounds__(kFeatWarps * 32)
           }
         }
       } else if (KIND == 2) {
-        float* Fi = F + i * ldr;
+        float* Fi = F + i * ldf - c0;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           const int col = 4 * lane + 128 * j;
-          if (col < ldr) {
+          if (col < ldr && col >= c0) {
             float4 o;
             o.x = (col + 0 < m.rf) ? acc[q][j][0] - mx : -INFINITY;
             o.y = (col + 1 < m.rf) ? acc[q][j][1] - mx : -INFINITY;
@@ -360,8 +365,10 @@ int launch_features_tiled(const float* X, int64_t n, int d, const float* U, cons
 // Shared front end of the feature entry points (both maps, all three kinds).
 template <int KIND, int MAP>
 int launch_map(const float* X, int64_t n, int d, const float* U, const float* c, int ldr,
-               const MapArgs& m, float* F, float* shift, float* spread, cudaStream_t st) {
+               const MapArgs& m, float* F, float* shift, float* spread, cudaStream_t st,
+               int c0 = 0) {
   constexpr bool STORE = KIND != 0;
+  const int ldf = ldr - c0;
   if (!X || !shift || (STORE && !F)) return fail(LSF_ERR_ARG, "features: NULL argument");
   if (!U || !c) return fail(LSF_ERR_ARG, "features: NULL anchors or constants");
   if (n < 1) return fail(LSF_ERR_ARG, "features: n must be >= 1");
@@ -371,7 +378,11 @@ int launch_map(const float* X, int64_t n, int d, const float* U, const float* c,
   if (STORE && reinterpret_cast<uintptr_t>(F) % 16 != 0)
     return fail(LSF_ERR_ARG, "features: F must be 16-byte aligned");
   unsigned* skey = reinterpret_cast<unsigned*>(spread);
-  if (STORE && d > kFeatDChunk) return launch_features_tiled<KIND, MAP>(X, n, d, U, c, ldr, m, F, shift, skey, st);
+  if (c0 < 0 || c0 % 4 != 0 || c0 >= ldr) return fail(LSF_ERR_ARG, "features: bad column window");
+  if (STORE && d > kFeatDChunk) {
+    if (c0 != 0) return fail(LSF_ERR_UNSUPPORTED, "features: a column window needs d <= 32");
+    return launch_features_tiled<KIND, MAP>(X, n, d, U, c, ldr, m, F, shift, skey, st);
+  }
   const int C = (ldr + 127) / 128;
   const int dchunk = d < kFeatDChunk ? d : kFeatDChunk;
   const size_t smem = sizeof(float) * (static_cast<size_t>(dchunk) * ldr + ldr);
@@ -379,13 +390,13 @@ int launch_map(const float* X, int64_t n, int d, const float* U, const float* c,
   int64_t grid = (n + rows_per_cta - 1) / rows_per_cta;
   const int64_t cap = static_cast<int64_t>(device_info().sms) * 8;
   if (grid > cap) grid = cap;
-  double bytes = 4.0 * n * d + 4.0 * n + (STORE ? 4.0 * n * ldr : 0.0);
+  double bytes = 4.0 * n * d + 4.0 * n + (STORE ? 4.0 * n * ldf : 0.0);
   LaunchScope ls(st, LSF_KERNEL_FEATURES, bytes);
 #define LSF_FEAT_CASE(CC)                                                                   \
   case CC: {                                                                                \
     auto kern = features_kernel<CC, KIND, MAP>;                                            \
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-    kern<<<(unsigned)grid, kFeatWarps * 32, smem, st>>>(X, n, d, U, c, ldr, m, F, shift, skey); \
+    kern<<<(unsigned)grid, kFeatWarps * 32, smem, st>>>(X, n, d, U, c, ldr, m, F, shift, skey, c0, ldf); \
   } break;
   switch (C <= 1 ? 1 : C <= 2 ? 2 : C <= 4 ? 4 : 8) {
     LSF_FEAT_CASE(1)
@@ -399,7 +410,7 @@ int launch_map(const float* X, int64_t n, int d, const float* U, const float* c,
 
 template <int KIND>
 int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, float* shift,
-                    float* spread, cudaStream_t st) {
+                    float* spread, cudaStream_t st, int c0 = 0) {
   if (!th) return fail(LSF_ERR_ARG, "features: NULL theta");
   if (th->r > th->ldr) return fail(LSF_ERR_ARG, "features: need r <= ldr");
   if (!(th->eps > 0.0)) return fail(LSF_ERR_ARG, "features: eps must be > 0");
@@ -407,7 +418,7 @@ int launch_features(const float* X, int64_t n, const lsf_theta* th, float* F, fl
   m.r = th->r;
   m.rf = th->r;
   m.two_over_eps = static_cast<float>(2.0 / th->eps);
-  return launch_map<KIND, kMapGauss>(X, n, th->d, th->U, th->c, th->ldr, m, F, shift, spread, st);
+  return launch_map<KIND, kMapGauss>(X, n, th->d, th->U, th->c, th->ldr, m, F, shift, spread, st, c0);
 }
 
 template <int KIND>
@@ -490,6 +501,23 @@ int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta, float* L
 int lsf_row_shift(const float* X, int64_t n, const lsf_theta* theta, float* shift,
                   float* spread, void* stream) {
   return launch_features<0>(X, n, theta, nullptr, shift, spread, as_stream(stream));
+}
+
+int lsf_hybrid_columns(int ldr, int* c0) {
+  if (!c0) return fail(LSF_ERR_ARG, "lsf_hybrid_columns: NULL output");
+  if (ldr < 8 || ldr % 4 != 0 || ldr > 1024)
+    return fail(LSF_ERR_UNSUPPORTED, "lsf_hybrid_columns: ldr must be a multiple of 4 in [8, 1024]");
+  *c0 = hybrid_first_stored(ldr);
+  return LSF_OK;
+}
+
+int lsf_hybrid_features(const float* X, int64_t n, const lsf_theta* theta, float* Fs, float* shift,
+                        float* spread, void* stream) {
+  if (!theta) return fail(LSF_ERR_ARG, "lsf_hybrid_features: NULL theta");
+  int c0 = 0;
+  const int rc = lsf_hybrid_columns(theta->ldr, &c0);
+  if (rc != LSF_OK) return rc;
+  return launch_features<1>(X, n, theta, Fs, shift, spread, as_stream(stream), c0);
 }
 
 int lsf_arccos_anchors(const float* Z, int r, int d, double sigma, float* U, float* c, void* stream) {

@@ -42,33 +42,6 @@ constexpr int kRcWarps = 8;                      // compute warps
 constexpr int kRcThreads = (kRcWarps + 1) * 32;  // + the service warp
 constexpr int kRcRB = 8;  // rows per group per batch
 
-// Row record in shared memory, in float4s: (x_0, x_0, x_1, x_1), ..., (B, B)
-// (each value twice, so one load gives the broadcast pair a packed instruction
-// takes; padded to a float4 boundary), then (w, old) of each right-hand side.
-template <int D>
-struct RowPack {
-  static constexpr int kXV = (2 * (D + 1) + 3) / 4;  // float4s of x and B, doubled
-  static constexpr int kSV = kXV + 1;                // + (w0, old0, w1, old1)
-};
-
-// The GW warp partials of one row, summed in a fixed tree order (vector loads;
-// the partials of a row are contiguous and GW-aligned).
-template <int GW>
-__device__ __forceinline__ float sum_partials(const float* p) {
-  if constexpr (GW == 8) {
-    const float4 lo = reinterpret_cast<const float4*>(p)[0], hi = reinterpret_cast<const float4*>(p)[1];
-    return ((lo.x + lo.y) + (lo.z + lo.w)) + ((hi.x + hi.y) + (hi.z + hi.w));
-  } else if constexpr (GW == 4) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    return (v.x + v.y) + (v.z + v.w);
-  } else if constexpr (GW == 2) {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    return v.x + v.y;
-  } else {
-    return p[0];
-  }
-}
-
 template <int GW, int D, int NRHS>
 __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     recompute_kernel(const RecomputeArgs a, const int mode) {

@@ -91,11 +91,12 @@ __device__ __forceinline__ void ring_produce(const Ring& r, const float* F, int6
 }
 
 // Consumer side: wait (bounded) until the stage of the it-th tile is full.
-__device__ __forceinline__ bool ring_wait_full(const Ring& r, int it, int lane) {
+__device__ __forceinline__ bool ring_wait_full(const Ring& r, int it, int lane,
+                                               unsigned long long limit_ns = kWaitLimitNs) {
   const int s = it % r.S;
   const uint32_t ph = static_cast<uint32_t>(it / r.S) & 1u;
   int ok = 1;
-  if (lane == 0) ok = mbar_wait_bounded(&r.full[s], ph) ? 1 : 0;
+  if (lane == 0) ok = mbar_wait_bounded(&r.full[s], ph, limit_ns) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 

@@ -187,6 +187,10 @@ int check_cloud(const lsf_cloud* c, int mode, const char* name) {
       return fail(LSF_ERR_ARG, "%s: F must be 16-byte aligned", name);
   } else if (mode == LSF_MODE_RECOMPUTE) {
     if (!c->X) return fail(LSF_ERR_ARG, "%s: recompute mode needs X", name);
+  } else if (mode == LSF_MODE_HYBRID) {
+    if (!c->X || !c->F) return fail(LSF_ERR_ARG, "%s: hybrid mode needs X and the stored block in F", name);
+    if (reinterpret_cast<uintptr_t>(c->F) % 16 != 0)
+      return fail(LSF_ERR_ARG, "%s: F must be 16-byte aligned", name);
   } else if (mode == LSF_MODE_LOG) {
     if (!c->F) return fail(LSF_ERR_ARG, "%s: log mode needs the log features in F", name);
     if (reinterpret_cast<uintptr_t>(c->F) % 16 != 0)
@@ -237,6 +241,13 @@ int run_pass(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, int 
   a.rpart = ws.rpart;
   a.counter = ws.counters + kPassCounter;
   a.status = status;
+  if (mode == LSF_MODE_HYBRID) {
+    HybridArgs h{};
+    h.rc = a;
+    h.Fs = cl->F;
+    h.c0 = hybrid_first_stored(th->ldr);
+    return launch_hybrid_pass(pmode, nrhs, h, st);
+  }
   return launch_recompute_pass(pmode, nrhs, a, st);
 }
 

@@ -71,3 +71,13 @@ def test_device_entry_points_validate_before_launching():
 
 def test_ldr_rounding():
     assert [lsf.ldr_for(r) for r in (1, 3, 4, 100, 1023, 1024)] == [4, 4, 4, 100, 1024, 1024]
+
+
+def test_hybrid_column_split_is_host_only():
+    # half of the float4 column groups (rounded down) are stored; the rest rebuilt
+    assert [lsf.lsf_hybrid_columns(ldr) for ldr in (8, 12, 100, 256, 1020, 1024)] == \
+        [4, 8, 52, 128, 512, 512]
+    for bad in (4, 6, 1028):
+        with pytest.raises(B.LsfError) as e:
+            lsf.lsf_hybrid_columns(bad)
+        assert e.value.status == B.LSF_ERR_UNSUPPORTED

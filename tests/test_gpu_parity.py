@@ -194,10 +194,13 @@ def test_runs_are_bitwise_deterministic(lsf):
 
 # ---------------------------------------------------------------- large-workload shape
 
-def test_large_workload_shape_at_reduced_n(lsf):
-    """Unit cube vs N(0.5, 0.1^2 I) in R^3, eps 0.1, r 1024, 200 iterations, debiased."""
+@pytest.mark.parametrize("mode", ["stored", "recompute", "hybrid"])
+def test_large_workload_shape_at_reduced_n(lsf, mode):
+    """Unit cube vs N(0.5, 0.1^2 I) in R^3, eps 0.1, r 1024, 200 iterations, debiased,
+    in every scaling-domain variant (the recompute and hybrid passes are the
+    benchmark's configuration at reduced n)."""
     p = synth.large_problem(seed=0, n=1 << 13)
-    _, g = gpu_run(lsf, p)
+    _, g = gpu_run(lsf, p, mode=mode)
     ref = oracle_run(p, mode="scaled")
     check_w(g, ref)
 
