@@ -26,6 +26,7 @@ workloads: ``--workload tiny|diff|batched|serving|arccos|accel|multi`` print the
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -73,6 +74,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--batch-strategy", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--pairs", type=int, default=16, help="weight pairs of --workload multi (1..32)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and serving sub-objects of the default line")
+    ap.add_argument("--serve-count", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -298,16 +302,22 @@ def workload_config(args, mode=None):
 # ---------------------------------------------------------------- our arm
 
 def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(batched_measure(args, args.count)))
+    return 0
+
+
+def batched_measure(args, count):
     """Batched workload: independent problems of uneven shape, one persistent launch per
     feature width, CUDA-graph captured; against the same problems solved one after
-    another with the plain solver on the same stream."""
+    another with the plain solver on the same stream. Returns the JSON line."""
     import torch
     import paper_2006_07057_gb300 as lsf
-    torch.cuda.set_device(0)
     lsf.lsf_set_batch_strategy(args.batch_strategy)
     iters = 100
-    probs = synth.batched_problems(seed=0, count=args.count, iters=iters)
-    dev = torch.device("cuda", 0)
+    probs = synth.batched_problems(seed=0, count=count, iters=iters)
+    dev = torch.device("cuda", torch.cuda.current_device())
 
     class Dev:
         def __init__(self, p):
@@ -383,54 +393,82 @@ def run_batched(args):
                              "latency_ms_p50": pct(lat_plain, 0.5), "latency_ms_p99": pct(lat_plain, 0.99)},
         "speedup_vs_plain": ms_plain / ms_batched,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(serving_measure(args, args.count, args.rate)))
+    return 0
+
+
+def extra_legs(args) -> dict:
+    """The batched and served solves/s of the metric, measured in the default run
+    (with the GPU clocks sampled during each), as sub-objects of its JSON line."""
+    out = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    b = batched_measure(args, 512)
+    out["batched"] = {"solves_per_s": b["value"], "ms_per_batch": b["ms_per_step"],
+                      "config": b["config"]["workload"], **b["batched"],
+                      "plain_sequential": b["plain_sequential"],
+                      "speedup_vs_plain": b["speedup_vs_plain"], "clocks": sampler.stop()}
+    sampler = ClockSampler(0)
+    sampler.start()
+    v = serving_measure(args, args.serve_count, 2000.0)
+    out["serving"] = {"solves_per_s": v["value"], "config": v["config"]["workload"],
+                      "served": v["served"], "plain_sequential": v["plain_sequential"],
+                      "p99_ratio_plain_over_served": v["p99_ratio_plain_over_served"],
+                      "max_rel_diff_served_vs_alone": v["max_rel_diff_served_vs_alone"],
+                      "note": f"{args.serve_count} requests of the 10k-request stream's distribution "
+                              "(a reduced count keeps the default run within minutes)",
+                      "clocks": sampler.stop()}
+    return out
+
+
+def serving_measure(args, count, rate):
     """Serving workload: a Poisson stream of debiased-divergence requests of uneven
     shape served by the continuous-batching server (40 GB admission budget), against
-    the same stream served one request at a time."""
+    the same stream served one request at a time. Returns the JSON line."""
+    import dataclasses
     import torch
     import paper_2006_07057_gb300 as lsf
     from paper_2006_07057_gb300 import serve
-    torch.cuda.set_device(0)
     lsf.lib()
     iters = 100
-    count = args.count
-
-    def make():
-        out = []
-        for i, rq in enumerate(synth.serving_stream(seed=0, count=count, rate_per_s=args.rate,
-                                                    iters=iters)):
-            p = rq.problem
-            out.append(serve.Request(i, p.X, p.Y, p.a, p.b, p.Z, p.eps, iters, rq.arrival_s))
-        return out
-
-    warm = make()[: min(8, count)]
-    serve.Server(budget_bytes=40e9).serve(warm, realtime=False)
-    torch.cuda.synchronize()
+    base = []
+    for i, rq in enumerate(synth.serving_stream(seed=0, count=count, rate_per_s=rate, iters=iters)):
+        p = rq.problem
+        base.append(serve.Request(i, p.X, p.Y, p.a, p.b, p.Z, p.eps, iters, rq.arrival_s).pin())
+    fresh = lambda: [dataclasses.replace(r, result={}) for r in base]  # noqa: E731
     srv = serve.Server(budget_bytes=40e9, slots=args.slots)
-    mixed = srv.serve(make(), realtime=True)
+    srv.serve(fresh()[: min(16, count)], realtime=False)   # warm-up (kernels loaded, pool touched)
+    torch.cuda.synchronize()
+    mixed = srv.serve(fresh(), realtime=True)
     st_mixed = serve.latency_stats(mixed)
-    seq = serve.serve_sequential(make(), realtime=True)
+    seq = serve.serve_sequential(fresh(), realtime=True)
     st_seq = serve.latency_stats(seq)
     nonfinite = sum(1 for r in mixed if r.status & lsf.LSF_ERR_NONFINITE)
+    by_id = {r.rid: r for r in seq}
+    worst = max(abs(r.W_bar - by_id[r.rid].W_bar) /
+                max(abs(r.result["W_xy"]) + 0.5 * abs(r.result["W_xx"]) + 0.5 * abs(r.result["W_yy"]), 1e-30)
+                for r in mixed)
     line = {
         "metric": METRIC, "value": st_mixed["throughput_per_s"], "unit": "solves/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * st_mixed["span_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serving: Poisson stream of {count} debiased-divergence requests at "
-                               f"{args.rate:g}/s, n,m log-uniform [2^8, 2^18], d in {{2,3,16}}, "
+                               f"{rate:g}/s, n,m log-uniform [2^8, 2^18], d in {{2,3,16}}, "
                                f"r in {{128,512}}, eps in {{0.05,0.2,1.0}}, mixture clouds, uniform "
                                f"weights, {iters} iterations, 40 GB admission budget, {args.slots} slots"},
         "served": {**st_mixed, "peak_inflight": srv.peak_inflight, "peak_bytes": srv.peak_bytes,
-                   "nonfinite_requests": nonfinite},
+                   "nonfinite_requests": nonfinite, "relaunched_in_log_domain": srv.relaunched},
         "plain_sequential": st_seq,
         "p99_ratio_plain_over_served": st_seq["latency_ms_p99"] / st_mixed["latency_ms_p99"],
+        "max_rel_diff_served_vs_alone": worst,
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def _profile_roofline(lsf, cls, kernel, peak, peak_kind, ms_total):
@@ -970,22 +1008,24 @@ def main():
     runs = [measure(m) for m in modes]
     best = max(runs, key=lambda r: r["value"])
 
-    # ---- end to end from pinned host buffers through the public API (best variant)
+    # ---- end to end from pinned host buffers through one C-ABI call
+    # (lsf_pipeline_run: inputs copied in, the whole path, the result record copied
+    # out, all on the stream), best variant
     e2e = None
     if not args.no_e2e:
-        out_host = torch.empty(1, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host.values())
+        hp = lsf.HostPipeline(dev)
+        hargs = [host[k] for k in ("X", "Y", "a", "b", "Z")]
 
         def step_e2e():
             if best["mode"] in ("recompute", "hybrid"):
                 l2_flush.zero_()
-            d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
-            pr = lsf.SinkhornProblem(d["X"], d["Y"], d["a"], d["b"], d["Z"], p.eps, mode=best["mode"])
-            pr.run(args.iters, debiased=True)
-            out_host.copy_(pr.wbar, non_blocking=True)
-            return pr
+            hp.run(*hargs, p.eps, args.iters, debiased=True, mode=best["mode"])
 
         step_e2e()
+        chk = hp.result()
+        if chk["status"] != 0 or abs(chk["W"] - best["vals"]["W_bar"]) > 1e-5 * abs(best["vals"]["W_xy"]):
+            raise SystemExit(f"e2e path disagrees: {chk['W']} vs {best['vals']['W_bar']}")
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -996,7 +1036,9 @@ def main():
         barrier()
         ms_e2e = slowest(f0.elapsed_time(f1) / args.steps)
         e2e = {"value": whole_job_value(updates, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(ctypes.sizeof(lsf.LsfPipelineOut)),
+               "api": "lsf_pipeline_run (host inputs, host result record)",
+               "W_bar": hp.result()["W"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1022,6 +1064,8 @@ def main():
             "features_ms_per_step": best["features_ms_per_step"],
             "pipe_rates": rates,
         }
+        if world == 1 and not args.no_extra:
+            line.update(extra_legs(args))
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

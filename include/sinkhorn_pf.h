@@ -55,13 +55,29 @@ typedef enum {
                               F holds log features (lsf_log_features), the scalings
                               u, v hold log u~, log v~, t_u, t_v hold log t, and the
                               global factor M is 0                                    */
-  LSF_MODE_HYBRID = 3      /* the first c0 feature columns recomputed in registers (as
+  LSF_MODE_HYBRID = 3,     /* the first c0 feature columns recomputed in registers (as
                               RECOMPUTE), the other ldr - c0 streamed from a stored
                               block (as STORED), in the same pass, so HBM and the
                               FP32 pipe work at once. F holds the stored block
                               (lsf_hybrid_features, n x (ldr - c0)); X is needed too.
                               c0 = lsf_hybrid_columns(ldr). Scalings as STORED.       */
+  LSF_MODE_AUTO = 4        /* lsf_solve / lsf_debiased pick the domain: F and shift of
+                              both clouds are OUTPUT buffers here (F: n x ldr floats,
+                              16-byte aligned); the library builds the features
+                              itself from X and theta, with the within-row
+                              log-feature spread. Spread above LSF_AUTO_SPREAD nats:
+                              log features and LSF_MODE_LOG. Otherwise shifted
+                              features and LSF_MODE_STORED, and if that run reports
+                              LSF_ERR_NONFINITE, F is rebuilt as log features and the
+                              solve repeated in LSF_MODE_LOG. lsf_result.mode records
+                              the mode whose features, scalings and W are returned.
+                              Synchronises the stream (the spread and the status are
+                              read on the host).                                      */
 } lsf_mode;
+
+/* AUTO's spread threshold (nats): the shifted features of rows whose log-features
+   spread more than this underflow so far that a scaling-domain run is pointless. */
+#define LSF_AUTO_SPREAD 4000.0
 
 /* Feature parameters theta = (U, c), shared by every term of Eq. (2). Device pointers. */
 typedef struct {
@@ -102,11 +118,14 @@ typedef struct {
                         run is void and W, the scalings and the r-vectors are not
                         meaningful (repeat it with LSF_MODE_LOG).                    */
   int32_t iters;     /* iterations run                                                         */
+  int32_t mode;      /* the lsf_mode the scalings and W are in (LSF_MODE_LOG: logs); with
+                        LSF_MODE_AUTO the mode it picked                                     */
+  int32_t reserved;  /* zero                                                                  */
 } lsf_result;
 
 /* ---------------------------------------------------------------- library */
 
-/* ABI version of this header (increments on any incompatible change). */
+/* ABI version of this header (increments on any incompatible change): 2. */
 int lsf_version(void);
 
 /* Last error message of the calling host thread ("" if none). Never NULL. */
@@ -257,7 +276,8 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
  *   result[t].W = eps (sum_i a_i log u_i + sum_j b_j log v_j)   (FP64 compensated sum)
  *   *combined   = sum_t coef[t] * result[t].W    (combined may be NULL)
  * With coef = {1, -1/2, -1/2} over (xy, xx, yy) this is Eq. (2).
- * mode: the lsf_mode the scalings were produced in (LSF_MODE_LOG scalings are logs).
+ * mode: the lsf_mode the scalings were produced in (LSF_MODE_LOG scalings are logs);
+ * LSF_MODE_AUTO takes each term's mode from its result record (lsf_result.mode).
  */
 int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* xs,
                    const lsf_cloud* const* ys, const lsf_scalings* const* s,
@@ -303,6 +323,64 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
  */
 int lsf_solve_noalloc(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
                       int mode, const lsf_scalings* out, lsf_result* result, void* stream);
+
+/* ---------------------------------------------------------------- whole path */
+
+/*
+ * One divergence problem from host inputs to host results, for callers that
+ * hold their data in host memory (a request in a serving loop, an end-to-end
+ * measurement): Lemma 1 (R from both clouds, then q and sigma from the Lambert
+ * W0 of Sec. 3.2 evaluated on the device, anchors U = sigma Z and constants
+ * c_k), the features of the chosen mode, Alg. 1 (Sec. 2) on K = xi zeta^T
+ * (Sec. 3.1) for each term, Eq. (6) and, when debiased, Eq. (2) with one shared
+ * theta. Every device buffer lives in one caller-owned arena.
+ */
+typedef struct {
+  int64_t n, m;    /* points of X and Y, >= 1                                       */
+  int d;           /* dimension, >= 1                                               */
+  int r;           /* features (anchors), >= 1                                      */
+  int ldr;         /* feature row stride (0: r rounded up to a multiple of 4)       */
+  double eps;      /* entropic regularisation, > 0                                  */
+  int iters;       /* Alg. 1 iterations per solve, >= 1                             */
+  int debiased;    /* 1: Eq. (2) (three solves); 0: Eq. (6) of W(a, b) alone        */
+  int mode;        /* LSF_MODE_STORED, _RECOMPUTE, _HYBRID, _LOG or _AUTO          */
+} lsf_pipeline;
+
+/* Host results of lsf_pipeline_run. */
+typedef struct {
+  double W;                 /* Eq. (2) when debiased, else Eq. (6) of W(a, b)       */
+  double W_xy, W_xx, W_yy;  /* Eq. (6) per term (W_xx, W_yy zero when not debiased) */
+  double residual_xy, residual_xx, residual_yy;  /* ||u o (K v) - a||_1 per term    */
+  double R, q, sigma;       /* the Lemma 1 parameters used                          */
+  int32_t status;           /* OR of the device status bits of every solve          */
+  int32_t mode;             /* the lsf_mode that produced the result                */
+  int32_t iters;            /* iterations run                                       */
+  int32_t reserved;
+} lsf_pipeline_out;
+
+/* Arena bytes lsf_pipeline_run needs for a problem description. Host only.
+ * Errors: LSF_ERR_ARG / LSF_ERR_UNSUPPORTED for an invalid description. */
+int lsf_pipeline_bytes(const lsf_pipeline* p, size_t* bytes);
+
+/*
+ * Run the whole path. X (n x d), Y (m x d), a (n), b (m): host points and
+ * weights (a, b positive, each summing to 1); Z (r x d): host standard normal
+ * draws of the anchors. arena: device, 256-byte aligned, >= lsf_pipeline_bytes;
+ * it holds copies of the inputs, theta, features, scalings, results and the
+ * solver workspace, and no two calls that can overlap on the GPU may share it.
+ * out: host record, written by a copy at the end of the call's work on the
+ * stream.
+ * Nothing is allocated. Except in LSF_MODE_AUTO, the call never waits on the
+ * device: the host-to-device copies of the inputs, every kernel and the copy of
+ * *out are queued on the stream, and *out is valid once the stream has
+ * reached it (cudaStreamSynchronize, or an event recorded after the call). Host
+ * inputs in pinned memory must stay unchanged until then; pageable ones are
+ * staged by the copy. LSF_MODE_AUTO synchronises the stream inside (see
+ * lsf_mode). Errors: those of the steps, with device status bits in out->status.
+ */
+int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, const float* a,
+                     const float* b, const float* Z, void* arena, size_t arena_bytes,
+                     lsf_pipeline_out* out, void* stream);
 
 /* ---------------------------------------------------------------- batched */
 
@@ -580,6 +658,23 @@ int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes);
 int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
                     const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* out,
                     lsf_result* results, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Eq. (2) for each of the k weight pairs (a_p, b_p) on the same two clouds and
+ * features: W_bar_p = W(a_p, b_p) - (W(a_p, a_p) + W(b_p, b_p)) / 2 with one
+ * shared theta. Three lsf_solve_multi calls (on (x, y), (x, x) and (y, y), with
+ * the scalings s_xy, s_xx, s_yy) and a device combination: results is a device
+ * array of 3k records, [0, k) for the (x, y) terms, [k, 2k) for (x, x) and
+ * [2k, 3k) for (y, y), each with W, residual, log_scale, iters; the three
+ * records of a pair carry the OR of their status bits. wbar: device array of k
+ * doubles receiving W_bar_p (may be NULL). Other arguments, shapes and errors as
+ * lsf_solve_multi; one workspace serves the three solves in turn.
+ */
+int lsf_multi_debiased(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
+                       const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* s_xy,
+                       const lsf_multi_scalings* s_xx, const lsf_multi_scalings* s_yy,
+                       lsf_result* results, double* wbar, void* workspace, size_t ws_bytes,
+                       void* stream);
 
 /*
  * Tuning of lsf_solve_multi (process-wide, not thread-safe against concurrent

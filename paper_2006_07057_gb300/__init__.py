@@ -29,22 +29,23 @@ from ._binding import (LSF_ERR_ARG, LSF_ERR_UNSUPPORTED, LSF_ERR_WORKSPACE,  # n
                        LsfAccelInfo, LsfBatchInfo, LsfBatchProblem, LsfMultiCloud,
                        LsfMultiScalings, LSF_KERNEL_PASS_MULTI,
                        LSF_KERNEL_PASS_RECOMPUTE, LSF_KERNEL_PASS_HYBRID, LSF_MODE_HYBRID,
+                       LSF_MODE_AUTO, LSF_AUTO_SPREAD,
                        LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
-                       LsfArccos, LsfTheta, check, header_symbols, lib)
+                       LsfArccos, LsfTheta, LsfPipeline, LsfPipelineOut, check, header_symbols,
+                       lib)
 
 MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG,
-         "hybrid": LSF_MODE_HYBRID}
+         "hybrid": LSF_MODE_HYBRID, "auto": LSF_MODE_AUTO}
+MODE_NAMES = {v: k for k, v in MODES.items()}
 
-# "auto" routes a problem straight to the log domain when the within-row
-# log-feature spread exceeds this many nats. Shifted features only underflow
-# harmlessly below that (most problems with spreads of several hundred nats still
-# solve in FP32 scaling form); the decisive check is the device status: a run
-# that reports a non-finite scaling is repeated in the log domain.
-LOG_SPREAD = 4000.0
+# The library's "auto" threshold: a problem goes straight to the log domain when
+# the within-row log-feature spread exceeds this many nats (the batched solver's
+# routing uses the same value).
+LOG_SPREAD = LSF_AUTO_SPREAD
 
 RESULT_DTYPE = np.dtype([("W", "<f8"), ("residual", "<f8"), ("log_scale", "<f8"),
-                         ("status", "<i4"), ("iters", "<i4")])
+                         ("status", "<i4"), ("iters", "<i4"), ("mode", "<i4"), ("reserved", "<i4")])
 assert RESULT_DTYPE.itemsize == RESULT_BYTES
 
 
@@ -339,6 +340,74 @@ def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, o
                                   _stream(stream)), "lsf_solve_noalloc")
 
 
+def pipeline_desc(n: int, m: int, d: int, r: int, eps: float, iters: int, debiased: bool = True,
+                  mode: str = "stored", ldr: int = 0) -> LsfPipeline:
+    return LsfPipeline(int(n), int(m), int(d), int(r), int(ldr), float(eps), int(iters),
+                       int(bool(debiased)), MODES[mode])
+
+
+def lsf_pipeline_bytes(desc: LsfPipeline) -> int:
+    b = ctypes.c_size_t()
+    check(lib().lsf_pipeline_bytes(ctypes.byref(desc), ctypes.byref(b)), "lsf_pipeline_bytes")
+    return b.value
+
+
+def lsf_pipeline_run(desc: LsfPipeline, X, Y, a, b, Z, arena, out_ptr: int, stream=None) -> None:
+    """Queue the whole path for host arrays X, Y, a, b, Z (contiguous float32 CPU
+    tensors, pinned for an asynchronous call) into the device arena; the host
+    record lands at out_ptr (sizeof(LsfPipelineOut) bytes, pinned) when the
+    stream reaches the end of the call."""
+    for t in (X, Y, a, b, Z):
+        if t.dtype != torch.float32 or t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected contiguous float32 host tensors")
+    check(lib().lsf_pipeline_run(ctypes.byref(desc), _p(X), _p(Y), _p(a), _p(b), _p(Z), _p(arena),
+                                 arena.numel(), ctypes.cast(ctypes.c_void_p(out_ptr),
+                                                            ctypes.POINTER(LsfPipelineOut)),
+                                 _stream(stream)), "lsf_pipeline_run")
+
+
+def alloc_arena(nbytes: int, device) -> torch.Tensor:
+    """A 256-byte aligned device byte buffer of nbytes."""
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + nbytes]
+
+
+class HostPipeline:
+    """The whole path for problems held in host memory, through lsf_pipeline_run.
+
+    Owns one device arena (grown when a larger problem comes) and a pinned host
+    record; ``run`` queues a problem on the stream (no host wait, except in
+    ``auto`` mode) and ``result`` waits for it and returns the host values.
+    """
+
+    def __init__(self, device=None, stream=None):
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream
+        self.arena = None
+        self._out = torch.zeros(ctypes.sizeof(LsfPipelineOut), dtype=torch.uint8).pin_memory()
+        self.event = torch.cuda.Event()
+
+    def run(self, X, Y, a, b, Z, eps: float, iters: int, debiased: bool = True,
+            mode: str = "stored") -> None:
+        n, d = X.shape
+        desc = pipeline_desc(n, Y.shape[0], d, Z.shape[0], eps, iters, debiased, mode)
+        need = lsf_pipeline_bytes(desc)
+        if self.arena is None or self.arena.numel() < need:
+            self.arena = alloc_arena(need, self.device)
+        lsf_pipeline_run(desc, X, Y, a, b, Z, self.arena, self._out.data_ptr(), self.stream)
+        self.event.record(self.stream if self.stream is not None else torch.cuda.current_stream())
+
+    def done(self) -> bool:
+        return self.event.query()
+
+    def result(self) -> dict:
+        self.event.synchronize()
+        o = LsfPipelineOut.from_address(self._out.data_ptr())
+        return {k: getattr(o, k) for k, _ in LsfPipelineOut._fields_ if k != "reserved"} | {
+            "mode_name": MODE_NAMES.get(o.mode, "?")}
+
+
 def ldr2_for(r: int) -> int:
     """Row stride of the bf16 pair features of the tensor-core pass: r rounded up to 128."""
     return (r + 127) // 128 * 128
@@ -389,6 +458,23 @@ def lsf_solve_multi(theta: Theta, ldr2: int, F2x, shift_x, Wx, F2y, shift_y, Wy,
     check(lib().lsf_solve_multi(ctypes.byref(th), int(ldr2), ctypes.byref(cx), ctypes.byref(cy), k,
                                 int(iters), ctypes.byref(so), _p(results), _p(workspace),
                                 workspace.numel(), _stream(stream)), "lsf_solve_multi")
+
+
+def lsf_multi_debiased(theta: Theta, ldr2: int, F2x, shift_x, Wx, F2y, shift_y, Wy, iters: int,
+                       s_xy: dict, s_xx: dict, s_yy: dict, results, wbar, workspace,
+                       stream=None) -> None:
+    """Eq. (2) for the k weight pairs: three multi-pair solves and the per-pair
+    combination on the device (results: 3k records xy, xx, yy; wbar: k doubles)."""
+    k = int(Wx.shape[0])
+    th = theta.as_c()
+    cx = LsfMultiCloud(_p(F2x), _p(shift_x), _p(Wx), int(Wx.shape[1]))
+    cy = LsfMultiCloud(_p(F2y), _p(shift_y), _p(Wy), int(Wy.shape[1]))
+    sc = [LsfMultiScalings(_p(s["U"]), _p(s["V"]), _p(s["Tu"]), _p(s["Tv"]))
+          for s in (s_xy, s_xx, s_yy)]
+    check(lib().lsf_multi_debiased(ctypes.byref(th), int(ldr2), ctypes.byref(cx), ctypes.byref(cy),
+                                   k, int(iters), ctypes.byref(sc[0]), ctypes.byref(sc[1]),
+                                   ctypes.byref(sc[2]), _p(results), _p(wbar), _p(workspace),
+                                   workspace.numel(), _stream(stream)), "lsf_multi_debiased")
 
 
 def lsf_debiased(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, s_xy: Scalings,
@@ -524,16 +610,18 @@ class SinkhornProblem:
     Eq. (2), result records and the workspace. ``run`` launches the solve
     asynchronously; ``values`` reads the scalars back.
 
-    ``mode="auto"`` starts in the scaling domain and moves to the log domain
-    when the within-row log-feature spread exceeds ``LOG_SPREAD`` or when a run
-    reports a non-finite scaling (the run is then repeated in the log domain).
+    ``mode="auto"`` hands the choice of domain to the library (LSF_MODE_AUTO):
+    at ``run`` it builds the features itself, goes to the log domain when the
+    within-row log-feature spread exceeds ``LOG_SPREAD``, else solves in the
+    scaling domain and repeats the solve in the log domain if that run reports a
+    non-finite scaling. ``used_mode`` then tells which domain produced the result.
     """
 
     def __init__(self, X, Y, a, b, Z, eps: float, mode: str = "stored", ldr: int | None = None,
                  theta: Theta | None = None, stream=None, scalings: bool = True,
                  kernel: str = "gaussian", s: int = 1, sigma: float = 1.5, kappa: float = 0.1):
-        if mode not in MODES and mode != "auto":
-            raise ValueError(f"mode must be one of {sorted(MODES) + ['auto']}")
+        if mode not in MODES:
+            raise ValueError(f"mode must be one of {sorted(MODES)}")
         if kernel not in ("gaussian", "arccos"):
             raise ValueError("kernel must be 'gaussian' or 'arccos'")
         if kernel == "arccos" and mode in ("recompute", "hybrid"):
@@ -566,10 +654,10 @@ class SinkhornProblem:
         self.theta = theta
         ldr = theta.ldr
         self.spread = torch.zeros(1, dtype=torch.float32, device=dev)
-        self.mode = "stored" if self.auto else mode
+        if self.auto and kernel == "arccos":
+            raise ValueError("auto mode builds Gaussian features; pick a mode for arc-cosine")
+        self.mode = mode
         self._build_features()
-        if self.auto and float(self.spread.item()) > LOG_SPREAD:
-            self.switch_mode("log")
         self.debiased = None
         self.iters = None
         if not scalings:
@@ -583,6 +671,12 @@ class SinkhornProblem:
 
     def _build_features(self):
         X, Y, th, st = self.X, self.Y, self.theta, self.stream
+        if self.mode == "auto":
+            # the library builds the features of the domain it picks into these
+            e = lambda *s_: torch.empty(s_, dtype=torch.float32, device=X.device)  # noqa: E731
+            self.x = Cloud(X, e(X.shape[0], th.ldr), e(X.shape[0]), self.a)
+            self.y = Cloud(Y, e(Y.shape[0], th.ldr), e(Y.shape[0]), self.b)
+            return
         if self.arccos is not None:
             build = lsf_arccos_features if self.mode == "stored" else lsf_arccos_log_features
             Fx, sx = build(X, self.arccos, spread=self.spread, stream=st)
@@ -618,16 +712,23 @@ class SinkhornProblem:
     def run(self, iters: int, debiased: bool = True) -> None:
         """Launch the solve (and Eq. (6)/(2) reductions) on the stream.
 
-        No host synchronisation, except in ``auto`` mode, which reads the status
-        back to decide whether to repeat the run in the log domain.
+        No host synchronisation, except in ``auto`` mode, where the library reads
+        the spread and the status back to pick the domain (``used_mode``).
         """
         self.debiased = bool(debiased)
         self.iters = iters
+        self._used = None
         self._launch(iters)
-        if self.auto and self.mode != "log":
-            if read_results(self.results)[0]["status"] & LSF_ERR_NONFINITE:
-                self.switch_mode("log")
-                self._launch(iters)
+
+    @property
+    def used_mode(self) -> str:
+        """The mode the last run's features, scalings and W are in (reads the
+        result record once in ``auto`` mode)."""
+        if not self.auto:
+            return self.mode
+        if getattr(self, "_used", None) is None:
+            self._used = MODE_NAMES[read_results(self.result_view(0))[0]["mode"]]
+        return self._used
 
     def _launch(self, iters: int) -> None:
         if self.debiased:
@@ -672,7 +773,7 @@ class SinkhornProblem:
         """Host copy of the results of the last run (synchronises)."""
         recs = read_results(self.results)
         out = {"W_xy": recs[0]["W"], "res_xy": recs[0]["residual"], "status": recs[0]["status"],
-               "iters": recs[0]["iters"], "records": recs, "mode": self.mode}
+               "iters": recs[0]["iters"], "records": recs, "mode": MODE_NAMES[recs[0]["mode"]]}
         out["W"] = float(self.wbar.item())
         if self.debiased:
             out.update(W_xx=recs[1]["W"], W_yy=recs[2]["W"], res_xx=recs[1]["residual"],
@@ -685,9 +786,11 @@ class SinkhornProblem:
         s = {"xy": self.s_xy, "xx": self.s_xx, "yy": self.s_yy}[which]
         xs = self.x.shift if which in ("xy", "xx") else self.y.shift
         ys = self.y.shift if which in ("xy", "yy") else self.x.shift
-        M = read_results(self.results)[k]["log_scale"]
-        lu = s.u.double() if self.mode == "log" else torch.log(s.u.double())
-        lv = s.v.double() if self.mode == "log" else torch.log(s.v.double())
+        rec = read_results(self.results)[k]
+        M = rec["log_scale"]
+        lg = rec["mode"] == LSF_MODE_LOG
+        lu = s.u.double() if lg else torch.log(s.u.double())
+        lv = s.v.double() if lg else torch.log(s.v.double())
         return lu - xs.double() - M, lv - ys.double() + M
 
     def gradient(self, debiased: bool | None = None):
@@ -695,7 +798,7 @@ class SinkhornProblem:
         deb = self.debiased if debiased is None else bool(debiased)
         if deb and not self.debiased:
             raise ValueError("the debiased gradient needs a debiased run")
-        if self.mode in ("recompute", "hybrid"):
+        if self.used_mode in ("recompute", "hybrid"):
             raise NotImplementedError("the adjoint reads the full stored features")
         if self.arccos is not None:
             raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
@@ -706,7 +809,7 @@ class SinkhornProblem:
         gb = torch.empty(self.y.n, dtype=torch.float32, device=dev)
         lsf_gradient(self.theta, self.x, self.y, self.s_xy, self.s_xx if deb else None,
                      self.s_yy if deb else None, self.results, deb, gX, gY, ga, gb,
-                     self.stream, mode=self.mode)
+                     self.stream, mode=self.used_mode)
         return gX, gY, ga, gb
 
 
@@ -719,7 +822,7 @@ class SinkhornProblem:
         deb = self.debiased if debiased is None else bool(debiased)
         if deb and not self.debiased:
             raise ValueError("the debiased gradient needs a debiased run")
-        if self.mode in ("recompute", "hybrid"):
+        if self.used_mode in ("recompute", "hybrid"):
             raise NotImplementedError("the adjoint reads the full stored features")
         if self.arccos is not None:
             raise NotImplementedError("the adjoint kernels differentiate the Gaussian map")
@@ -730,7 +833,7 @@ class SinkhornProblem:
         lsf_anchor_gradient(th, self.x, self.y, self.s_xy, self.s_xx if deb else None,
                             self.s_yy if deb else None, deb, gU, self.workspace,
                             scale=th.sigma if wrt == "Z" else 1.0, stream=self.stream,
-                            mode=self.mode)
+                            mode=self.used_mode)
         return gU
 
 
@@ -975,33 +1078,43 @@ class MultiSinkhornProblem:
         return x, y
 
     def run(self, iters: int, debiased: bool = False) -> None:
-        """Launch the k solves of each term and their Eq. (6) reductions on the
-        stream (asynchronous)."""
+        """Launch the k solves (of each term of Eq. (2) when debiased) and their
+        reductions on the stream (asynchronous); Eq. (2) is formed on the device."""
         self.debiased = bool(debiased)
-        terms = ("xy", "xx", "yy") if self.debiased else ("xy",)
         dev = self.A.device
-        for t in terms:
+        if not self.debiased:
+            x, y = self._term("xy")
+            s = self.s["xy"]
+            lsf_solve_multi(self.theta, self.ldr2, x[0], x[1], x[2], y[0], y[1], y[2], iters,
+                            s["U"], s["V"], s["Tu"], s["Tv"], self.res["xy"], self.workspace,
+                            self.stream)
+            return
+        for t in ("xx", "yy"):
             if t not in self.s:
                 x, y = self._term(t)
                 self.s[t] = self._scal(x[2].shape[1], y[2].shape[1])
-                self.res[t] = alloc_results(self.k, dev)
-            x, y = self._term(t)
-            s = self.s[t]
-            lsf_solve_multi(self.theta, self.ldr2, x[0], x[1], x[2], y[0], y[1], y[2], iters,
-                            s["U"], s["V"], s["Tu"], s["Tv"], self.res[t], self.workspace,
-                            self.stream)
+        if getattr(self, "res3", None) is None:
+            self.res3 = alloc_results(3 * self.k, dev)
+            self.wbar = torch.zeros(self.k, dtype=torch.float64, device=dev)
+        lsf_multi_debiased(self.theta, self.ldr2, self.F2x, self.shift_x, self.A, self.F2y,
+                           self.shift_y, self.B, iters, self.s["xy"], self.s["xx"], self.s["yy"],
+                           self.res3, self.wbar, self.workspace, self.stream)
 
     def values(self) -> list[dict]:
         """Per pair: W (Eq. (6)), residual, status, iters, and with ``debiased``
-        W_xx, W_yy and W_bar (Eq. (2)) (synchronises)."""
-        xy = read_results(self.res["xy"])
-        out = [{"W": r["W"], "residual": r["residual"], "status": r["status"], "iters": r["iters"],
-                "log_scale": r["log_scale"]} for r in xy]
-        if self.debiased:
-            xx = read_results(self.res["xx"])
-            yy = read_results(self.res["yy"])
-            for o_, a_, b_ in zip(out, xx, yy):
-                o_.update(W_xx=a_["W"], W_yy=b_["W"], res_xx=a_["residual"], res_yy=b_["residual"],
-                          W_bar=o_["W"] - 0.5 * (a_["W"] + b_["W"]),
-                          status=o_["status"] | a_["status"] | b_["status"])
+        W_xx, W_yy and W_bar (Eq. (2), formed on the device) (synchronises)."""
+        if not self.debiased:
+            xy = read_results(self.res["xy"])
+            return [{"W": r["W"], "residual": r["residual"], "status": r["status"],
+                     "iters": r["iters"], "log_scale": r["log_scale"]} for r in xy]
+        recs = read_results(self.res3)
+        k = self.k
+        wbar = self.wbar.cpu().tolist()
+        out = []
+        for p in range(k):
+            a_, b_, c_ = recs[p], recs[k + p], recs[2 * k + p]
+            out.append({"W": a_["W"], "residual": a_["residual"], "status": a_["status"],
+                        "iters": a_["iters"], "log_scale": a_["log_scale"], "W_xx": b_["W"],
+                        "W_yy": c_["W"], "res_xx": b_["residual"], "res_yy": c_["residual"],
+                        "W_bar": wbar[p]})
         return out

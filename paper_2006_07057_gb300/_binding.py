@@ -31,6 +31,8 @@ LSF_MODE_STORED = 0
 LSF_MODE_RECOMPUTE = 1
 LSF_MODE_LOG = 2
 LSF_MODE_HYBRID = 3
+LSF_MODE_AUTO = 4
+LSF_AUTO_SPREAD = 4000.0
 
 LSF_KERNEL_PASS = 0
 LSF_KERNEL_PASS_RECOMPUTE = 1
@@ -65,10 +67,23 @@ class LsfScalings(ctypes.Structure):
 
 class LsfResult(ctypes.Structure):
     _fields_ = [("W", c_double), ("residual", c_double), ("log_scale", c_double),
-                ("status", ctypes.c_int32), ("iters", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 RESULT_BYTES = ctypes.sizeof(LsfResult)
+
+
+class LsfPipeline(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("m", c_int64), ("d", c_int), ("r", c_int), ("ldr", c_int),
+                ("eps", c_double), ("iters", c_int), ("debiased", c_int), ("mode", c_int)]
+
+
+class LsfPipelineOut(ctypes.Structure):
+    _fields_ = [("W", c_double), ("W_xy", c_double), ("W_xx", c_double), ("W_yy", c_double),
+                ("residual_xy", c_double), ("residual_xx", c_double), ("residual_yy", c_double),
+                ("R", c_double), ("q", c_double), ("sigma", c_double), ("status", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class LsfBatchProblem(ctypes.Structure):
@@ -119,6 +134,9 @@ _SIGNATURES = {
     "lsf_hybrid_features": (c_int, [c_void_p, c_int64, _P(LsfTheta), c_void_p, c_void_p, c_void_p,
                                     c_void_p]),
     "lsf_workspace_bytes": (c_int, [c_int, _P(c_size_t)]),
+    "lsf_pipeline_bytes": (c_int, [_P(LsfPipeline), _P(c_size_t)]),
+    "lsf_pipeline_run": (c_int, [_P(LsfPipeline), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_size_t, _P(LsfPipelineOut), c_void_p]),
     "lsf_accel_workspace_bytes": (c_int, [c_int64, c_int64, c_int, _P(c_size_t)]),
     "lsf_solve_accelerated": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double,
                                       _P(LsfScalings), c_void_p, _P(LsfAccelInfo), c_void_p,
@@ -129,6 +147,10 @@ _SIGNATURES = {
     "lsf_solve_multi": (c_int, [_P(LsfTheta), c_int, _P(LsfMultiCloud), _P(LsfMultiCloud), c_int,
                                 c_int, _P(LsfMultiScalings), c_void_p, c_void_p, c_size_t,
                                 c_void_p]),
+    "lsf_multi_debiased": (c_int, [_P(LsfTheta), c_int, _P(LsfMultiCloud), _P(LsfMultiCloud), c_int,
+                                   c_int, _P(LsfMultiScalings), _P(LsfMultiScalings),
+                                   _P(LsfMultiScalings), c_void_p, c_void_p, c_void_p, c_size_t,
+                                   c_void_p]),
     "lsf_solve": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                           _P(LsfScalings), c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_divergence": (c_int, [_P(LsfTheta), c_int, _P(_P(LsfCloud)), _P(_P(LsfCloud)),

@@ -209,6 +209,7 @@ __global__ void accel_decide_kernel(const double* part, int nparts, double L, Ac
   if (final_iters > 0) {
     result->residual = S[2] + S[3];
     result->iters = final_iters;
+    result->mode = LSF_MODE_LOG;
   }
 }
 

@@ -455,6 +455,8 @@ __global__ void __launch_bounds__(256) batched_start_kernel(BProb* probs, unsign
     pb.result->log_scale = static_cast<double>(M);
     pb.result->status = 0;
     pb.result->iters = iters;
+    pb.result->mode = log_domain ? LSF_MODE_LOG : LSF_MODE_STORED;
+    pb.result->reserved = 0;
     counter[blockIdx.x] = 0u;
     flag[blockIdx.x] = 0u;
   }

@@ -52,6 +52,12 @@ struct Workspace {
 size_t workspace_bytes(int ldr);
 int carve_workspace(void* base, size_t bytes, int ldr, Workspace* ws);
 
+// Lemma 1 on the device (no host round trip): q, sigma from the device radius R
+// into qs = {q, sigma}; and anchors U = sigma Z with their log-constants from qs.
+int launch_params_device(const float* R, double eps, int d, double* qs, cudaStream_t st);
+int launch_anchors_device(const float* Z, int r, int d, const double* qs, double eps, float* U,
+                          float* c, cudaStream_t st);
+
 // Most CTAs any pass may launch: the workspace holds one partial r-vector slot per
 // CTA, so every pass launcher clamps its grid to this.
 int max_pass_ctas();

@@ -32,10 +32,46 @@ __global__ void radius_finish_kernel(const unsigned* __restrict__ key, float* __
   if (threadIdx.x == 0) R[0] = sqrtf(__uint_as_float(key[0]));
 }
 
+// Principal Lambert branch W0(z), z >= 0, in FP64 on the device: Newton's
+// iteration on w e^w - z from log(1 + z), as on the host (the iterates decrease
+// monotonically to the root).
+__device__ double lambert_w0_device(double z) {
+  if (z == 0.0) return 0.0;
+  double w = log1p(z);
+  for (int i = 0; i < 200; ++i) {
+    const double ew = exp(w);
+    const double next = w - (w * ew - z) / (ew * (w + 1.0));
+    if (fabs(next - w) <= 1e-16 * fabs(next)) return next;
+    w = next;
+  }
+  return w;
+}
+
+// Lemma 1 parameters from the device radius: q = z / (2 W0(z)) with
+// z = R^2 / (eps d) (q = 1/2 at R = 0), sigma = sqrt(q eps / 4); qs = {q, sigma}.
+// A non-finite R gives NaN parameters (and, downstream, a non-finite status).
+__global__ void params_kernel(const float* __restrict__ R, double eps, int d, double* __restrict__ qs) {
+  if (threadIdx.x != 0) return;
+  const double Rd = static_cast<double>(R[0]);
+  const double z = Rd * Rd / (eps * d);
+  double q = 0.5;
+  if (!isfinite(z)) q = NAN;
+  else if (z > 0.0) q = z / (2.0 * lambert_w0_device(z));
+  qs[0] = q;
+  qs[1] = sqrt(q * eps / 4.0);
+}
+
+// Anchors u_k = sigma z_k and log-constants c_k; q and sigma come from the host
+// arguments, or from the device pair qs = {q, sigma} when qs is not NULL.
 __global__ void anchors_kernel(const float* __restrict__ Z, int r, int d, double q, double sigma,
-                               double eps, float* __restrict__ U, float* __restrict__ c) {
+                               const double* __restrict__ qs, double eps, float* __restrict__ U,
+                               float* __restrict__ c) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= r) return;
+  if (qs) {
+    q = qs[0];
+    sigma = qs[1];
+  }
   double nrm = 0.0;
   for (int j = 0; j < d; ++j) {
     const float u = static_cast<float>(sigma * static_cast<double>(Z[static_cast<int64_t>(k) * d + j]));
@@ -451,6 +487,20 @@ __global__ void arccos_anchors_kernel(const float* __restrict__ Z, int r, int d,
 }
 
 }  // namespace
+
+int launch_params_device(const float* R, double eps, int d, double* qs, cudaStream_t st) {
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 20.0);
+  params_kernel<<<1, 32, 0, st>>>(R, eps, d, qs);
+  return check_launch("params_kernel");
+}
+
+int launch_anchors_device(const float* Z, int r, int d, const double* qs, double eps, float* U,
+                          float* c, cudaStream_t st) {
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * r * d + 4.0 * r);
+  anchors_kernel<<<(r + 127) / 128, 128, 0, st>>>(Z, r, d, 0.0, 0.0, qs, eps, U, c);
+  return check_launch("anchors_kernel");
+}
+
 }  // namespace lsf
 
 using namespace lsf;
@@ -484,7 +534,7 @@ int lsf_anchors(const float* Z, int r, int d, double q, double sigma, double eps
     return fail(LSF_ERR_ARG, "lsf_anchors: need q > 0, sigma >= 0, eps > 0");
   cudaStream_t st = as_stream(stream);
   LaunchScope ls(st, LSF_KERNEL_OTHER, 8.0 * r * d + 4.0 * r);
-  anchors_kernel<<<(r + 127) / 128, 128, 0, st>>>(Z, r, d, q, sigma, eps, U, c);
+  anchors_kernel<<<(r + 127) / 128, 128, 0, st>>>(Z, r, d, q, sigma, nullptr, eps, U, c);
   return check_launch("anchors_kernel");
 }
 

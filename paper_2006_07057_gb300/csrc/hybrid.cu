@@ -256,12 +256,11 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
       // data beyond them)
       const int nval = static_cast<int>(min(static_cast<int64_t>(kHyRB),
                                             max(static_cast<int64_t>(0), a.n - (b * RPB + g * kHyRB))));
-      if (!mbar_wait_bounded(&s_full[slot], static_cast<uint32_t>(it / kHySlots) & 1u))
-        flag |= LSF_ERR_TIMEOUT;
       const float4* srow = reinterpret_cast<const float4*>(s_ring + (static_cast<size_t>(slot) * RPB + g * kHyRB) * lds) + tg;
       const int ldq = lds >> 2;  // float4s per stored row
+      // the recomputed entries first: they need only the row records, so the
+      // stored rows' copy lands meanwhile
       float2 F[kHyRB][2];
-      float dots[NRHS][kHyRB];
 #pragma unroll
       for (int q = 0; q < kHyRB; ++q) {
         const float4* rw = rows + (g * kHyRB + q) * SV;
@@ -279,6 +278,12 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
           for (int dd = 0; dd < D; ++dd) E = __ffma2_rn(xb[dd], W2[p][dd], E);
           F[q][p] = make_float2(ex2_approx(E.x), ex2_approx(E.y));
         }
+      }
+      if (!mbar_wait_bounded(&s_full[slot], static_cast<uint32_t>(it / kHySlots) & 1u))
+        flag |= LSF_ERR_TIMEOUT;
+      float dots[NRHS][kHyRB];
+#pragma unroll
+      for (int q = 0; q < kHyRB; ++q) {
         const float4 fs = (has_st && q < nval) ? srow[q * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 fs0 = make_float2(fs.x, fs.y), fs1 = make_float2(fs.z, fs.w);
 #pragma unroll

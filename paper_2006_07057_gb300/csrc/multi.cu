@@ -790,8 +790,26 @@ __global__ void multi_init_kernel(const float* __restrict__ shift, int64_t n, in
   if (blockIdx.x == 0 && threadIdx.x < k) res[threadIdx.x].log_scale = static_cast<double>(M);
 }
 
+// Eq. (2) per weight pair from the three terms' Eq. (6) values:
+// wbar[p] = W(a_p, b_p) - (W(a_p, a_p) + W(b_p, b_p)) / 2. The three records of a
+// pair report their status bits jointly, as the single-pair debiased solve does.
+__global__ void multi_debias_kernel(lsf_result* rxy, lsf_result* rxx, lsf_result* ryy, int k,
+                                    double* wbar) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= k) return;
+  if (wbar) wbar[p] = rxy[p].W - 0.5 * (rxx[p].W + ryy[p].W);
+  const int32_t s = rxy[p].status | rxx[p].status | ryy[p].status;
+  rxy[p].status = s;
+  rxx[p].status = s;
+  ryy[p].status = s;
+}
+
 __global__ void multi_iters_kernel(lsf_result* res, int k, int iters) {
-  if (static_cast<int>(threadIdx.x) < k) res[threadIdx.x].iters = iters;
+  if (static_cast<int>(threadIdx.x) < k) {
+    res[threadIdx.x].iters = iters;
+    res[threadIdx.x].mode = LSF_MODE_STORED;
+    res[threadIdx.x].reserved = 0;
+  }
 }
 
 // bf16 pair planes from stored FP32 features (zero beyond r).
@@ -1102,6 +1120,22 @@ int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
     LSF_TRY(launch_divergence(theta, nt, xs, ys, sp, rs, nullptr, nullptr, mw.ws, st, 0));
   }
   return LSF_OK;
+}
+
+int lsf_multi_debiased(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
+                       const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* s_xy,
+                       const lsf_multi_scalings* s_xx, const lsf_multi_scalings* s_yy,
+                       lsf_result* results, double* wbar, void* workspace, size_t ws_bytes,
+                       void* stream) {
+  if (!x || !y || !results) return fail(LSF_ERR_ARG, "lsf_multi_debiased: NULL argument");
+  if (k < 1 || k > 32) return fail(LSF_ERR_UNSUPPORTED, "lsf_multi_debiased: k must be 1..32");
+  LSF_TRY(lsf_solve_multi(theta, ldr2, x, y, k, iters, s_xy, results, workspace, ws_bytes, stream));
+  LSF_TRY(lsf_solve_multi(theta, ldr2, x, x, k, iters, s_xx, results + k, workspace, ws_bytes, stream));
+  LSF_TRY(lsf_solve_multi(theta, ldr2, y, y, k, iters, s_yy, results + 2 * k, workspace, ws_bytes, stream));
+  cudaStream_t st = as_stream(stream);
+  LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+  multi_debias_kernel<<<1, 32, 0, st>>>(results, results + k, results + 2 * k, k, wbar);
+  return check_launch("multi_debias_kernel");
 }
 
 }  // extern "C"

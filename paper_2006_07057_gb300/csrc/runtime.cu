@@ -170,7 +170,7 @@ using namespace lsf;
 
 extern "C" {
 
-int lsf_version(void) { return 1; }
+int lsf_version(void) { return 2; }
 
 const char* lsf_last_error(void) { return g_last_error.c_str(); }
 

@@ -305,6 +305,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(const SmallA
     P.result->W = 0.0;
     P.result->residual = 0.0;
     P.result->status = 0;
+    P.result->mode = LSF_MODE_STORED;
+    P.result->reserved = 0;
   }
   // M = max_j shift_y(j) over the whole cloud (the start v = 1 as v~ = exp(shift - M))
   float m = -INFINITY;

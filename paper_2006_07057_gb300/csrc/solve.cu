@@ -39,11 +39,14 @@ __global__ void init_scaling_kernel(const float* __restrict__ shift, int64_t n,
   }
 }
 
-__global__ void set_iters_kernel(lsf_result* r0, lsf_result* r1, lsf_result* r2, int iters) {
+__global__ void set_iters_kernel(lsf_result* r0, lsf_result* r1, lsf_result* r2, int iters, int mode) {
   if (threadIdx.x == 0) {
-    if (r0) r0->iters = iters;
-    if (r1) r1->iters = iters;
-    if (r2) r2->iters = iters;
+    lsf_result* rs[3] = {r0, r1, r2};
+    for (lsf_result* r : rs)
+      if (r) {
+        r->iters = iters;
+        r->mode = mode;
+      }
   }
 }
 
@@ -79,7 +82,8 @@ struct DivSeg {
   int64_t n;
   int term;            // which result record
   double sign;         // +1: log u = log u~ - shift - M ; -1: log v = log v~ - shift + M
-  int is_log;          // the scaling array already holds log u~ (log-domain mode)
+  int is_log;          // 1: the scaling array holds log u~ (log-domain mode); 0: u~;
+                       // -1: as the term's result record says (its mode field)
 };
 
 struct DivArgs {
@@ -112,12 +116,13 @@ __global__ void __launch_bounds__(256) divergence_kernel(const DivArgs a) {
   for (int sgi = 0; sgi < a.nseg; ++sgi) {
     const DivSeg sg = a.seg[sgi];
     const double off = static_cast<double>(sg.sign) * a.res[sg.term]->log_scale;
+    const bool lg = sg.is_log < 0 ? a.res[sg.term]->mode == LSF_MODE_LOG : sg.is_log != 0;
     const int64_t chunk = (sg.n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = chunk * blockIdx.x;
     const int64_t hi = min(sg.n, lo + chunk);
     double part = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double ls = sg.is_log ? static_cast<double>(sg.s[i]) : static_cast<double>(logf(sg.s[i]));
+      const double ls = lg ? static_cast<double>(sg.s[i]) : static_cast<double>(logf(sg.s[i]));
       part = fma(static_cast<double>(sg.w[i]), ls - static_cast<double>(sg.shift[i]) - off, part);
     }
     if (sg.term == 0) acc[0] += part;
@@ -264,6 +269,55 @@ int start_solve(void* workspace, size_t ws_bytes, int ldr, lsf_result* result, i
 
 namespace {
 
+// LSF_MODE_AUTO: build the features of both clouds into their (output) F and
+// shift buffers with the spread, pick the domain, run, and repeat in the log
+// domain after a range failure. run(mode) launches the solve in one mode;
+// status0 is the record that collects the device status bits.
+template <class Run>
+int solve_auto(const lsf_theta* th, const lsf_cloud* x, const lsf_cloud* y, lsf_result* status0,
+               void* workspace, size_t ws_bytes, cudaStream_t st, Run run) {
+  for (const lsf_cloud* c : {x, y}) {
+    if (!c || c->n < 1 || !c->X || !c->F || !c->shift || !c->w)
+      return fail(LSF_ERR_ARG, "auto mode: each cloud needs n >= 1, X, w and F, shift buffers");
+    if (reinterpret_cast<uintptr_t>(c->F) % 16 != 0)
+      return fail(LSF_ERR_ARG, "auto mode: F must be 16-byte aligned");
+  }
+  if (!th->U || !th->c) return fail(LSF_ERR_ARG, "auto mode: theta needs U and c");
+  if (!status0) return fail(LSF_ERR_ARG, "result is NULL");
+  Workspace ws{};
+  LSF_TRY(carve_workspace(workspace, ws_bytes, th->ldr, &ws));
+  float* spread = reinterpret_cast<float*>(ws.keys + 4);
+  auto build = [&](bool logd, float* spr) -> int {
+    for (const lsf_cloud* c : {x, y}) {
+      if (c == y && y->F == x->F) break;  // one cloud on both sides
+      float* F = const_cast<float*>(c->F);
+      float* sh = const_cast<float*>(c->shift);
+      LSF_TRY(logd ? lsf_log_features(c->X, c->n, th, F, sh, spr, st)
+                   : lsf_features(c->X, c->n, th, F, sh, spr, st));
+    }
+    return LSF_OK;
+  };
+  if (cudaMemsetAsync(spread, 0, sizeof(float), st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "auto mode: memset failed");
+  LSF_TRY(build(false, spread));
+  float h_spread = 0.f;
+  if (cudaMemcpyAsync(&h_spread, spread, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "auto mode: spread read-back failed");
+  if (static_cast<double>(h_spread) > LSF_AUTO_SPREAD) {
+    LSF_TRY(build(true, nullptr));
+    return run(LSF_MODE_LOG);
+  }
+  LSF_TRY(run(LSF_MODE_STORED));
+  int32_t status = 0;
+  if (cudaMemcpyAsync(&status, &status0->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "auto mode: status read-back failed");
+  if (!(status & LSF_ERR_NONFINITE)) return LSF_OK;
+  LSF_TRY(build(true, nullptr));
+  return run(LSF_MODE_LOG);
+}
+
 int init_side(const lsf_cloud* cl, unsigned* key, float* v, double* ls_a, double* ls_b, int mode,
               cudaStream_t st) {
   const int grid = device_info().sms * 2;
@@ -313,6 +367,12 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
               const lsf_scalings* out, lsf_result* result, void* workspace, size_t ws_bytes,
               void* stream) {
   LSF_TRY(check_theta(theta));
+  if (mode == LSF_MODE_AUTO) {
+    if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+    return solve_auto(theta, x, y, result, workspace, ws_bytes, as_stream(stream), [&](int m) {
+      return lsf_solve(theta, x, y, iters, m, out, result, workspace, ws_bytes, stream);
+    });
+  }
   LSF_TRY(check_cloud(x, mode, "x"));
   LSF_TRY(check_cloud(y, mode, "y"));
   LSF_TRY(check_scalings(out, "out"));
@@ -348,7 +408,7 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
   }
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
-    set_iters_kernel<<<1, 32, 0, st>>>(result, nullptr, nullptr, iters);
+    set_iters_kernel<<<1, 32, 0, st>>>(result, nullptr, nullptr, iters, mode);
   }
   return check_launch("set_iters_kernel");
 }
@@ -372,7 +432,7 @@ int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* x
   if (cudaMemsetAsync(ws.counters + 1, 0, sizeof(unsigned), st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "lsf_divergence: memset failed");
   return launch_divergence(theta, nterms, xs, ys, s, result, coef, combined, ws, st,
-                           mode == LSF_MODE_LOG ? 1 : 0);
+                           mode == LSF_MODE_LOG ? 1 : mode == LSF_MODE_AUTO ? -1 : 0);
 }
 
 int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
@@ -380,6 +440,13 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  const lsf_scalings* s_yy, lsf_result* result, double* wbar, void* workspace,
                  size_t ws_bytes, void* stream) {
   LSF_TRY(check_theta(theta));
+  if (mode == LSF_MODE_AUTO) {
+    if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
+    return solve_auto(theta, x, y, result, workspace, ws_bytes, as_stream(stream), [&](int m) {
+      return lsf_debiased(theta, x, y, iters, m, s_xy, s_xx, s_yy, result, wbar, workspace,
+                          ws_bytes, stream);
+    });
+  }
   LSF_TRY(check_cloud(x, mode, "x"));
   LSF_TRY(check_cloud(y, mode, "y"));
   LSF_TRY(check_scalings(s_xy, "xy"));
@@ -467,7 +534,7 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
   }
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
-    set_iters_kernel<<<1, 32, 0, st>>>(rxy, rxx, ryy, iters);
+    set_iters_kernel<<<1, 32, 0, st>>>(rxy, rxx, ryy, iters, mode);
   }
   // Status bits of all passes were collected in the first record; mirror them.
   if (cudaMemcpyAsync(&rxx->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=

@@ -1,33 +1,39 @@
 """Continuous-batching server for debiased Sinkhorn divergence requests.
 
-Requests of uneven shape (n, m, d, r, eps) arrive over time. The server keeps
-each admitted request's features and scalings resident on the device, admits
-waiting requests whenever a slot and enough of the HBM budget are free, and runs
-every admitted request on its own CUDA stream, so the kernels of requests that
-arrived while others were running overlap on the GPU (small requests occupy few
-SMs). Completion is detected by polling CUDA events; the latency of a request is
-its completion time minus its arrival time.
+Requests of uneven shape (n, m, d, r, eps) arrive over time. The server owns one
+device pool the size of its HBM budget, carved first-fit into per-request
+arenas, and a set of slots, each a CUDA stream with a pinned result record. A
+waiting request is admitted as soon as a slot is free and its arena fits in the
+pool; it then runs the whole path on its slot's stream with one library call
+(lsf_pipeline_run: inputs copied in, Lemma 1 parameters and anchors on the
+device, features, the lock-step solves of Eq. (2), the result record copied
+out), so the kernels of requests that arrived while others were running overlap
+on the GPU. Admission never waits on the device and allocates nothing;
+completion is detected by polling CUDA events. The latency of a request is its
+completion time minus its arrival time.
 
-Each request runs exactly the single-problem path (lsf_features, lsf_debiased),
-so its result does not depend on what else is running: the kernels reduce in
-a fixed order for a given shape. A request whose scaling-domain run reports a
-non-finite scaling (features or scalings outside the FP32 range) is run again
-in the log domain in the same slot, found at completion time, so the scheduler
-never blocks on it.
+Each request runs exactly the single-problem path, so its result does not depend
+on what else is running: the kernels reduce in a fixed order for a given shape.
+A request whose scaling-domain run reports a non-finite scaling (features or
+scalings outside the FP32 range) is run again in the log domain in the same
+slot and arena, found at completion time, so the scheduler never blocks on it.
 
 The plain competitor, `serve_sequential`, takes the same requests in arrival
-order and solves them one at a time on one stream.
+order and solves them one at a time on one stream with the same call and the
+same routing.
 """
 from __future__ import annotations
 
 import collections
+import ctypes
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 import torch
 
-from . import LSF_ERR_NONFINITE, SinkhornProblem, ldr_for, lsf_workspace_bytes
+from . import (LSF_ERR_NONFINITE, MODE_NAMES, LsfPipelineOut, alloc_arena, lsf_pipeline_bytes,
+               lsf_pipeline_run, pipeline_desc)
 
 
 @dataclass
@@ -49,76 +55,135 @@ class Request:
     W_bar: float = float("nan")
     status: int = -1
     result: dict = field(default_factory=dict)
+    host: list | None = None   # the inputs in pinned host memory (see pin)
 
     @property
     def latency_s(self) -> float:
         return self.done_s - self.arrival_s
 
+    def pin(self) -> "Request":
+        """Hold the inputs in pinned host memory, as a server receiving requests into
+        pinned buffers would; the copies to the device are then asynchronous."""
+        if self.host is None:
+            self.host = [torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).pin_memory()
+                         for v in (self.X, self.Y, self.a, self.b, self.Z)]
+        return self
 
-def request_bytes(n: int, m: int, r: int, d: int) -> int:
-    """Device bytes a request holds while admitted (features, points, scalings, workspace)."""
-    ldr = ldr_for(r)
-    feats = 4 * (n + m) * ldr
-    pts = 4 * (n + m) * (d + 2) + 4 * r * (d + 1) + 4 * r * d
-    scal = 4 * (2 * n + 2 * m + (n + m)) + 4 * 6 * ldr
-    return feats + pts + scal + lsf_workspace_bytes(ldr) + 4096
+    def desc(self, mode: str):
+        return pipeline_desc(self.X.shape[0], self.Y.shape[0], self.X.shape[1], self.Z.shape[0],
+                             self.eps, self.iters, True, mode)
+
+
+def request_bytes(n: int, m: int, r: int, d: int, mode: str = "stored") -> int:
+    """Device bytes a request holds while admitted: its lsf_pipeline_run arena
+    (inputs, theta, features, scalings, results, workspace)."""
+    return lsf_pipeline_bytes(pipeline_desc(n, m, d, r, 1.0, 1, True, mode))
+
+
+class Pool:
+    """First-fit allocator of 256-byte aligned ranges in one device buffer."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes: int, device):
+        self.size = int(nbytes) // self.ALIGN * self.ALIGN
+        self.buf = alloc_arena(self.size, device)
+        self.free_list = [(0, self.size)]   # (offset, length), sorted, coalesced
+        self.in_use = 0
+
+    def alloc(self, nbytes: int):
+        need = (int(nbytes) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        for k, (off, ln) in enumerate(self.free_list):
+            if ln >= need:
+                if ln == need:
+                    self.free_list.pop(k)
+                else:
+                    self.free_list[k] = (off + need, ln - need)
+                self.in_use += need
+                return off, need
+        return None
+
+    def free(self, off: int, ln: int) -> None:
+        self.in_use -= ln
+        fl = self.free_list
+        k = 0
+        while k < len(fl) and fl[k][0] < off:
+            k += 1
+        fl.insert(k, (off, ln))
+        # coalesce with the neighbours
+        if k + 1 < len(fl) and fl[k][0] + fl[k][1] == fl[k + 1][0]:
+            fl[k] = (fl[k][0], fl[k][1] + fl[k + 1][1])
+            fl.pop(k + 1)
+        if k > 0 and fl[k - 1][0] + fl[k - 1][1] == fl[k][0]:
+            fl[k - 1] = (fl[k - 1][0], fl[k - 1][1] + fl[k][1])
+            fl.pop(k)
+
+    def view(self, off: int, ln: int) -> torch.Tensor:
+        return self.buf[off:off + ln]
 
 
 class _Slot:
     def __init__(self, device):
         self.stream = torch.cuda.Stream(device=device)
-        self.req = None
-        self.prob = None
-        self.mode = "stored"
-        self.host_out = torch.empty(1, dtype=torch.float64).pin_memory()
+        self.out = torch.zeros(ctypes.sizeof(LsfPipelineOut), dtype=torch.uint8).pin_memory()
         self.done = torch.cuda.Event()
-        self.bytes = 0
+        self.req = None
+        self.mode = "stored"
+        self.range = None   # (offset, bytes) in the pool
+
+    def record(self) -> dict:
+        o = LsfPipelineOut.from_address(self.out.data_ptr())
+        return {k: getattr(o, k) for k, _ in LsfPipelineOut._fields_ if k != "reserved"}
+
+
+def _launch(req: Request, mode: str, arena: torch.Tensor, out: torch.Tensor, stream) -> None:
+    req.pin()
+    lsf_pipeline_run(req.desc(mode), *req.host, arena, out.data_ptr(), stream)
+
+
+def _finished(req: Request, rec: dict, now: float) -> Request:
+    req.done_s = now
+    req.W_bar = rec["W"]
+    req.status = rec["status"]
+    req.result = {"mode": MODE_NAMES.get(rec["mode"], "?"), "W_xy": rec["W_xy"], "W_xx": rec["W_xx"],
+                  "W_yy": rec["W_yy"], "res_xy": rec["residual_xy"], "R": rec["R"], "q": rec["q"]}
+    return req
 
 
 class Server:
-    """Admit-by-budget continuous batching over CUDA streams."""
+    """Admit-by-budget continuous batching over CUDA streams, one device pool."""
 
     def __init__(self, budget_bytes: float = 40e9, slots: int = 16, device=None):
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.budget = float(budget_bytes)
-        self.in_use = 0.0
+        self.pool = Pool(int(budget_bytes), self.device)
         self.slots = [_Slot(self.device) for _ in range(slots)]
         self.peak_bytes = 0.0
         self.peak_inflight = 0
         self.relaunched = 0
 
-    def _launch(self, slot: _Slot, req: Request, now: float, mode: str = "stored") -> None:
+    @property
+    def in_use(self) -> float:
+        return float(self.pool.in_use)
+
+    def _start(self, slot: _Slot, req: Request, mode: str) -> None:
         slot.req = req
         slot.mode = mode
-        if mode == "stored":
-            req.start_s = now
-        with torch.cuda.stream(slot.stream):
-            t = {k: torch.from_numpy(getattr(req, k)).pin_memory().to(self.device, non_blocking=True)
-                 for k in ("X", "Y", "a", "b", "Z")}
-            prob = SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], req.eps, mode=mode,
-                                   stream=slot.stream)
-            prob.run(req.iters, debiased=True)
-            slot.host_out.copy_(prob.wbar, non_blocking=True)
-            slot.done.record(slot.stream)
-        slot.prob = prob
+        _launch(req, mode, self.pool.view(*slot.range), slot.out, slot.stream)
+        slot.done.record(slot.stream)
 
     def _finish(self, slot: _Slot, now: float):
         """Finish the slot's request, or relaunch it in the log domain (returns None)."""
         req = slot.req
-        vals = slot.prob.values()
-        if (vals["status"] & LSF_ERR_NONFINITE) and slot.mode == "stored":
+        rec = slot.record()
+        if (rec["status"] & LSF_ERR_NONFINITE) and slot.mode == "stored":
             self.relaunched += 1
-            self._launch(slot, req, now, mode="log")
+            self._start(slot, req, "log")
             return None
-        req.done_s = now
-        req.W_bar = float(slot.host_out.item())
-        req.status = vals["status"]
-        req.result["mode"] = slot.mode
-        req.result.update({k: vals[k] for k in ("W_xy", "W_xx", "W_yy", "res_xy") if k in vals})
-        self.in_use -= slot.bytes
+        _finished(req, rec, now)
+        self.pool.free(*slot.range)
         slot.req = None
-        slot.prob = None
-        slot.bytes = 0
+        slot.range = None
         return req
 
     def serve(self, requests: list[Request], realtime: bool = True) -> list[Request]:
@@ -128,6 +193,8 @@ class Server:
         (a request cannot start before it arrives); otherwise all are present at
         time 0.
         """
+        for r in requests:
+            r.pin()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
         waiting: collections.deque = collections.deque()
         finished = []
@@ -146,20 +213,23 @@ class Server:
                     r = self._finish(s, now())
                     if r is not None:
                         finished.append(r)
-            # admissions: first come, first served, as budget and slots allow
+            # admissions: first come, first served, as slots and the pool allow
             while waiting:
-                req = waiting[0]
-                need = request_bytes(req.X.shape[0], req.Y.shape[0], req.Z.shape[0], req.X.shape[1])
                 free = next((s for s in self.slots if s.req is None), None)
                 if free is None:
                     break
-                if self.in_use + need > self.budget and self.in_use > 0:
+                req = waiting[0]
+                rng = self.pool.alloc(request_bytes(req.X.shape[0], req.Y.shape[0], req.Z.shape[0],
+                                                    req.X.shape[1]))
+                if rng is None:
+                    if all(s.req is None for s in self.slots):
+                        raise MemoryError(f"request {req.rid} does not fit the {self.budget:.3g}-byte budget")
                     break
                 waiting.popleft()
-                free.bytes = need
-                self.in_use += need
-                self.peak_bytes = max(self.peak_bytes, self.in_use)
-                self._launch(free, req, now())
+                free.range = rng
+                req.start_s = now()
+                self._start(free, req, "stored")
+                self.peak_bytes = max(self.peak_bytes, float(self.pool.in_use))
                 self.peak_inflight = max(self.peak_inflight, sum(s.req is not None for s in self.slots))
             if not waiting and pending and all(s.req is None for s in self.slots):
                 # idle until the next arrival
@@ -172,10 +242,16 @@ class Server:
 
 
 def serve_sequential(requests: list[Request], realtime: bool = True, device=None) -> list[Request]:
-    """The plain competitor: one request at a time, in arrival order, one stream."""
+    """The plain competitor: one request at a time, in arrival order, one stream, the
+    same library call and the same routing (log domain after a non-finite run)."""
     device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
     reqs = sorted(requests, key=lambda r: r.arrival_s)
-    host_out = torch.empty(1, dtype=torch.float64).pin_memory()
+    for r in reqs:
+        r.pin()
+    arena = alloc_arena(max(request_bytes(r.X.shape[0], r.Y.shape[0], r.Z.shape[0], r.X.shape[1])
+                            for r in reqs), device)
+    out = torch.zeros(ctypes.sizeof(LsfPipelineOut), dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream(device)
     t0 = time.perf_counter()
     if not realtime:
         for r in reqs:
@@ -185,15 +261,14 @@ def serve_sequential(requests: list[Request], realtime: bool = True, device=None
         if wait > 0:
             time.sleep(wait)
         req.start_s = time.perf_counter() - t0
-        t = {k: torch.from_numpy(getattr(req, k)).pin_memory().to(device, non_blocking=True)
-             for k in ("X", "Y", "a", "b", "Z")}
-        prob = SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], req.eps, mode="auto")
-        prob.run(req.iters, debiased=True)
-        host_out.copy_(prob.wbar, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        req.done_s = time.perf_counter() - t0
-        req.W_bar = float(host_out.item())
-        req.status = prob.values()["status"]
+        for mode in ("stored", "log"):
+            _launch(req, mode, arena, out, stream)
+            stream.synchronize()
+            rec = LsfPipelineOut.from_address(out.data_ptr())
+            rec = {k: getattr(rec, k) for k, _ in LsfPipelineOut._fields_}
+            if not (rec["status"] & LSF_ERR_NONFINITE):
+                break
+        _finished(req, rec, time.perf_counter() - t0)
     return reqs
 
 

@@ -24,7 +24,7 @@ def test_library_exports_every_header_symbol():
 
 
 def test_version_and_empty_error():
-    assert lsf.lsf_version() == 1
+    assert lsf.lsf_version() == 2
     assert isinstance(lsf.lib().lsf_last_error(), bytes)
 
 

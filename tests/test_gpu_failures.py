@@ -2,12 +2,12 @@
 
 Two kinds of failure are made on purpose, both from the host:
 
-* bad data: a NaN planted in the points or the weights. A NaN in the points
-  makes the Lemma 1 radius non-finite, which the host-side parameter check
-  rejects (LSF_ERR_ARG) before any solve; with theta fixed beforehand, the NaN
-  reaches the features and the solve reports LSF_ERR_NONFINITE in its device
-  status. A NaN in the weights is reported the same way in every solver variant.
-  Nothing hangs and the device stays usable.
+* bad data: an infinite coordinate makes the Lemma 1 radius infinite, which
+  the host-side parameter check rejects (LSF_ERR_ARG) before any solve. A NaN
+  in the points (which the radius, a maximum, passes over) or in the weights
+  reaches the features or the scalings, and the solve reports LSF_ERR_NONFINITE
+  in its device status, in every solver variant. Nothing hangs and the device
+  stays usable.
 * a bounded wait that runs out: the batched solver's test hook makes its
   consumers wait for a round flag that nothing sets, with a 20 ms limit. Every
   problem must then carry LSF_ERR_TIMEOUT, the launch must end within seconds
@@ -41,16 +41,26 @@ def _dev(p):
     return c(p.X), c(p.Y), c(p.a), c(p.b), c(p.Z)
 
 
-def test_nan_in_points_is_rejected_by_the_parameter_check(lsf):
+def test_infinite_point_is_rejected_by_the_parameter_check(lsf):
     p = synth.small_problem(71, 500, 400, 3, 128, 0.3, 10)
     X, Y, a, b, Z = _dev(p)
-    X[17, 1] = float("nan")
+    X[17, 1] = float("inf")
     with pytest.raises(lsf.LsfError) as e:
         lsf.SinkhornProblem(X, Y, a, b, Z, p.eps)
     assert e.value.status == lsf.LSF_ERR_ARG
 
 
-@pytest.mark.parametrize("mode", ["stored", "recompute", "log"])
+@pytest.mark.parametrize("mode", ["stored", "hybrid", "auto"])
+def test_nan_point_gives_a_nonfinite_status(lsf, mode):
+    p = synth.small_problem(71, 500, 400, 3, 128, 0.3, 10)
+    X, Y, a, b, Z = _dev(p)
+    X[17, 1] = float("nan")
+    prob = lsf.SinkhornProblem(X, Y, a, b, Z, p.eps, mode=mode)
+    prob.run(p.iters, debiased=True)
+    assert prob.values()["status"] & lsf.LSF_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("mode", ["stored", "recompute", "log", "hybrid"])
 @pytest.mark.parametrize("where", ["points", "weights"])
 def test_nan_reaches_the_device_status(lsf, mode, where):
     p = synth.small_problem(72, 3000, 2500, 3, 256, 0.3, 15)
