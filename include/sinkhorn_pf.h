@@ -306,12 +306,12 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
  * block on the allocator. Such a caller still passes its inputs and outputs
  * exactly as for lsf_solve, but no workspace.
  *
- * Scratch: a fixed 8 MiB array in the library's device image (kept by every GPU
+ * Scratch: a fixed 12 MiB array in the library's device image (kept by every GPU
  * that loads the library until the process exits). Problems whose
- * lsf_workspace_bytes(theta->ldr) exceeds 8 MiB are rejected with
+ * lsf_workspace_bytes(theta->ldr) exceeds 12 MiB are rejected with
  * LSF_ERR_UNSUPPORTED and a message; nothing is allocated, ever. (The scratch
- * grows with the SM count: at ldr = 1024 it is about 5.3 MB on 152 SMs, so the
- * rejection is only reached on parts with about 256 SMs or more.)
+ * grows with the SM count: at ldr = 1024 it is about 8.0 MB on 152 SMs, so the
+ * rejection is only reached on parts with about 240 SMs or more.)
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
  * before any stream capture. The address is kept for the life of the process:

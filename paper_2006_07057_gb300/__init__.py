@@ -331,7 +331,7 @@ def lsf_solve_noalloc(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, o
                       result, stream=None):
     """lsf_solve without a workspace, for callers that cannot allocate device memory.
 
-    The scratch comes from a fixed 8 MiB array inside the library; calls that can
+    The scratch comes from a fixed 12 MiB array inside the library; calls that can
     overlap on the GPU share it and must not run concurrently.
     """
     th, cx, cy, so = theta.as_c(), x.as_c(), y.as_c(), out.as_c()

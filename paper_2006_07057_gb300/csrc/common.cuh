@@ -61,7 +61,7 @@ int launch_anchors_device(const float* Z, int r, int d, const double* qs, double
 // Most CTAs any pass may launch: the workspace holds one partial r-vector slot per
 // CTA, so every pass launcher clamps its grid to this.
 int max_pass_ctas();
-constexpr int kMaxPassCtasPerSm = 2;
+constexpr int kMaxPassCtasPerSm = 3;
 
 // Two-level pass reduction: CTAs are summed in groups of kReduceGroup, then the
 // groups. The pass counters start at counters[kPassCounter]: one for the groups,

@@ -12,10 +12,13 @@
 // feed the same row products, divisions and transposed products, so the
 // iterates are those of Alg. 1; only the source of each entry differs.
 //
-// Layout: 8 compute warps and one service warp, as in the recompute pass. A row
-// group of GW warps covers a row: thread tg of the group owns the recomputed
-// columns 4tg..4tg+3 (when below c0) and the stored columns c0+4tg..c0+4tg+3
-// (when below ldr). A batch gives each group 8 rows. The service warp copies a
+// Layout: 4 compute warps and one service warp per CTA, three CTAs per SM (128
+// registers a thread: 15 warps leave at most 4 on each of an SM's four
+// sub-partitions, whose register files hold 4 x 32 x 128 each; a 9-warp CTA at
+// more than 96 registers fits only once per SM). A row group of GW warps covers a
+// row: thread tg of the group owns the recomputed columns 4tg..4tg+3 (when below
+// c0) and the stored columns c0+4tg..c0+4tg+3 (when below ldr). A batch gives
+// each group 8 rows. The service warp copies a
 // batch's stored rows (one contiguous block of the stored matrix) into a
 // three-slot shared-memory ring with one bulk copy, two batches ahead, on an
 // mbarrier; the compute warps read their stored entries from shared memory twice
@@ -34,7 +37,7 @@
 namespace lsf {
 namespace {
 
-constexpr int kHyWarps = 8;                      // compute warps
+constexpr int kHyWarps = 4;                      // compute warps
 constexpr int kHyThreads = (kHyWarps + 1) * 32;  // + the service warp
 constexpr int kHyRB = 8;                         // rows per group per batch
 constexpr int kHySlots = 3;                      // stored-row ring depth
@@ -149,8 +152,7 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
       }
     };
     // prime both rings with the first two batches
-    copy_stored(blockIdx.x, 0);
-    copy_stored(static_cast<int64_t>(blockIdx.x) + gridDim.x, 1);
+    for (int j = 0; j < kHySlots - 1; ++j) copy_stored(static_cast<int64_t>(blockIdx.x) + j * gridDim.x, j);
     load_rows(blockIdx.x);
     park_rows(0);
     load_rows(static_cast<int64_t>(blockIdx.x) + gridDim.x);
@@ -161,7 +163,7 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
       load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight across the barrier
       __syncthreads();
       // slot (it + 2) % 3 was last read in the previous batch, before this barrier
-      copy_stored(b + 2 * static_cast<int64_t>(gridDim.x), (it + 2) % kHySlots);
+      copy_stored(b + (kHySlots - 1) * static_cast<int64_t>(gridDim.x), (it + kHySlots - 1) % kHySlots);
       if (!kAx) {
         const float4* rows = s_rows[it % 3];
         const int64_t row0 = b * RPB;
@@ -381,10 +383,10 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
                             a.status, s_flag, &s_last);
 }
 
-// Two CTAs of 288 threads per SM for d <= 4 (112 registers each: the whole
-// register file); one CTA with its full register need for larger d.
+// Three CTAs of 160 threads per SM for d <= 4 (128 registers a thread); for
+// larger d each thread takes its full register need.
 template <int GW, int D, int NRHS>
-__global__ void __maxnreg__(112) hybrid_kernel(const HybridArgs h, const int mode) {
+__global__ void __maxnreg__(128) hybrid_kernel(const HybridArgs h, const int mode) {
   hybrid_body<GW, D, NRHS>(h, mode);
 }
 template <int GW, int D, int NRHS>
@@ -407,6 +409,11 @@ int launch_gdn(int mode, const HybridArgs& h, cudaStream_t st) {
     kern = hybrid_kernel_wide<GW, D, NRHS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
+  // the whole unified L1 as shared memory, so that the CTAs the registers allow
+  // are not cut by a smaller carveout
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             static_cast<int>(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "hybrid: smem attribute: %s", cudaGetErrorString(e));
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHyThreads, smem);

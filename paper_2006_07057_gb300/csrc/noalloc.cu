@@ -17,10 +17,10 @@
 namespace {
 
 // Largest scratch this entry point can use. One solve needs
-// lsf_workspace_bytes(ldr): about 32 * SMs * ldr bytes, i.e. ~5 MB at
+// lsf_workspace_bytes(ldr): about 52 * SMs * ldr bytes, i.e. ~8 MB at
 // ldr = 1024 on a 152-SM GB300. Every GPU that loads the library keeps this
 // array until the process exits.
-constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;  // 12 MiB
 
 // In host code this name is only a stand-in for the device array: its device
 // address must be fetched with cudaGetSymbolAddress on each device.
