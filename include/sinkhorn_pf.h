@@ -377,10 +377,34 @@ int lsf_pipeline_bytes(const lsf_pipeline* p, size_t* bytes);
  * inputs in pinned memory must stay unchanged until then; pageable ones are
  * staged by the copy. LSF_MODE_AUTO synchronises the stream inside (see
  * lsf_mode). Errors: those of the steps, with device status bits in out->status.
+ *
+ * With p->iters == 0 the call only prepares the problem (inputs in, Lemma 1,
+ * anchors and the features of p->mode, which must then be LSF_MODE_STORED or
+ * LSF_MODE_LOG); out may be NULL. A batched solve (lsf_batch_plan and
+ * lsf_solve_batched on the buffers lsf_pipeline_layout names) then solves the
+ * terms, and lsf_pipeline_finish writes the record.
  */
 int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, const float* a,
                      const float* b, const float* Z, void* arena, size_t arena_bytes,
                      lsf_pipeline_out* out, void* stream);
+
+/* Device views into a pipeline arena: theta, both clouds (X, features, shifts,
+ * weights), the scalings of the terms (xy, xx, yy) and their 3 result records. */
+typedef struct {
+  lsf_theta theta;
+  lsf_cloud x, y;
+  lsf_scalings s[3];
+  lsf_result* result;
+} lsf_pipeline_views;
+
+/* Fill *v for a description and an arena (host only; nothing is launched). */
+int lsf_pipeline_layout(const lsf_pipeline* p, void* arena, lsf_pipeline_views* v);
+
+/* The host record of a problem whose terms were solved on the arena's buffers
+ * by another call (a batched solve): Eq. (2) (when debiased) from the three
+ * result records' Eq. (6) values, R, q, sigma, status, mode; copied to the host
+ * record *out on the stream (valid once the stream has reached it). */
+int lsf_pipeline_finish(const lsf_pipeline* p, void* arena, lsf_pipeline_out* out, void* stream);
 
 /* ---------------------------------------------------------------- batched */
 

@@ -32,8 +32,8 @@ from ._binding import (LSF_ERR_ARG, LSF_ERR_UNSUPPORTED, LSF_ERR_WORKSPACE,  # n
                        LSF_MODE_AUTO, LSF_AUTO_SPREAD,
                        LSF_MODE_LOG, LSF_MODE_RECOMPUTE,
                        LSF_MODE_STORED, RESULT_BYTES, LsfCloud, LsfError, LsfResult, LsfScalings,
-                       LsfArccos, LsfTheta, LsfPipeline, LsfPipelineOut, check, header_symbols,
-                       lib)
+                       LsfArccos, LsfTheta, LsfPipeline, LsfPipelineOut, LsfPipelineViews, check,
+                       header_symbols, lib)
 
 MODES = {"stored": LSF_MODE_STORED, "recompute": LSF_MODE_RECOMPUTE, "log": LSF_MODE_LOG,
          "hybrid": LSF_MODE_HYBRID, "auto": LSF_MODE_AUTO}
@@ -364,6 +364,21 @@ def lsf_pipeline_run(desc: LsfPipeline, X, Y, a, b, Z, arena, out_ptr: int, stre
                                  arena.numel(), ctypes.cast(ctypes.c_void_p(out_ptr),
                                                             ctypes.POINTER(LsfPipelineOut)),
                                  _stream(stream)), "lsf_pipeline_run")
+
+
+def lsf_pipeline_layout(desc: LsfPipeline, arena) -> LsfPipelineViews:
+    """Device views (theta, clouds, scalings, result records) into a pipeline arena."""
+    v = LsfPipelineViews()
+    check(lib().lsf_pipeline_layout(ctypes.byref(desc), _p(arena), ctypes.byref(v)),
+          "lsf_pipeline_layout")
+    return v
+
+
+def lsf_pipeline_finish(desc: LsfPipeline, arena, out_ptr: int, stream=None) -> None:
+    """Eq. (2) from the arena's result records and the host record copy (on the stream)."""
+    check(lib().lsf_pipeline_finish(ctypes.byref(desc), _p(arena),
+                                    ctypes.cast(ctypes.c_void_p(out_ptr), ctypes.POINTER(LsfPipelineOut)),
+                                    _stream(stream)), "lsf_pipeline_finish")
 
 
 def alloc_arena(nbytes: int, device) -> torch.Tensor:

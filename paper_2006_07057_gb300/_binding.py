@@ -86,6 +86,11 @@ class LsfPipelineOut(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class LsfPipelineViews(ctypes.Structure):
+    _fields_ = [("theta", LsfTheta), ("x", LsfCloud), ("y", LsfCloud), ("s", LsfScalings * 3),
+                ("result", c_void_p)]
+
+
 class LsfBatchProblem(ctypes.Structure):
     _fields_ = [("Fx", c_void_p), ("Fy", c_void_p), ("shift_x", c_void_p), ("shift_y", c_void_p),
                 ("a", c_void_p), ("b", c_void_p), ("n", c_int64), ("m", c_int64),
@@ -137,6 +142,8 @@ _SIGNATURES = {
     "lsf_pipeline_bytes": (c_int, [_P(LsfPipeline), _P(c_size_t)]),
     "lsf_pipeline_run": (c_int, [_P(LsfPipeline), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_size_t, _P(LsfPipelineOut), c_void_p]),
+    "lsf_pipeline_layout": (c_int, [_P(LsfPipeline), c_void_p, _P(LsfPipelineViews)]),
+    "lsf_pipeline_finish": (c_int, [_P(LsfPipeline), c_void_p, _P(LsfPipelineOut), c_void_p]),
     "lsf_accel_workspace_bytes": (c_int, [c_int64, c_int64, c_int, _P(c_size_t)]),
     "lsf_solve_accelerated": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double,
                                       _P(LsfScalings), c_void_p, _P(LsfAccelInfo), c_void_p,

@@ -41,6 +41,32 @@ __global__ void pipeline_out_kernel(const lsf_result* res, int nres, const doubl
   *out = o;
 }
 
+// The record of a problem whose three terms were solved elsewhere (a batched
+// solve on the arena's buffers): Eq. (2) from the three Eq. (6) values.
+__global__ void finish_out_kernel(const lsf_result* res, int nres, const float* R, const double* qs,
+                                  lsf_pipeline_out* out) {
+  if (threadIdx.x != 0) return;
+  lsf_pipeline_out o{};
+  o.W_xy = res[0].W;
+  o.residual_xy = res[0].residual;
+  o.status = res[0].status;
+  o.mode = res[0].mode;
+  o.W = res[0].W;
+  if (nres == 3) {
+    o.W_xx = res[1].W;
+    o.W_yy = res[2].W;
+    o.residual_xx = res[1].residual;
+    o.residual_yy = res[2].residual;
+    o.status |= res[1].status | res[2].status;
+    o.W = res[0].W - 0.5 * (res[1].W + res[2].W);
+  }
+  o.R = static_cast<double>(R[0]);
+  o.q = qs[0];
+  o.sigma = qs[1];
+  o.iters = res[0].iters;
+  *out = o;
+}
+
 // Offsets of every buffer in the arena (bytes, each 256-aligned).
 struct Layout {
   size_t X, Y, a, b, Z, U, c, R, qs, Fx, Fy, sx, sy, s[3][4], res, wbar, out, ws, total;
@@ -52,7 +78,9 @@ int layout(const lsf_pipeline* p, Layout* L) {
   if (p->n < 1 || p->m < 1) return fail(LSF_ERR_ARG, "pipeline: need n, m >= 1");
   if (p->d < 1 || p->r < 1) return fail(LSF_ERR_ARG, "pipeline: need d, r >= 1");
   if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(LSF_ERR_ARG, "pipeline: eps must be > 0");
-  if (p->iters < 1) return fail(LSF_ERR_ARG, "pipeline: iters must be >= 1");
+  if (p->iters < 0) return fail(LSF_ERR_ARG, "pipeline: iters must be >= 0");
+  if (p->iters == 0 && p->mode != LSF_MODE_STORED && p->mode != LSF_MODE_LOG)
+    return fail(LSF_ERR_ARG, "pipeline: preparing (iters = 0) takes the stored or log mode");
   const int ldr = p->ldr ? p->ldr : (p->r + 3) / 4 * 4;
   if (ldr < p->r || ldr % 4 != 0 || ldr > 1024)
     return fail(LSF_ERR_UNSUPPORTED, "pipeline: ldr must be a multiple of 4 in [r, 1024]");
@@ -130,7 +158,8 @@ int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, cons
                      lsf_pipeline_out* out, void* stream) {
   Layout L{};
   LSF_TRY(layout(p, &L));
-  if (!X || !Y || !a || !b || !Z || !out) return fail(LSF_ERR_ARG, "lsf_pipeline_run: NULL argument");
+  if (!X || !Y || !a || !b || !Z || (!out && p->iters > 0))
+    return fail(LSF_ERR_ARG, "lsf_pipeline_run: NULL argument");
   if (!arena || reinterpret_cast<uintptr_t>(arena) % 256 != 0)
     return fail(LSF_ERR_ARG, "lsf_pipeline_run: the arena must be 256-byte aligned");
   if (arena_bytes < L.total)
@@ -169,6 +198,7 @@ int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, cons
       default: break;
     }
   }
+  if (p->iters == 0) return LSF_OK;  // prepared: a batched solve takes it from here
   lsf_scalings s[3];
   for (int t = 0; t < 3; ++t)
     s[t] = lsf_scalings{F(L.s[t][0]), F(L.s[t][1]), F(L.s[t][2]), F(L.s[t][3])};
@@ -196,6 +226,40 @@ int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, cons
   }
   if (cudaMemcpyAsync(out, dout, sizeof(lsf_pipeline_out), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail(LSF_ERR_CUDA, "lsf_pipeline_run: result copy failed");
+  return LSF_OK;
+}
+
+int lsf_pipeline_layout(const lsf_pipeline* p, void* arena, lsf_pipeline_views* v) {
+  Layout L{};
+  LSF_TRY(layout(p, &L));
+  if (!arena || !v) return fail(LSF_ERR_ARG, "lsf_pipeline_layout: NULL argument");
+  char* base = static_cast<char*>(arena);
+  auto F = [&](size_t o) { return reinterpret_cast<float*>(base + o); };
+  v->theta = lsf_theta{F(L.U), F(L.c), p->r, L.ldr, p->d, p->eps};
+  v->x = lsf_cloud{F(L.X), L.ldf ? F(L.Fx) : nullptr, F(L.sx), F(L.a), p->n};
+  v->y = lsf_cloud{F(L.Y), L.ldf ? F(L.Fy) : nullptr, F(L.sy), F(L.b), p->m};
+  for (int t = 0; t < 3; ++t)
+    v->s[t] = lsf_scalings{F(L.s[t][0]), F(L.s[t][1]), F(L.s[t][2]), F(L.s[t][3])};
+  v->result = reinterpret_cast<lsf_result*>(base + L.res);
+  return LSF_OK;
+}
+
+int lsf_pipeline_finish(const lsf_pipeline* p, void* arena, lsf_pipeline_out* out, void* stream) {
+  Layout L{};
+  LSF_TRY(layout(p, &L));
+  if (!arena || !out) return fail(LSF_ERR_ARG, "lsf_pipeline_finish: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  char* base = static_cast<char*>(arena);
+  lsf_pipeline_out* dout = reinterpret_cast<lsf_pipeline_out*>(base + L.out);
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    finish_out_kernel<<<1, 32, 0, st>>>(reinterpret_cast<const lsf_result*>(base + L.res),
+                                        p->debiased ? 3 : 1, reinterpret_cast<const float*>(base + L.R),
+                                        reinterpret_cast<const double*>(base + L.qs), dout);
+    LSF_TRY(check_launch("finish_out_kernel"));
+  }
+  if (cudaMemcpyAsync(out, dout, sizeof(lsf_pipeline_out), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "lsf_pipeline_finish: result copy failed");
   return LSF_OK;
 }
 

@@ -20,8 +20,9 @@
 // shuffles) and writes them to shared memory; after one barrier every compute
 // warp of the group sums the group's partials for the 8 rows in the same fixed
 // order and forms the new scalings itself, so no warp waits for another to
-// finish a row. The side work of a batch (building the rows' records two
-// batches ahead, writing the new scalings, the residual terms and the status)
+// finish a row. The side work of a batch (loading the rows' records three
+// batches ahead and packing them two ahead, writing the new scalings, the
+// residual terms and the status)
 // belongs to the service warp, so the compute warps carry identical
 // instruction streams and meet at the barrier together (done by one of them,
 // that work made the other seven wait at every barrier). One barrier per batch
@@ -88,56 +89,70 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
     constexpr int kPer = (RPB + 31) / 32;  // rows per lane
-    float4 pre[kPer][SV];
-    auto load_rows = [&](int64_t b) {
+    // A row's raw record (x, shift, weights, previous scalings) is loaded two
+    // batches before its batch and only turned into the packed record (x
+    // doubled, B = -log2(e) ((2/eps)||x||^2 + shift)) when it is parked in shared
+    // memory, so the service warp does not wait for the loads before a barrier.
+    struct Raw {
+      float x[D];
+      float sh;
+      float w[NRHS];
+      float o[NRHS];
+    };
+    Raw ra[kPer], rb[kPer];
+    auto load_raw = [&](int64_t b, Raw (&r)[kPer]) {
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int64_t i = b * RPB + lane + 32 * u;
+        const bool ok = b < nbatch && i < a.n;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) r[u].x[dd] = (ok && dd < d) ? a.X[i * d + dd] : 0.f;
+        r[u].sh = ok ? a.shift[i] : INFINITY;  // rows past the end: B = -inf, no mass
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          r[u].w[k] = (ok && !kAx) ? a.rhs[k].w[i] : 0.f;
+          r[u].o[k] = (ok && has_old[k]) ? a.rhs[k].old[i] : 0.f;
+        }
+      }
+    };
+    auto park_raw = [&](const Raw (&r)[kPer], int bf) {
 #pragma unroll
       for (int u = 0; u < kPer; ++u) {
         const int rr = lane + 32 * u;
-        const int64_t i = b * RPB + rr;
         float rec[4 * SV];
 #pragma unroll
         for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
-        if (b < nbatch && i < a.n) {
-          float nrm = 0.f;
+        float nrm = 0.f;
 #pragma unroll
-          for (int dd = 0; dd < D; ++dd) {
-            const float x = (dd < d) ? a.X[i * d + dd] : 0.f;
-            rec[2 * dd] = x;
-            rec[2 * dd + 1] = x;
-            nrm = fmaf(x, x, nrm);
-          }
-          rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + a.shift[i]);
-#pragma unroll
-          for (int k = 0; k < NRHS; ++k) {
-            rec[4 * XV + 2 * k] = kAx ? 0.f : a.rhs[k].w[i];
-            rec[4 * XV + 2 * k + 1] = has_old[k] ? a.rhs[k].old[i] : 0.f;
-          }
-        } else {
-          rec[2 * D] = rec[2 * D + 1] = -INFINITY;  // rows past the end carry no mass
+        for (int dd = 0; dd < D; ++dd) {
+          rec[2 * dd] = rec[2 * dd + 1] = r[u].x[dd];
+          nrm = fmaf(r[u].x[dd], r[u].x[dd], nrm);
         }
+        rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + r[u].sh);
 #pragma unroll
-        for (int v = 0; v < SV; ++v)
-          pre[u][v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
-      }
-    };
-    auto park_rows = [&](int bf) {
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int rr = lane + 32 * u;
+        for (int k = 0; k < NRHS; ++k) {
+          rec[4 * XV + 2 * k] = r[u].w[k];
+          rec[4 * XV + 2 * k + 1] = r[u].o[k];
+        }
         if (rr < RPB)
 #pragma unroll
-          for (int v = 0; v < SV; ++v) s_rows[bf][rr * SV + v] = pre[u][v];
+          for (int v = 0; v < SV; ++v)
+            s_rows[bf][rr * SV + v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
       }
     };
-    // prime the ring with the first two batches
-    load_rows(blockIdx.x);
-    park_rows(0);
-    load_rows(static_cast<int64_t>(blockIdx.x) + gridDim.x);
-    park_rows(1);
+    // prime the ring with the first two batches; the third batch's raw records
+    // are parked after the first barrier
+    const int64_t G = gridDim.x;
+    load_raw(blockIdx.x, ra);
+    park_raw(ra, 0);
+    load_raw(blockIdx.x + G, ra);
+    park_raw(ra, 1);
+    load_raw(blockIdx.x + 2 * G, ra);
     __syncthreads();
-    int it = 0;
-    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
-      load_rows(b + 2 * static_cast<int64_t>(gridDim.x));  // in flight across the barrier
+    // one batch: the raw records of batch b + 3G load into `ld` (waited for two
+    // batches later), the records of batch b + 2G (in `pk`) are parked
+    auto step = [&](int64_t b, int it, Raw (&ld)[kPer], const Raw (&pk)[kPer]) {
+      load_raw(b + 3 * G, ld);
       __syncthreads();
       if (!kAx) {
         // the batch's records: row sums from the group partials (the same fixed
@@ -178,7 +193,17 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
       }
       // the batch two ahead goes to the slot the compute warps last read in the
       // previous batch (before this barrier)
-      park_rows((it + 2) % 3);
+      park_raw(pk, (it + 2) % 3);
+    };
+    int it = 0;
+    for (int64_t b = blockIdx.x; b < nbatch;) {
+      step(b, it, rb, ra);
+      b += G;
+      ++it;
+      if (b >= nbatch) break;
+      step(b, it, ra, rb);
+      b += G;
+      ++it;
     }
   } else {
     // ---- compute warps ----

@@ -32,8 +32,9 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (LSF_ERR_NONFINITE, MODE_NAMES, LsfPipelineOut, alloc_arena, lsf_pipeline_bytes,
-               lsf_pipeline_run, pipeline_desc)
+from . import (LSF_ERR_NONFINITE, MODE_NAMES, RESULT_BYTES, LsfBatchProblem, LsfPipelineOut, alloc_arena,
+               ldr_for, lsf_batch_plan, lsf_pipeline_bytes, lsf_pipeline_finish, lsf_pipeline_layout,
+               lsf_pipeline_run, lsf_solve_batched, pipeline_desc)
 
 
 @dataclass
@@ -233,6 +234,154 @@ class Server:
                 self.peak_inflight = max(self.peak_inflight, sum(s.req is not None for s in self.slots))
             if not waiting and pending and all(s.req is None for s in self.slots):
                 # idle until the next arrival
+                dt = pending[0].arrival_s - now()
+                if dt > 0:
+                    time.sleep(min(dt, 0.01))
+            else:
+                time.sleep(0)
+        return finished
+
+
+class _Group:
+    """Requests admitted together: prepared, solved by one persistent batched launch
+    per feature width, finished; one event marks the end of its work."""
+
+    def __init__(self, reqs, mode, plans):
+        self.reqs = reqs
+        self.mode = mode
+        self.plans = plans          # keeps the device plans alive while the group runs
+        self.done = torch.cuda.Event()
+
+
+class BatchingServer:
+    """Continuous batching through the persistent batched solver.
+
+    Waiting requests are admitted in groups whenever fewer than ``inflight``
+    groups are on the GPU. Each admitted request gets an arena from the pool
+    (first fit, the budget bounds the pool) and a pinned result record, and is
+    prepared on the device (lsf_pipeline_run with iters = 0: inputs in, Lemma 1
+    on the device, anchors, features). The three terms of Eq. (2) of every
+    request of the group become rows of a device problem table (one
+    lsf_batch_plan per feature width), which one cooperative persistent launch
+    solves for all iterations (lsf_solve_batched); lsf_pipeline_finish then forms
+    Eq. (2) per request and copies its record out. Requests that report a
+    non-finite scaling go back to the head of the queue and are re-admitted in a
+    log-domain group (log features, the batched solver's log mode). Admission
+    does not wait on the device; the only host waits are the plan copies (small,
+    on their own stream).
+    """
+
+    def __init__(self, budget_bytes: float = 40e9, max_group: int = 256, inflight: int = 2,
+                 device=None):
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.budget = float(budget_bytes)
+        self.pool = Pool(int(budget_bytes), self.device)
+        self.max_group = int(max_group)
+        self.inflight = int(inflight)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.plan_stream = torch.cuda.Stream(device=self.device)
+        self.outs = torch.zeros((max_group * (inflight + 1), ctypes.sizeof(LsfPipelineOut)),
+                                dtype=torch.uint8).pin_memory()
+        self.free_outs = list(range(self.outs.shape[0]))
+        self.peak_bytes = 0.0
+        self.peak_inflight = 0
+        self.relaunched = 0
+        self.groups_run = 0
+
+    def _admit(self, reqs: list, mode: str) -> _Group:
+        st = self.stream
+        by_ldr: dict = {}
+        for r in reqs:
+            desc = pipeline_desc(r.X.shape[0], r.Y.shape[0], r.X.shape[1], r.Z.shape[0], r.eps, 0,
+                                 True, mode)
+            r._desc = desc
+            arena = self.pool.view(*r._range)
+            v = lsf_pipeline_layout(desc, arena)
+            recs = []
+            for t, (cx, cy) in enumerate(((v.x, v.y), (v.x, v.x), (v.y, v.y))):
+                sc = v.s[t]
+                recs.append(LsfBatchProblem(cx.F, cy.F, cx.shift, cy.shift, cx.w, cy.w, cx.n, cy.n,
+                                            float(r.eps), sc.u, sc.v, sc.t_u, sc.t_v,
+                                            v.result + t * RESULT_BYTES))
+            by_ldr.setdefault(ldr_for(r.Z.shape[0]), []).extend(recs)
+        # the device problem tables, planned on their own stream (small host waits)
+        plans = []
+        for ldr, recs in sorted(by_ldr.items()):
+            info, plan = lsf_batch_plan(recs, ldr, 0, self.plan_stream, mode=mode)
+            plans.append((info, plan))
+        # the group's work, in order, on the group stream
+        for r in reqs:
+            r.pin()
+            lsf_pipeline_run(r._desc, *r.host, self.pool.view(*r._range), 0, st)
+        iters = reqs[0].iters
+        for info, plan in plans:
+            lsf_solve_batched(info, plan, iters, st)
+        for r in reqs:
+            lsf_pipeline_finish(r._desc, self.pool.view(*r._range), self.outs[r._out].data_ptr(), st)
+        g = _Group(reqs, mode, plans)
+        g.done.record(st)
+        self.groups_run += 1
+        return g
+
+    def serve(self, requests: list[Request], realtime: bool = True) -> list[Request]:
+        """Serve requests in arrival order; returns them with timings and results."""
+        if len({r.iters for r in requests}) > 1:
+            raise ValueError("one iteration count per served stream (the batched solve shares it)")
+        for r in requests:
+            r.pin()
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        waiting: collections.deque = collections.deque()
+        retry: collections.deque = collections.deque()   # range failures, arenas kept
+        running: list = []
+        finished = []
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+        if not realtime:
+            for r in pending:
+                r.arrival_s = 0.0
+        while pending or waiting or retry or running:
+            tnow = now()
+            while pending and pending[0].arrival_s <= tnow:
+                waiting.append(pending.popleft())
+            for g in [g for g in running if g.done.query()]:
+                running.remove(g)
+                t = now()
+                for r in g.reqs:
+                    o = LsfPipelineOut.from_address(self.outs[r._out].data_ptr())
+                    rec = {k: getattr(o, k) for k, _ in LsfPipelineOut._fields_}
+                    if (rec["status"] & LSF_ERR_NONFINITE) and g.mode == "stored":
+                        self.relaunched += 1
+                        retry.append(r)
+                        continue
+                    _finished(r, rec, t)
+                    self.pool.free(*r._range)
+                    self.free_outs.append(r._out)
+                    finished.append(r)
+            while len(running) < self.inflight and (retry or waiting):
+                if retry:
+                    group = [retry.popleft() for _ in range(min(len(retry), self.max_group))]
+                    running.append(self._admit(group, "log"))
+                    continue
+                group = []
+                while waiting and len(group) < self.max_group and self.free_outs:
+                    r = waiting[0]
+                    rng = self.pool.alloc(request_bytes(r.X.shape[0], r.Y.shape[0], r.Z.shape[0],
+                                                        r.X.shape[1]))
+                    if rng is None:
+                        if not group and not running:
+                            raise MemoryError(f"request {r.rid} does not fit the {self.budget:.3g}-byte budget")
+                        break
+                    waiting.popleft()
+                    r._range = rng
+                    r._out = self.free_outs.pop()
+                    r.start_s = now()
+                    group.append(r)
+                if not group:
+                    break
+                running.append(self._admit(group, "stored"))
+                self.peak_bytes = max(self.peak_bytes, float(self.pool.in_use))
+                self.peak_inflight = max(self.peak_inflight, sum(len(g.reqs) for g in running))
+            if not waiting and not retry and pending and not running:
                 dt = pending[0].arrival_s - now()
                 if dt > 0:
                     time.sleep(min(dt, 0.01))

@@ -132,8 +132,10 @@ def test_auto_through_the_debiased_entry_point(lsf):
 def test_pipeline_rejects_bad_descriptions_and_small_arenas(lsf):
     L = lsf.lib()
     b = ctypes.c_size_t()
+    # (iters = 0 only prepares, which the stored and log modes allow)
     for bad in (lsf.pipeline_desc(0, 10, 2, 8, 0.5, 3), lsf.pipeline_desc(10, 10, 2, 8, -1.0, 3),
-                lsf.pipeline_desc(10, 10, 2, 8, 0.5, 0)):
+                lsf.pipeline_desc(10, 10, 2, 8, 0.5, -1), lsf.pipeline_desc(10, 10, 2, 8, 0.5, 0,
+                                                                           mode="hybrid")):
         assert L.lsf_pipeline_bytes(ctypes.byref(bad), ctypes.byref(b)) == lsf.LSF_ERR_ARG
     desc = lsf.pipeline_desc(10, 10, 2, 2000, 0.5, 3)
     assert L.lsf_pipeline_bytes(ctypes.byref(desc), ctypes.byref(b)) == lsf.LSF_ERR_UNSUPPORTED

@@ -60,3 +60,49 @@ def test_admission_respects_the_budget(serve):
     assert srv.peak_bytes <= budget
     stats = serve.latency_stats(done)
     assert stats["latency_ms_p99"] >= stats["latency_ms_p50"] > 0
+
+
+def test_batching_server_matches_alone_and_the_oracle(serve):
+    # the continuous-batching server solves each request's three terms as rows of
+    # a batched problem table; the result must match the request solved alone
+    # (sequential arm) and the oracle at the divergence tolerance
+    from oracle import oracle as o
+    reqs = requests(serve, 20, seed=3)
+    alone = serve.serve_sequential([serve.Request(r.rid, r.X, r.Y, r.a, r.b, r.Z, r.eps, r.iters)
+                                    for r in reqs], realtime=False)
+    srv = serve.BatchingServer(budget_bytes=20e9, max_group=8)
+    mixed = srv.serve(reqs, realtime=False)
+    assert len(mixed) == len(reqs)
+    assert srv.groups_run >= 3 and srv.peak_inflight > 1
+    by_id = {r.rid: r for r in alone}
+    for r in mixed:
+        a = by_id[r.rid]
+        assert r.status == 0 and a.status == 0, (r.rid, r.status, a.status)
+        scale = abs(r.result["W_xy"]) + 0.5 * abs(r.result["W_xx"]) + 0.5 * abs(r.result["W_yy"])
+        assert abs(r.W_bar - a.W_bar) <= 1e-4 * scale, (r.rid, r.W_bar, a.W_bar)
+    for r in mixed[:4]:
+        ref = o.divergence(r.X, r.Y, r.a, r.b, r.Z, r.eps, r.iters, debiased=True)
+        scale = abs(ref["W_xy"]) + 0.5 * abs(ref["W_xx"]) + 0.5 * abs(ref["W_yy"])
+        assert abs(r.W_bar - ref["W_bar"]) <= 1e-4 * scale
+
+
+def test_batching_server_routes_range_failures_to_the_log_domain(serve):
+    # small eps with d = 16 puts some requests outside the FP32 range of the
+    # scaling domain; they are re-admitted in a log-domain group
+    out = []
+    for i, rq in enumerate(synth.serving_stream(seed=5, count=12, rate_per_s=4000.0, iters=30,
+                                                n_lo=1 << 8, n_hi=1 << 11)):
+        p = rq.problem
+        out.append(serve.Request(i, p.X, p.Y, p.a, p.b, p.Z, 0.05, 30, rq.arrival_s))
+    alone = serve.serve_sequential([serve.Request(r.rid, r.X, r.Y, r.a, r.b, r.Z, r.eps, r.iters)
+                                    for r in out], realtime=False)
+    srv = serve.BatchingServer(budget_bytes=10e9, max_group=6)
+    mixed = srv.serve(out, realtime=False)
+    by_id = {r.rid: r for r in alone}
+    for r in mixed:
+        a = by_id[r.rid]
+        assert r.status == 0 and a.status == 0, (r.rid, r.status, a.status)
+        scale = abs(r.result["W_xy"]) + 0.5 * abs(r.result["W_xx"]) + 0.5 * abs(r.result["W_yy"])
+        assert abs(r.W_bar - a.W_bar) <= 1e-4 * scale, (r.rid, r.W_bar, a.W_bar)
+    if any(a.result["mode"] == "log" for a in alone):
+        assert srv.relaunched > 0 and any(r.result["mode"] == "log" for r in mixed)
