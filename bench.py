@@ -478,6 +478,15 @@ def serving_measure(args, count, rate):
     seq = serve.serve_sequential(fresh(), realtime=True)
     st_seq = serve.latency_stats(seq)
     nonfinite = sum(1 for r in mixed if r.status & lsf.LSF_ERR_NONFINITE)
+    # where the GPU time goes: the sequential arm serves one request at a time,
+    # so each request's start-to-done time is its whole service time
+    service = {}
+    for r in seq:
+        key = r.result.get("mode", "?")
+        service.setdefault(key, [0, 0.0])
+        service[key][0] += 1
+        service[key][1] += r.done_s - r.start_s
+    st_seq["service_s_by_domain"] = {k: {"requests": v[0], "seconds": v[1]} for k, v in service.items()}
     by_id = {r.rid: r for r in seq}
     worst = max(abs(r.W_bar - by_id[r.rid].W_bar) /
                 max(abs(r.result["W_xy"]) + 0.5 * abs(r.result["W_xx"]) + 0.5 * abs(r.result["W_yy"]), 1e-30)
