@@ -79,6 +79,13 @@ __device__ __forceinline__ void tile_range(int64_t ntiles, int64_t* lo, int64_t*
   *hi = ntiles * (blockIdx.x + 1) / gridDim.x;
 }
 
+// The current value of a status word that other CTAs OR bits into (no caching).
+__device__ __forceinline__ int ld_status(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -112,9 +119,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
     // ------------------------------------------------------------ producer
     int it = 0;
     bool dead = false;
+    int prod_p = -1, prod_void = 0;
     for (int r = 0; r < A.rounds && !dead; ++r) {
       const int side = round_side(r, A.rounds);
       const bool copy_w = round_mode(r, A.rounds) != kPassAxpy;
+      prod_p = -1;
       int64_t lo, hi;
       tile_range(side ? A.ntiles[1] : A.ntiles[0], &lo, &hi);
       for (int64_t ti = lo; ti < hi; ++ti, ++it) {
@@ -130,13 +139,28 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
         }
         const BTile tl = (side ? A.tiles[1] : A.tiles[0])[ti];
         const BProb& pb = A.probs[tl.p];
-        if (lane == 0) {
-          const uint32_t bytes = static_cast<uint32_t>(tl.rows) * static_cast<uint32_t>(ldr) * 4u;
-          mbar_arrive_expect_tx(&ring.full[s], bytes);
-          bulk_copy_g2s(ring.sF + static_cast<size_t>(s) * TR * ldr, pb.F[side] + tl.row0 * ldr, bytes,
-                        &ring.full[s]);
+        // a problem that has produced a non-finite scaling is void (it is solved
+        // again in the log domain): its tiles are not streamed; the stage still
+        // completes (one plain arrival instead of the copy's). The status is read
+        // once per run of tiles of one problem.
+        if (tl.p != prod_p) {
+          prod_p = tl.p;
+          int v = 0;
+          if (lane == 0) v = (ld_status(&pb.result->status) & LSF_ERR_NONFINITE) ? 1 : 0;
+          prod_void = __shfl_sync(0xffffffffu, v, 0);
         }
-        if (copy_w) {
+        const int void_p = prod_void;
+        if (lane == 0) {
+          if (void_p) {
+            mbar_arrive(&ring.full[s]);
+          } else {
+            const uint32_t bytes = static_cast<uint32_t>(tl.rows) * static_cast<uint32_t>(ldr) * 4u;
+            mbar_arrive_expect_tx(&ring.full[s], bytes);
+            bulk_copy_g2s(ring.sF + static_cast<size_t>(s) * TR * ldr, pb.F[side] + tl.row0 * ldr, bytes,
+                          &ring.full[s]);
+          }
+        }
+        if (copy_w && !void_p) {
           float* dw = ring.sV + static_cast<size_t>(s * 2) * TR;
           const float* w = pb.w[side];
           for (int i = lane; i < tl.rows; i += 32) cp_async_4(dw + i, w + tl.row0 + i);
@@ -164,6 +188,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
       int64_t lo, hi;
       tile_range(side ? A.ntiles[1] : A.ntiles[0], &lo, &hi);
       int cur = -1;
+      // whether problem cur is void (read at each switch of problem, after the
+      // producer read it for the same tiles: the bit only gets set, so a tile the
+      // producer did not copy is always skipped here)
+      int cur_void = 0;
       // scaling domain: t = r-vector, acc = transposed product;
       // log domain: t = log r-vector, acc = running column max, lsum = column sums
       float t[C][4], acc[C][4], lsum[LOGD ? C : 1][4];
@@ -280,6 +308,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
             flag |= LSF_ERR_TIMEOUT;
             dead = true;
           }
+          int v = 0;
+          if (lane == 0) v = (ld_status(&A.probs[cur].result->status) & LSF_ERR_NONFINITE) ? 1 : 0;
+          cur_void = __shfl_sync(0xffffffffu, v, 0);
           const BProb& pb = A.probs[cur];
           const float* tin = pb.t[1 - side];
 #pragma unroll
@@ -297,7 +328,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) batched_kernel(const BatchArg
           }
           res = 0.0;
         }
-        if (!dead) {
+        if (!dead && !cur_void) {
           const BProb& pb = A.probs[cur];
           const int rows = tl.rows;
           const float* tF = ring.sF + static_cast<size_t>(s) * TR * ldr;
