@@ -81,19 +81,19 @@ def request_bytes(n: int, m: int, r: int, d: int, mode: str = "stored") -> int:
     return lsf_pipeline_bytes(pipeline_desc(n, m, d, r, 1.0, 1, True, mode))
 
 
-class Pool:
-    """First-fit allocator of 256-byte aligned ranges in one device buffer."""
+class FreeList:
+    """First-fit allocation of 256-byte aligned ranges of [0, size) (host only)."""
 
     ALIGN = 256
 
-    def __init__(self, nbytes: int, device):
+    def __init__(self, nbytes: int):
         self.size = int(nbytes) // self.ALIGN * self.ALIGN
-        self.buf = alloc_arena(self.size, device)
-        self.free_list = [(0, self.size)]   # (offset, length), sorted, coalesced
+        self.free_list = [(0, self.size)] if self.size else []   # (offset, length), sorted, coalesced
         self.in_use = 0
 
     def alloc(self, nbytes: int):
-        need = (int(nbytes) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        """(offset, length) of the first free range that fits, or None."""
+        need = max(self.ALIGN, (int(nbytes) + self.ALIGN - 1) // self.ALIGN * self.ALIGN)
         for k, (off, ln) in enumerate(self.free_list):
             if ln >= need:
                 if ln == need:
@@ -118,6 +118,14 @@ class Pool:
         if k > 0 and fl[k - 1][0] + fl[k - 1][1] == fl[k][0]:
             fl[k - 1] = (fl[k - 1][0], fl[k - 1][1] + fl[k][1])
             fl.pop(k)
+
+
+class Pool(FreeList):
+    """A FreeList over one device buffer (the server's admission budget)."""
+
+    def __init__(self, nbytes: int, device):
+        super().__init__(nbytes)
+        self.buf = alloc_arena(self.size, device)
 
     def view(self, off: int, ln: int) -> torch.Tensor:
         return self.buf[off:off + ln]

@@ -113,3 +113,14 @@ def test_hybrid_rejects_large_d_and_tiny_ldr(lsf):
     with pytest.raises(lsf.LsfError) as e:
         gpu(lsf, p, "hybrid", False)
     assert e.value.status == lsf.LSF_ERR_UNSUPPORTED
+
+
+def test_pipe_rate_probe(lsf):
+    # the denominators of the recompute and hybrid rooflines: packed FMA near the
+    # FP32 pipe's 128 lanes per clock per SM, ex2 near the special-function
+    # unit's 32; the packed form is not slower than the scalar one
+    r = lsf.lsf_probe_pipe_rates()
+    assert 96.0 <= r["ffma2_lane_ops_per_clk_sm"] <= 132.0, r
+    assert 64.0 <= r["ffma_lane_ops_per_clk_sm"] <= 132.0, r
+    assert 16.0 <= r["ex2_per_clk_sm"] <= 33.0, r
+    assert r["ffma2_lane_ops_per_clk_sm"] >= 0.95 * r["ffma_lane_ops_per_clk_sm"], r

@@ -24,3 +24,42 @@ def test_latency_stats_percentiles():
     st = serve.latency_stats(reqs)
     assert st["requests"] == 100
     assert abs(st["latency_ms_p50"] - 51.0) < 1e-6 and abs(st["latency_ms_p99"] - 100.0) < 1e-6
+
+
+def test_free_list_first_fit_against_a_brute_force_model():
+    # random allocations and frees; the free list must hand out disjoint,
+    # 256-byte aligned ranges inside the pool, account for every byte, coalesce
+    # neighbours, and fail exactly when no free gap is large enough
+    rng = np.random.default_rng(0)
+    size = 1 << 20
+    fl = serve.FreeList(size)
+    used = {}   # offset -> length
+    for _ in range(3000):
+        if used and rng.random() < 0.45:
+            off = int(rng.choice(list(used)))
+            fl.free(off, used.pop(off))
+        else:
+            want = int(rng.integers(1, 40000))
+            got = fl.alloc(want)
+            need = max(256, (want + 255) // 256 * 256)
+            # brute force: the gaps between used ranges, in address order
+            gaps, pos = [], 0
+            for o in sorted(used):
+                if o > pos:
+                    gaps.append((pos, o - pos))
+                pos = o + used[o]
+            if pos < size:
+                gaps.append((pos, size - pos))
+            first = next((g for g in gaps if g[1] >= need), None)
+            if first is None:
+                assert got is None
+                continue
+            assert got == (first[0], need)
+            used[got[0]] = got[1]
+        assert fl.in_use == sum(used.values())
+        assert sum(ln for _, ln in fl.free_list) == size - fl.in_use
+        offs = [o for o, _ in fl.free_list]
+        assert offs == sorted(offs)
+        for (o1, l1), (o2, _) in zip(fl.free_list, fl.free_list[1:]):
+            assert o1 + l1 < o2            # coalesced: no two free ranges touch
+        assert all(o % 256 == 0 and ln % 256 == 0 for o, ln in fl.free_list)
