@@ -42,11 +42,18 @@ constexpr int kHyThreads = (kHyWarps + 1) * 32;  // + the service warp
 constexpr int kHyRB = 8;                         // rows per group per batch
 constexpr int kHySlots = 3;                      // stored-row ring depth
 
-template <int GW, int D, int NRHS>
-__device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode) {
+// FLDR = 0: any row stride and pass mode. FLDR > 0: the update pass over rows of
+// exactly FLDR columns, compiled with the row stride, the column split and the
+// mode fixed, and with every compute thread owning both a recomputed and a
+// stored column quad (the configuration of the large workload, r = 1024).
+template <int GW, int D, int NRHS, int FLDR>
+__device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_in) {
   constexpr int NG = kHyWarps / GW;   // row groups per CTA
   constexpr int RPB = NG * kHyRB;     // rows per batch
   constexpr int TPG = GW * 32;        // threads per group
+  static_assert(FLDR == 0 || (4 * TPG == hybrid_first_stored(FLDR) && 4 * TPG == FLDR - hybrid_first_stored(FLDR)),
+                "the fixed-stride variant needs one column quad of each kind per thread");
+  const int mode = FLDR > 0 ? static_cast<int>(kPassUpdate) : mode_in;
   constexpr int XV = RowPack<D>::kXV;
   constexpr int SV = RowPack<D>::kSV;
   constexpr int kItems = NG * NRHS * kHyRB;
@@ -63,14 +70,14 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
   const bool kUpd = mode == kPassUpdate, kAx = mode == kPassAxpy, kDt = mode == kPassDot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool service = warp == kHyWarps;
-  const int g = service ? 0 : warp / GW;
+  const int g = (NG == 1 || service) ? 0 : warp / GW;
   const int tg = tid - g * TPG;
-  const int ldr = a.ldr, d = a.d;
-  const int c0 = h.c0;
+  const int ldr = FLDR > 0 ? FLDR : a.ldr, d = a.d;
+  const int c0 = FLDR > 0 ? hybrid_first_stored(FLDR) : h.c0;
   const int lds = ldr - c0;       // stored columns per row
   const int col0 = 4 * tg;        // my recomputed columns (valid below c0)
-  const bool has_rc = col0 < c0;
-  const bool has_st = col0 < lds; // my stored columns c0 + col0 .. + 3
+  const bool has_rc = FLDR > 0 ? !service : col0 < c0;
+  const bool has_st = FLDR > 0 ? !service : col0 < lds; // my stored columns c0 + col0 .. + 3
 
   if (tid == 0) {
     s_flag = 0;
@@ -154,12 +161,24 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
     auto copy_stored = [&](int64_t b, int s) {
       if (b >= nbatch) return;
       ++issued;
+      const int64_t row0 = b * RPB;
+      const int rows = static_cast<int>(min(static_cast<int64_t>(RPB), a.n - row0));
+      float* dst = s_ring + static_cast<size_t>(s) * RPB * lds;
+      if (rows < RPB) {
+        // the last batch: its rows past the end read as zeros, so that the
+        // compute warps take every row of a batch unpredicated (the slot may
+        // hold stale rows or nothing yet); these stores reach them through the
+        // arrive below, as the copy's bytes do through its completion
+        float4* z = reinterpret_cast<float4*>(dst + static_cast<size_t>(rows) * lds);
+        const int nz = (RPB - rows) * (lds >> 2);
+        for (int j = lane; j < nz; j += 32) z[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __threadfence_block();
+        __syncwarp();
+      }
       if (lane == 0) {
-        const int64_t row0 = b * RPB;
-        const int rows = static_cast<int>(min(static_cast<int64_t>(RPB), a.n - row0));
         const uint32_t bytes = static_cast<uint32_t>(rows) * static_cast<uint32_t>(lds) * 4u;
         mbar_arrive_expect_tx(&s_full[s], bytes);
-        bulk_copy_g2s(s_ring + static_cast<size_t>(s) * RPB * lds, h.Fs + row0 * lds, bytes, &s_full[s]);
+        bulk_copy_g2s(dst, h.Fs + row0 * lds, bytes, &s_full[s]);
       }
     };
     // prime both rings with the first two batches
@@ -274,14 +293,13 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();  // the rings are primed
-    int it = 0;
+    // batch it uses record buffer and ring slot it % 3 (both three deep) and
+    // the ring slot's mbarrier phase (it / 3) & 1, kept as running counters
+    int it = 0, slot = 0;
+    uint32_t phase = 0;
+    static_assert(kHySlots == 3, "record buffers and ring slots advance together");
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
-      const float4* rows = s_rows[it % 3];
-      const int slot = it % kHySlots;
-      // rows of this group in this batch that exist (the stored ring holds stale
-      // data beyond them)
-      const int nval = static_cast<int>(min(static_cast<int64_t>(kHyRB),
-                                            max(static_cast<int64_t>(0), a.n - (b * RPB + g * kHyRB))));
+      const float4* rows = s_rows[slot];
       const float4* srow = reinterpret_cast<const float4*>(s_ring + (static_cast<size_t>(slot) * RPB + g * kHyRB) * lds) + tg;
       const int ldq = lds >> 2;  // float4s per stored row
       // the recomputed entries first: they need only the row records, so the
@@ -305,12 +323,15 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
           F[q][p] = make_float2(ex2_approx(E.x), ex2_approx(E.y));
         }
       }
-      if (!mbar_wait_bounded(&s_full[slot], static_cast<uint32_t>(it / kHySlots) & 1u))
-        flag |= LSF_ERR_TIMEOUT;
+      if (!mbar_wait_bounded(&s_full[slot], phase)) flag |= LSF_ERR_TIMEOUT;
+      if (++slot == kHySlots) {
+        slot = 0;
+        phase ^= 1u;
+      }
       float dots[NRHS][kHyRB];
 #pragma unroll
       for (int q = 0; q < kHyRB; ++q) {
-        const float4 fs = (has_st && q < nval) ? srow[q * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 fs = has_st ? srow[q * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 fs0 = make_float2(fs.x, fs.y), fs1 = make_float2(fs.z, fs.w);
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
@@ -337,7 +358,8 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
       float scl = 0.f;
       if (!kAx) {
         const int kq = lane >> 3, qq = lane & 7;
-        if (kq < NRHS && qq < nval) {
+        // rows past the end have no mass (s = 0): their scaling stays 0
+        if (kq < NRHS && b * RPB + g * kHyRB + qq < a.n) {
           const float s = sum_partials<GW>(&s_red[it & 1][kq][qq][g * GW]);
           const float4 wo = rows[(g * kHyRB + qq) * SV + XV];
           scl = ((NRHS == 1 || kq == 0) ? wo.x : wo.z) * __frcp_rn(s);
@@ -345,7 +367,7 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
       }
 #pragma unroll
       for (int qq = 0; qq < kHyRB; ++qq) {
-        const float4 fs = (has_st && qq < nval) ? srow[qq * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 fs = has_st ? srow[qq * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 fs0 = make_float2(fs.x, fs.y), fs1 = make_float2(fs.z, fs.w);
         float4 wo;
         if (kAx) wo = rows[(g * kHyRB + qq) * SV + XV];
@@ -409,16 +431,16 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode)
 
 // Three CTAs of 160 threads per SM for d <= 4 (128 registers a thread); for
 // larger d each thread takes its full register need.
-template <int GW, int D, int NRHS>
+template <int GW, int D, int NRHS, int FLDR>
 __global__ void __maxnreg__(128) hybrid_kernel(const HybridArgs h, const int mode) {
-  hybrid_body<GW, D, NRHS>(h, mode);
+  hybrid_body<GW, D, NRHS, FLDR>(h, mode);
 }
 template <int GW, int D, int NRHS>
 __global__ void __launch_bounds__(kHyThreads, 1) hybrid_kernel_wide(const HybridArgs h, const int mode) {
-  hybrid_body<GW, D, NRHS>(h, mode);
+  hybrid_body<GW, D, NRHS, 0>(h, mode);
 }
 
-template <int GW, int D, int NRHS>
+template <int GW, int D, int NRHS, int FLDR = 0>
 int launch_gdn(int mode, const HybridArgs& h, cudaStream_t st) {
   constexpr int NG = kHyWarps / GW;
   constexpr int RPB = NG * kHyRB;
@@ -428,7 +450,7 @@ int launch_gdn(int mode, const HybridArgs& h, cudaStream_t st) {
   const size_t smem = std::max(ring, parts);
   void (*kern)(HybridArgs, int);
   if constexpr (D <= 4)
-    kern = hybrid_kernel<GW, D, NRHS>;
+    kern = hybrid_kernel<GW, D, NRHS, FLDR>;
   else
     kern = hybrid_kernel_wide<GW, D, NRHS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -451,6 +473,16 @@ int launch_gdn(int mode, const HybridArgs& h, cudaStream_t st) {
 
 template <int GW, int NRHS>
 int launch_gn(int mode, const HybridArgs& h, int Dp, cudaStream_t st) {
+  if constexpr (GW == 4) {
+    // the update pass at r = 1024, compiled for that stride
+    if (mode == kPassUpdate && h.rc.ldr == 1024 && Dp <= 4) {
+      switch (Dp) {
+        case 2: return launch_gdn<GW, 2, NRHS, 1024>(mode, h, st);
+        case 3: return launch_gdn<GW, 3, NRHS, 1024>(mode, h, st);
+        default: return launch_gdn<GW, 4, NRHS, 1024>(mode, h, st);
+      }
+    }
+  }
   switch (Dp) {
     case 2: return launch_gdn<GW, 2, NRHS>(mode, h, st);
     case 3: return launch_gdn<GW, 3, NRHS>(mode, h, st);

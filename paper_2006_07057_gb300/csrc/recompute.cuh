@@ -54,7 +54,7 @@ __device__ __forceinline__ float sum_partials(const float* p) {
 // Stored / recomputed column split of a hybrid pass for row stride ldr: the
 // first c0 columns are rebuilt in registers, the last ldr - c0 are streamed from
 // a stored block (half of the float4 columns, rounded down, are stored).
-inline int hybrid_first_stored(int ldr) {
+constexpr int hybrid_first_stored(int ldr) {
   const int q = ldr / 4;
   return 4 * (q - q / 2);
 }

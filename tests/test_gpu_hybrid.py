@@ -45,6 +45,12 @@ def gpu(lsf, p, mode, debiased):
     (4099, 131, 3, 600, 0.4, 10),
     (2000, 3000, 5, 512, 0.3, 20),
     (5003, 4001, 3, 1021, 0.1, 30),  # ragged r at the largest width, the large workload's eps
+    # r = 1024 with d <= 4 takes the update pass compiled for that stride:
+    # ragged row counts, and clouds smaller than one batch (the stored rows past
+    # the end are zero-filled in a ring slot that was never written)
+    (5003, 4001, 3, 1024, 0.1, 30),
+    (9, 3, 2, 1024, 0.5, 10),
+    (1001, 999, 4, 1024, 0.3, 20),
 ])
 def test_hybrid_matches_oracle(lsf, n, m, d, r, eps, iters, debiased):
     p = synth.small_problem(11 + n, n, m, d, r, eps, iters, weights="dirichlet")
