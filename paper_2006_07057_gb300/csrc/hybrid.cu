@@ -41,6 +41,7 @@ constexpr int kHyWarps = 4;                      // compute warps
 constexpr int kHyThreads = (kHyWarps + 1) * 32;  // + the service warp
 constexpr int kHyRB = 8;                         // rows per group per batch
 constexpr int kHySlots = 3;                      // stored-row ring depth
+constexpr int kAhead = 6;                        // row records copied this many batches ahead
 
 // FLDR = 0: any row stride and pass mode. FLDR > 0: the update pass over rows of
 // exactly FLDR columns, compiled with the row stride, the column split and the
@@ -61,6 +62,8 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
   __shared__ __align__(16) float s_red[2][NRHS][kHyRB][kHyWarps];
   __shared__ double s_res[kHyWarps + 1][2];
   __shared__ __align__(8) uint64_t s_full[kHySlots];
+  // row records in flight: [stage][row][x (D), shift, (w, old) per rhs]
+  __shared__ float s_stage[kAhead][RPB][D + 1 + 2 * NRHS];
   __shared__ int s_flag, s_last, s_skip;
   // [kHySlots][RPB][lds] stored rows; after the last batch, the per-group
   // partial r-vectors [NG][NRHS * ldr]
@@ -100,60 +103,79 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
 
   if (service) {
     // ---- service warp: row records and stored rows in, scalings out ----
+    // (the fixed-stride variant runs only without previous scalings)
     bool has_old[NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    for (int k = 0; k < NRHS; ++k) has_old[k] = FLDR == 0 && a.rhs[k].old != nullptr;
+    // Each lane serves one right-hand side (kItems <= 64 items in steps of
+    // 32 with kHyRB = 8) and sums the residual terms |old s - w| of its rows:
+    // each term in one rounding (a fused multiply-add), the sum compensated in
+    // FP32, widened once at the end (no FP64 arithmetic per batch).
+    const int kq_lane = (lane / kHyRB) % NRHS;
+    const bool lane_old = kq_lane == 0 ? has_old[0] : has_old[NRHS - 1];
+    CompSum racc;
     constexpr int kPer = (RPB + 31) / 32;  // rows per lane
-    // A row's raw record (x, shift, weights, previous scalings) is loaded two
-    // batches before its batch and only turned into the packed record (x
-    // doubled, B = -log2(e) ((2/eps)||x||^2 + shift)) when it is parked in shared
-    // memory: the loads are not waited for until then, so their latency (from
-    // HBM: the stored stream evicts the points from L2) stays off the barrier.
-    struct Raw {
-      float x[D];
-      float sh;
-      float w[NRHS];
-      float o[NRHS];
-    };
-    Raw ra[kPer], rb[kPer];
-    auto load_raw = [&](int64_t b, Raw (&r)[kPer]) {
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int64_t i = b * RPB + lane + 32 * u;
-        const bool ok = b < nbatch && i < a.n;
-#pragma unroll
-        for (int dd = 0; dd < D; ++dd) r[u].x[dd] = (ok && dd < d) ? a.X[i * d + dd] : 0.f;
-        r[u].sh = ok ? a.shift[i] : INFINITY;  // rows past the end: B = -inf, no mass
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-          r[u].w[k] = (ok && !kAx) ? a.rhs[k].w[i] : 0.f;
-          r[u].o[k] = (ok && has_old[k]) ? a.rhs[k].old[i] : 0.f;
-        }
-      }
-    };
-    auto park_raw = [&](const Raw (&r)[kPer], int bf) {
+    // A row's raw record (x, shift, weights, previous scalings) is copied
+    // into a shared-memory stage by 4-byte asynchronous copies kAhead batches
+    // before its batch, and turned into the packed record (x doubled, B =
+    // -log2(e) ((2/eps)||x||^2 + shift)) when it is parked two batches ahead:
+    // nothing waits for the copies until then, kAhead - 2 batches after their
+    // issue, so their latency (from HBM under the stored stream, which also
+    // evicts the points from L2) stays off the barrier. Each lane copies and
+    // later reads only its own rows' entries. Batch j uses stage j % kAhead,
+    // last read when batch j - kAhead was parked, kAhead - 2 batches earlier.
+    auto load_raw = [&](int64_t b, int stage) {
 #pragma unroll
       for (int u = 0; u < kPer; ++u) {
         const int rr = lane + 32 * u;
-        float rec[4 * SV];
+        if (rr < RPB) {
+          const int64_t i = b * RPB + rr;
+          const bool ok = b < nbatch && i < a.n;
+          float* st = s_stage[stage][rr];
 #pragma unroll
-        for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
-        float nrm = 0.f;
+          for (int dd = 0; dd < D; ++dd) {
+            if (ok && dd < d) cp_async_4(st + dd, a.X + i * d + dd);
+            else st[dd] = 0.f;
+          }
+          if (ok) cp_async_4(st + D, a.shift + i);
+          else st[D] = INFINITY;  // rows past the end: B = -inf, no mass
 #pragma unroll
-        for (int dd = 0; dd < D; ++dd) {
-          rec[2 * dd] = rec[2 * dd + 1] = r[u].x[dd];
-          nrm = fmaf(r[u].x[dd], r[u].x[dd], nrm);
+          for (int k = 0; k < NRHS; ++k) {
+            if (ok && !kAx) cp_async_4(st + D + 1 + 2 * k, a.rhs[k].w + i);
+            else st[D + 1 + 2 * k] = 0.f;
+            if (ok && has_old[k]) cp_async_4(st + D + 2 + 2 * k, a.rhs[k].old + i);
+            else st[D + 2 + 2 * k] = 0.f;
+          }
         }
-        rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + r[u].sh);
+      }
+      cp_async_commit();
+    };
+    auto park_raw = [&](int stage, int bf) {
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-          rec[4 * XV + 2 * k] = r[u].w[k];
-          rec[4 * XV + 2 * k + 1] = r[u].o[k];
-        }
-        if (rr < RPB)
+      for (int u = 0; u < kPer; ++u) {
+        const int rr = lane + 32 * u;
+        if (rr < RPB) {
+          const float* st = s_stage[stage][rr];
+          float rec[4 * SV];
+#pragma unroll
+          for (int q = 0; q < 4 * SV; ++q) rec[q] = 0.f;
+          float nrm = 0.f;
+#pragma unroll
+          for (int dd = 0; dd < D; ++dd) {
+            const float x = st[dd];
+            rec[2 * dd] = rec[2 * dd + 1] = x;
+            nrm = fmaf(x, x, nrm);
+          }
+          rec[2 * D] = rec[2 * D + 1] = -kLog2e * (a.two_over_eps * nrm + st[D]);
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) {
+            rec[4 * XV + 2 * k] = st[D + 1 + 2 * k];
+            rec[4 * XV + 2 * k + 1] = st[D + 2 + 2 * k];
+          }
 #pragma unroll
           for (int v = 0; v < SV; ++v)
             s_rows[bf][rr * SV + v] = make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]);
+        }
       }
     };
     // the stored rows of batch b into ring slot s (one bulk copy; lane 0)
@@ -184,16 +206,18 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
     // prime both rings with the first two batches
     for (int j = 0; j < kHySlots - 1; ++j) copy_stored(static_cast<int64_t>(blockIdx.x) + j * gridDim.x, j);
     const int64_t G = gridDim.x;
-    load_raw(blockIdx.x, ra);
-    park_raw(ra, 0);
-    load_raw(blockIdx.x + G, ra);
-    park_raw(ra, 1);
-    load_raw(blockIdx.x + 2 * G, ra);  // parked after the first batch's barrier
+    // one commit group per batch, in batch order: batches 0 .. kAhead - 1 here
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) load_raw(blockIdx.x + j * G, j);
+    cp_async_wait<kAhead - 1>();
+    park_raw(0, 0);
+    cp_async_wait<kAhead - 2>();
+    park_raw(1, 1);
     __syncthreads();
-    // one batch: the raw records of batch b + 3G load into `ld` (waited for two
-    // batches later), the records of batch b + 2G (in `pk`) are parked
-    auto step = [&](int64_t b, int it, Raw (&ld)[kPer], const Raw (&pk)[kPer]) {
-      load_raw(b + 3 * G, ld);
+    // one batch (the it-th of this CTA): the records of batch it + kAhead start
+    // to load, those of batch it + 2 (the group kAhead - 2 groups back) are parked
+    auto step = [&](int64_t b, int it) {
+      load_raw(b + kAhead * G, it % kAhead);
       __syncthreads();
       // slot (it + 2) % 3 was last read in the previous batch, before this barrier
       copy_stored(b + (kHySlots - 1) * G, (it + kHySlots - 1) % kHySlots);
@@ -209,40 +233,27 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
             if (i < a.n) {
               const float s = sum_partials<GW>(&s_red[it & 1][kq][qq][gg * GW]);
               const float4 wo = rows[(gg * kHyRB + qq) * SV + XV];
-              if (NRHS == 1 || kq == 0) {
-                if (has_old[0])
-                  res[0] += fabs(static_cast<double>(wo.y) * static_cast<double>(s) - static_cast<double>(wo.x));
-                if (kUpd) {
-                  const float sc = wo.x * __frcp_rn(s);
-                  a.rhs[0].out[i] = sc;
-                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
-                }
-              } else {
-                if (has_old[NRHS - 1])
-                  res[NRHS - 1] +=
-                      fabs(static_cast<double>(wo.w) * static_cast<double>(s) - static_cast<double>(wo.z));
-                if (kUpd) {
-                  const float sc = wo.z * __frcp_rn(s);
-                  a.rhs[NRHS - 1].out[i] = sc;
-                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
-                }
+              const bool k0 = NRHS == 1 || kq == 0;
+              const float w = k0 ? wo.x : wo.z, o = k0 ? wo.y : wo.w;
+              if (lane_old) racc.add(fabsf(fmaf(o, s, -w)));
+              if (kUpd) {
+                const float sc = w * __frcp_rn(s);
+                (k0 ? a.rhs[0].out : a.rhs[NRHS - 1].out)[i] = sc;
+                if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
               }
             }
           }
         }
       }
-      park_raw(pk, (it + 2) % 3);
+      cp_async_wait<kAhead - 2>();
+      park_raw((it + 2) % kAhead, (it + 2) % 3);
     };
     int it = 0;
-    for (int64_t b = blockIdx.x; b < nbatch;) {
-      step(b, it, rb, ra);
-      b += G;
-      ++it;
-      if (b >= nbatch) break;
-      step(b, it, ra, rb);
-      b += G;
-      ++it;
-    }
+    for (int64_t b = blockIdx.x; b < nbatch; b += G, ++it) step(b, it);
+    cp_async_wait<0>();  // copies for batches past the end (none issued) and stores settle
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k)
+      res[k] = kq_lane == k ? static_cast<double>(racc.s) + static_cast<double>(racc.c) : 0.0;
     // drain: every issued copy must have landed before the shared memory is
     // reused for the partials and before the CTA exits (the compute warps have
     // waited on each of them unless a wait ran out)
@@ -293,13 +304,12 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();  // the rings are primed
-    // batch it uses record buffer and ring slot it % 3 (both three deep) and
-    // the ring slot's mbarrier phase (it / 3) & 1, kept as running counters
-    int it = 0, slot = 0;
+    // batch it uses record buffer it % 3, ring slot it % kHySlots and that
+    // slot's mbarrier phase (it / kHySlots) & 1, kept as running counters
+    int it = 0, slot = 0, rbuf = 0;
     uint32_t phase = 0;
-    static_assert(kHySlots == 3, "record buffers and ring slots advance together");
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
-      const float4* rows = s_rows[slot];
+      const float4* rows = s_rows[rbuf];
       const float4* srow = reinterpret_cast<const float4*>(s_ring + (static_cast<size_t>(slot) * RPB + g * kHyRB) * lds) + tg;
       const int ldq = lds >> 2;  // float4s per stored row
       // the recomputed entries first: they need only the row records, so the
@@ -328,6 +338,7 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
         slot = 0;
         phase ^= 1u;
       }
+      if (++rbuf == 3) rbuf = 0;
       float dots[NRHS][kHyRB];
 #pragma unroll
       for (int q = 0; q < kHyRB; ++q) {
@@ -474,8 +485,11 @@ int launch_gdn(int mode, const HybridArgs& h, cudaStream_t st) {
 template <int GW, int NRHS>
 int launch_gn(int mode, const HybridArgs& h, int Dp, cudaStream_t st) {
   if constexpr (GW == 4) {
-    // the update pass at r = 1024, compiled for that stride
-    if (mode == kPassUpdate && h.rc.ldr == 1024 && Dp <= 4) {
+    // the update pass at r = 1024 without residual terms (the solvers' loop
+    // passes), compiled for that stride
+    bool old = false;
+    for (int k = 0; k < NRHS; ++k) old = old || h.rc.rhs[k].old != nullptr;
+    if (mode == kPassUpdate && !old && h.rc.ldr == 1024 && Dp <= 4) {
       switch (Dp) {
         case 2: return launch_gdn<GW, 2, NRHS, 1024>(mode, h, st);
         case 3: return launch_gdn<GW, 3, NRHS, 1024>(mode, h, st);
