@@ -346,10 +346,10 @@ __device__ __forceinline__ void hybrid_body(const HybridArgs& h, const int mode_
         const float2 fs0 = make_float2(fs.x, fs.y), fs1 = make_float2(fs.z, fs.w);
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
-          const float2 P = __ffma2_rn(F[q][0], t2[k][0], __fmul2_rn(F[q][1], t2[k][1]));
-          const float2 Q = __ffma2_rn(fs0, make_float2(ts[k].x, ts[k].y),
-                                      __fmul2_rn(fs1, make_float2(ts[k].z, ts[k].w)));
-          const float2 S = __fadd2_rn(P, Q);
+          float2 S = __fmul2_rn(F[q][0], t2[k][0]);
+          S = __ffma2_rn(F[q][1], t2[k][1], S);
+          S = __ffma2_rn(fs0, make_float2(ts[k].x, ts[k].y), S);
+          S = __ffma2_rn(fs1, make_float2(ts[k].z, ts[k].w), S);
           dots[k][q] = S.x + S.y;
         }
       }

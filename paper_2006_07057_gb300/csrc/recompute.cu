@@ -88,6 +88,13 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     bool has_old[NRHS];
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    // Each lane serves one right-hand side (items in steps of 32 with kRcRB = 8)
+    // and sums the residual terms |old s - w| of its rows: each term in one
+    // rounding (a fused multiply-add), the sum compensated in FP32, widened once
+    // at the end (no FP64 arithmetic per batch).
+    const int kq_lane = (lane / kRcRB) % NRHS;
+    const bool lane_old = kq_lane == 0 ? has_old[0] : has_old[NRHS - 1];
+    CompSum racc;
     constexpr int kPer = (RPB + 31) / 32;  // rows per lane
     // A row's raw record (x, shift, weights, previous scalings) is loaded two
     // batches before its batch and only turned into the packed record (x
@@ -168,24 +175,13 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
             if (i < a.n) {
               const float s = sum_partials<GW>(&s_red[it & 1][kq][qq][gg * GW]);
               const float4 wo = rows[(gg * kRcRB + qq) * SV + XV];
-              // compile-time rhs index on each side of the branch
-              if (NRHS == 1 || kq == 0) {
-                if (has_old[0])
-                  res[0] += fabs(static_cast<double>(wo.y) * static_cast<double>(s) - static_cast<double>(wo.x));
-                if (kUpd) {
-                  const float sc = wo.x * __frcp_rn(s);
-                  a.rhs[0].out[i] = sc;
-                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
-                }
-              } else {
-                if (has_old[NRHS - 1])
-                  res[NRHS - 1] +=
-                      fabs(static_cast<double>(wo.w) * static_cast<double>(s) - static_cast<double>(wo.z));
-                if (kUpd) {
-                  const float sc = wo.z * __frcp_rn(s);
-                  a.rhs[NRHS - 1].out[i] = sc;
-                  if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
-                }
+              const bool k0 = NRHS == 1 || kq == 0;
+              const float w = k0 ? wo.x : wo.z, o = k0 ? wo.y : wo.w;
+              if (lane_old) racc.add(fabsf(fmaf(o, s, -w)));
+              if (kUpd) {
+                const float sc = w * __frcp_rn(s);
+                (k0 ? a.rhs[0].out : a.rhs[NRHS - 1].out)[i] = sc;
+                if (!(s > 0.f) || !isfinite(sc)) flag |= LSF_ERR_NONFINITE;
               }
             }
           }
@@ -205,6 +201,9 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
       b += G;
       ++it;
     }
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k)
+      res[k] = kq_lane == k ? static_cast<double>(racc.s) + static_cast<double>(racc.c) : 0.0;
   } else {
     // ---- compute warps ----
     // per-column constants, as column pairs (col0, col0 + 1), (col0 + 2, col0 + 3)
