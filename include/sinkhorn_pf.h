@@ -743,6 +743,21 @@ int lsf_profile_enable(int on);
 int lsf_profile_read(int kernel_class, double* total_ms, int64_t* launches, double* bytes);
 
 /*
+ * NVTX ranges on the host timeline, for a profiler that records them (ncu
+ * --nvtx, Nsight Systems). level 0: none. Level 1 (the default): one range per
+ * call of the main entry points, named after the call (the features, solve,
+ * divergence and gradient calls, the whole-path, batched, multi-pair and
+ * accelerated solves). Level 2: also one range around every kernel launch, named
+ * after its lsf_kernel_class ("pass", "pass_hybrid", "features", ...). Without a
+ * profiler attached a range costs a few nanoseconds of host time. previous
+ * (host, may be NULL) receives the level in force before the call. Errors:
+ * LSF_ERR_ARG for a level outside 0..2 (the level is then unchanged).
+ * Process-wide; set it once, before the work, not concurrently with it.
+ * (Measurement plumbing; the paper has no counterpart.)
+ */
+int lsf_set_tracing(int level, int* previous);
+
+/*
  * Measured issue rates of the pipes the recompute and hybrid passes are bound by,
  * per SM clock per SM (not a paper quantity: the denominators of their ALU
  * roofline). One CTA of 1024 threads per SM runs independent chains of one

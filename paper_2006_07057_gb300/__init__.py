@@ -579,6 +579,14 @@ def lsf_profile_enable(on: bool) -> None:
     check(lib().lsf_profile_enable(int(bool(on))), "lsf_profile_enable")
 
 
+def lsf_set_tracing(level: int) -> int:
+    """NVTX ranges for a profiler: 0 none, 1 entry points (default), 2 also every
+    kernel launch by class. Returns the previous level."""
+    prev = ctypes.c_int()
+    check(lib().lsf_set_tracing(int(level), ctypes.byref(prev)), "lsf_set_tracing")
+    return prev.value
+
+
 def lsf_profile_read(kernel_class: int) -> tuple[float, int, float]:
     ms = ctypes.c_double()
     n = ctypes.c_int64()

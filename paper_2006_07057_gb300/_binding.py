@@ -183,6 +183,7 @@ _SIGNATURES = {
     "lsf_set_small_solver": (c_int, [c_int, ctypes.c_int64]),
     "lsf_get_pass_tiling": (c_int, [_P(c_int), _P(c_int)]),
     "lsf_profile_enable": (c_int, [c_int]),
+    "lsf_set_tracing": (c_int, [c_int, c_void_p]),
     "lsf_profile_read": (c_int, [c_int, _P(c_double), _P(c_int64), _P(c_double)]),
     "lsf_probe_pipe_rates": (c_int, [_P(c_double), _P(c_double), _P(c_double), c_void_p]),
     "lsf_launch_count": (c_int64, []),

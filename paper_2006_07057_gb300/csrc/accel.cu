@@ -408,6 +408,7 @@ int lsf_accel_workspace_bytes(int64_t n, int64_t m, int ldr, size_t* bytes) {
 int lsf_solve_accelerated(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters,
                           double L0, const lsf_scalings* out, lsf_result* result, lsf_accel_info* info,
                           void* workspace, size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_solve_accelerated");
   return accel_solve(theta, x, y, iters, L0, out, result, info, workspace, ws_bytes,
                      static_cast<cudaStream_t>(stream));
 }

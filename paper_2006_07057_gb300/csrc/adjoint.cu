@@ -469,6 +469,7 @@ extern "C" int lsf_gradient(const lsf_theta* th, const lsf_cloud* x, const lsf_c
                             const lsf_scalings* s_xy, const lsf_scalings* s_xx,
                             const lsf_scalings* s_yy, const lsf_result* result, int debiased,
                             int mode, float* gX, float* gY, float* ga, float* gb, void* stream) {
+  lsf::TraceRange trace_range("lsf_gradient");
   if (!th || !x || !y || !s_xy || !result) return fail(LSF_ERR_ARG, "lsf_gradient: NULL argument");
   if (debiased && (!s_xx || !s_yy))
     return fail(LSF_ERR_ARG, "lsf_gradient: the debiased gradient needs s_xx and s_yy");
@@ -534,6 +535,7 @@ extern "C" int lsf_anchor_gradient(const lsf_theta* th, double q, const lsf_clou
                                    const lsf_scalings* s_xx, const lsf_scalings* s_yy, int debiased,
                                    int mode, double scale, float* gU, void* workspace,
                                    size_t workspace_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_anchor_gradient");
   if (!th || !x || !y || !s_xy || !gU) return fail(LSF_ERR_ARG, "lsf_anchor_gradient: NULL argument");
   if (debiased && (!s_xx || !s_yy))
     return fail(LSF_ERR_ARG, "lsf_anchor_gradient: the debiased gradient needs s_xx and s_yy");

@@ -709,6 +709,7 @@ extern "C" int lsf_batch_plan(const lsf_batch_problem* probs, int count, int ldr
 }
 
 extern "C" int lsf_solve_batched(const lsf_batch_info* info, void* plan, int iters, void* stream) {
+  lsf::TraceRange trace_range("lsf_solve_batched");
   if (!info || !plan) return fail(LSF_ERR_ARG, "lsf_solve_batched: NULL argument");
   if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
   cudaStream_t st = as_stream(stream);

@@ -25,7 +25,8 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info();
 
-// Every launch goes through this so that it is counted and (optionally) timed.
+// Every launch goes through this so that it is counted and (optionally) timed
+// and named on the host timeline (tracing level 2).
 struct LaunchScope {
   LaunchScope(cudaStream_t s, int kernel_class, double bytes);
   ~LaunchScope();
@@ -33,6 +34,14 @@ struct LaunchScope {
   int cls;
   double bytes;
   int slot;
+  bool traced;
+};
+
+// An NVTX range named `name` for the life of the object (tracing level >= 1).
+struct TraceRange {
+  explicit TraceRange(const char* name);
+  ~TraceRange();
+  bool on;
 };
 
 int check_launch(const char* what);

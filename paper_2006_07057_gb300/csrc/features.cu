@@ -540,11 +540,13 @@ int lsf_anchors(const float* Z, int r, int d, double q, double sigma, double eps
 
 int lsf_features(const float* X, int64_t n, const lsf_theta* theta, float* F, float* shift,
                  float* spread, void* stream) {
+  lsf::TraceRange trace_range("lsf_features");
   return launch_features<1>(X, n, theta, F, shift, spread, as_stream(stream));
 }
 
 int lsf_log_features(const float* X, int64_t n, const lsf_theta* theta, float* L, float* shift,
                      float* spread, void* stream) {
+  lsf::TraceRange trace_range("lsf_log_features");
   return launch_features<2>(X, n, theta, L, shift, spread, as_stream(stream));
 }
 
@@ -563,6 +565,7 @@ int lsf_hybrid_columns(int ldr, int* c0) {
 
 int lsf_hybrid_features(const float* X, int64_t n, const lsf_theta* theta, float* Fs, float* shift,
                         float* spread, void* stream) {
+  lsf::TraceRange trace_range("lsf_hybrid_features");
   if (!theta) return fail(LSF_ERR_ARG, "lsf_hybrid_features: NULL theta");
   int c0 = 0;
   const int rc = lsf_hybrid_columns(theta->ldr, &c0);
@@ -582,11 +585,13 @@ int lsf_arccos_anchors(const float* Z, int r, int d, double sigma, float* U, flo
 
 int lsf_arccos_features(const float* X, int64_t n, const lsf_arccos* th, float* F, float* shift,
                         float* spread, void* stream) {
+  lsf::TraceRange trace_range("lsf_arccos_features");
   return launch_arccos<1>(X, n, th, F, shift, spread, as_stream(stream));
 }
 
 int lsf_arccos_log_features(const float* X, int64_t n, const lsf_arccos* th, float* L, float* shift,
                             float* spread, void* stream) {
+  lsf::TraceRange trace_range("lsf_arccos_log_features");
   return launch_arccos<2>(X, n, th, L, shift, spread, as_stream(stream));
 }
 

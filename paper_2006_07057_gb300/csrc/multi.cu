@@ -1038,6 +1038,7 @@ int lsf_multi_workspace_bytes(int ldr2, int k, size_t* bytes) {
 int lsf_solve_multi(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* x,
                     const lsf_multi_cloud* y, int k, int iters, const lsf_multi_scalings* out,
                     lsf_result* results, void* workspace, size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_solve_multi");
   LSF_TRY(check_theta(theta));
   LSF_TRY(check_multi_shape(ldr2, k));
   if (theta->r > ldr2) return fail(LSF_ERR_ARG, "multi solve: r exceeds ldr2");
@@ -1127,6 +1128,7 @@ int lsf_multi_debiased(const lsf_theta* theta, int ldr2, const lsf_multi_cloud* 
                        const lsf_multi_scalings* s_xx, const lsf_multi_scalings* s_yy,
                        lsf_result* results, double* wbar, void* workspace, size_t ws_bytes,
                        void* stream) {
+  lsf::TraceRange trace_range("lsf_multi_debiased");
   if (!x || !y || !results) return fail(LSF_ERR_ARG, "lsf_multi_debiased: NULL argument");
   if (k < 1 || k > 32) return fail(LSF_ERR_UNSUPPORTED, "lsf_multi_debiased: k must be 1..32");
   LSF_TRY(lsf_solve_multi(theta, ldr2, x, y, k, iters, s_xy, results, workspace, ws_bytes, stream));

@@ -156,6 +156,7 @@ int lsf_pipeline_bytes(const lsf_pipeline* p, size_t* bytes) {
 int lsf_pipeline_run(const lsf_pipeline* p, const float* X, const float* Y, const float* a,
                      const float* b, const float* Z, void* arena, size_t arena_bytes,
                      lsf_pipeline_out* out, void* stream) {
+  lsf::TraceRange trace_range("lsf_pipeline_run");
   Layout L{};
   LSF_TRY(layout(p, &L));
   if (!X || !Y || !a || !b || !Z || (!out && p->iters > 0))
@@ -245,6 +246,7 @@ int lsf_pipeline_layout(const lsf_pipeline* p, void* arena, lsf_pipeline_views* 
 }
 
 int lsf_pipeline_finish(const lsf_pipeline* p, void* arena, lsf_pipeline_out* out, void* stream) {
+  lsf::TraceRange trace_range("lsf_pipeline_finish");
   Layout L{};
   LSF_TRY(layout(p, &L));
   if (!arena || !out) return fail(LSF_ERR_ARG, "lsf_pipeline_finish: NULL argument");

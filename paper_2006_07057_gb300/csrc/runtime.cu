@@ -9,6 +9,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "pass.cuh"
 
@@ -77,8 +79,26 @@ const DeviceInfo& device_info() {
   return info;
 }
 
+namespace {
+std::atomic<int> g_trace_level{1};
+const char* const kClassNames[LSF_KERNEL_NCLASSES] = {
+    "pass", "pass_recompute", "features", "other", "pass_log", "batched",
+    "adjoint", "small", "pass_multi", "pass_hybrid"};
+}  // namespace
+
+TraceRange::TraceRange(const char* name) : on(g_trace_level.load(std::memory_order_relaxed) >= 1) {
+  if (on) nvtxRangePushA(name);
+}
+
+TraceRange::~TraceRange() {
+  if (on) nvtxRangePop();
+}
+
 LaunchScope::LaunchScope(cudaStream_t s, int kernel_class, double nbytes)
-    : stream(s), cls(kernel_class), bytes(nbytes), slot(-1) {
+    : stream(s), cls(kernel_class), bytes(nbytes), slot(-1),
+      traced(g_trace_level.load(std::memory_order_relaxed) >= 2 && kernel_class >= 0 &&
+             kernel_class < LSF_KERNEL_NCLASSES) {
+  if (traced) nvtxRangePushA(kClassNames[kernel_class]);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -90,6 +110,7 @@ LaunchScope::LaunchScope(cudaStream_t s, int kernel_class, double nbytes)
 }
 
 LaunchScope::~LaunchScope() {
+  if (traced) nvtxRangePop();
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (slot < static_cast<int>(g_prof.size())) cudaEventRecord(g_prof[slot].stop, stream);
@@ -192,6 +213,13 @@ int lsf_workspace_bytes(int ldr, size_t* bytes) {
   if (ldr < 4 || ldr % 4 != 0 || ldr > 1024)
     return fail(LSF_ERR_UNSUPPORTED, "ldr must be a multiple of 4 in [4, 1024]");
   *bytes = workspace_bytes(ldr);
+  return LSF_OK;
+}
+
+int lsf_set_tracing(int level, int* previous) {
+  if (level < 0 || level > 2) return lsf::fail(LSF_ERR_ARG, "tracing level must be 0, 1 or 2");
+  const int prev = lsf::g_trace_level.exchange(level);
+  if (previous) *previous = prev;
   return LSF_OK;
 }
 

@@ -366,6 +366,7 @@ extern "C" {
 int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int iters, int mode,
               const lsf_scalings* out, lsf_result* result, void* workspace, size_t ws_bytes,
               void* stream) {
+  lsf::TraceRange trace_range("lsf_solve");
   LSF_TRY(check_theta(theta));
   if (mode == LSF_MODE_AUTO) {
     if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");
@@ -417,6 +418,7 @@ int lsf_divergence(const lsf_theta* theta, int nterms, const lsf_cloud* const* x
                    const lsf_cloud* const* ys, const lsf_scalings* const* s,
                    lsf_result* const* result, const double* coef, double* combined, int mode,
                    void* workspace, size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_divergence");
   LSF_TRY(check_theta(theta));
   if (nterms < 1 || nterms > 3) return fail(LSF_ERR_ARG, "nterms must be 1..3");
   if (!xs || !ys || !s || !result) return fail(LSF_ERR_ARG, "lsf_divergence: NULL array");
@@ -439,6 +441,7 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  int mode, const lsf_scalings* s_xy, const lsf_scalings* s_xx,
                  const lsf_scalings* s_yy, lsf_result* result, double* wbar, void* workspace,
                  size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_debiased");
   LSF_TRY(check_theta(theta));
   if (mode == LSF_MODE_AUTO) {
     if (iters < 1) return fail(LSF_ERR_ARG, "iters must be >= 1");

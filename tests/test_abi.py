@@ -81,3 +81,14 @@ def test_hybrid_column_split_is_host_only():
         with pytest.raises(B.LsfError) as e:
             lsf.lsf_hybrid_columns(bad)
         assert e.value.status == B.LSF_ERR_UNSUPPORTED
+
+
+def test_tracing_level_switch():
+    # host-only: the level is a process-wide switch read at each entry point
+    assert lsf.lsf_set_tracing(2) == 1          # the default is entry-point ranges
+    assert lsf.lsf_set_tracing(0) == 2
+    for bad in (-1, 3):
+        with pytest.raises(B.LsfError) as e:
+            lsf.lsf_set_tracing(bad)
+        assert e.value.status == B.LSF_ERR_ARG
+    assert lsf.lsf_set_tracing(1) == 0
