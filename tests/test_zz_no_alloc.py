@@ -11,7 +11,8 @@ absolute).
 The cases cover the multi-launch streamed passes, which use every region of the
 scratch (per-CTA partial r-vectors, group partials, residual partials, arrival
 counters): the stored pass with the single-launch small-problem solver switched
-off, the recompute pass, and the log-domain pass, plus the small-problem solver
+off, the recompute pass, the log-domain pass and the hybrid pass (at r = 256 and
+at r = 1024, where its fixed-stride variant runs), plus the small-problem solver
 itself. Running two solves in a row checks that the array's leftover contents
 from one call do not leak into the next.
 
@@ -28,12 +29,13 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode,small", [("stored", 0), ("recompute", 1), ("log", 1), ("stored", 1)])
-def test_noalloc_solve_matches_workspace_solve_twice(mode, small):
+@pytest.mark.parametrize("mode,small,r", [("stored", 0, 256), ("recompute", 1, 256), ("log", 1, 256),
+                                          ("stored", 1, 256), ("hybrid", 1, 256), ("hybrid", 1, 1024)])
+def test_noalloc_solve_matches_workspace_solve_twice(mode, small, r):
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     import paper_2006_07057_gb300 as lsf
-    p = synth.small_problem(21, 3001, 2503, 3, 256, 0.3, 30, weights="dirichlet")
+    p = synth.small_problem(21, 3001, 2503, 3, r, 0.3, 30, weights="dirichlet")
     t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k))).cuda() for k in "XYabZ"}
     prob = lsf.SinkhornProblem(t["X"], t["Y"], t["a"], t["b"], t["Z"], p.eps, mode=mode)
     dev = t["X"].device
