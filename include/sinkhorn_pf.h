@@ -297,6 +297,38 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
                  void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Alg. 1 (Sec. 2) with its stopping rule: as lsf_solve, but the loop ends at the
+ * first check where the residual ||u o (K v) - a||_1 (after the v-half) is at
+ * most tol. The residual is evaluated every check_every iterations (1: after
+ * every iteration, as Alg. 1 states it; a larger interval trades up to
+ * check_every - 1 extra iterations for fewer residual reads of F), and after
+ * max_iters iterations at the latest. result->iters receives the iterations run
+ * and result->residual the last residual evaluated (above tol if max_iters was
+ * reached first). Every check synchronises the stream (the residual is read on
+ * the host), so this call blocks and is not for stream capture; the passes are
+ * those of lsf_solve (the single-launch small-problem solver is not used).
+ * Errors: LSF_ERR_ARG for max_iters < 1, tol < 0 or NaN, check_every < 1; then as
+ * lsf_solve. A run that reports LSF_ERR_NONFINITE stops at that check.
+ */
+int lsf_solve_tol(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int max_iters,
+                  double tol, int check_every, int mode, const lsf_scalings* out,
+                  lsf_result* result, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Eq. (2) with Alg. 1's stopping rule on each of its three terms: as
+ * lsf_debiased, but each term (xy, xx, yy) stops at the first check (every
+ * check_every iterations, and at max_iters) where its own residual is at most
+ * tol; the lock-step passes then carry only the terms still running. Each
+ * result record gets its own iteration count and last residual; W and W_bar are
+ * formed from every term's final scalings. Synchronises the stream at every
+ * check, as lsf_solve_tol. Errors as lsf_solve_tol.
+ */
+int lsf_debiased_tol(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int max_iters,
+                     double tol, int check_every, int mode, const lsf_scalings* s_xy,
+                     const lsf_scalings* s_xx, const lsf_scalings* s_yy, lsf_result* result,
+                     double* wbar, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * lsf_solve for callers that cannot allocate device memory. The paper has no
  * counterpart; this exists for the library's users.
  *

@@ -20,7 +20,9 @@ What it computes, in the paper's order and notation (Scetbon & Cuturi,
 * Sec. 3.1: K_theta = xi^T zeta (here xi is stored point-major, n x r).
 * Alg. 1 (Sec. 2): Sinkhorn scaling updates, run here as u <- a/(K v),
   v <- b/(K^T u) from v = 1 (one iteration = one u-half then one v-half); the
-  reported residual is ||u o (K v) - a||_1 after the last v-half.
+  reported residual is ||u o (K v) - a||_1 after the last v-half. With its
+  stopping rule (``sinkhorn_log_tol``) the loop ends at the first test where
+  that residual is at most the tolerance, tested every k iterations.
 * Eq. (6): W_hat = eps (a^T log u + b^T log v).
 * App. A.2: accelerated Sinkhorn, read as the accelerated alternating
   minimisation the appendix cites (its listing is garbled; see
@@ -260,6 +262,37 @@ def sinkhorn_scaled(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray
     return {"logu": logu, "logv": logv, "residual": residual}
 
 
+def sinkhorn_log_tol(Lx: np.ndarray, Ly: np.ndarray, a: np.ndarray, b: np.ndarray,
+                     max_iters: int, tol: float, check_every: int = 1) -> dict:
+    """Alg. 1 with its stopping rule (Sec. 2), in the log domain, FP64.
+
+    The iterates of ``sinkhorn_log``; the loop ends at the first check where the
+    row residual ||u o (K v) - a||_1 after the v-half is at most ``tol``.  The
+    test is made after every ``check_every`` iterations and after
+    ``max_iters`` at the latest (check_every = 1 is the algorithm as printed).
+    Returns log u, log v, the last residual evaluated and the iterations run.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    loga, logb = np.log(a), np.log(b)
+    logu = np.zeros(Lx.shape[0])
+    logv = np.zeros(Ly.shape[0])
+    done = 0
+    residual = math.inf
+    while done < max_iters:
+        for _ in range(min(check_every, max_iters - done)):
+            logKv, _ = _log_Kv(Lx, Ly, logv)
+            logu = loga - logKv
+            logKtu, _ = _log_Kv(Ly, Lx, logu)
+            logv = logb - logKtu
+            done += 1
+        logKv, _ = _log_Kv(Lx, Ly, logv)
+        residual = float(np.abs(np.exp(logu + logKv) - a).sum())
+        if residual <= tol:
+            break
+    return {"logu": logu, "logv": logv, "residual": residual, "iters": done}
+
+
 def dual_phi(Lx, Ly, a, b, eta1, eta2) -> float:
     """phi(eta) = log <e^eta1, K e^eta2> - <eta1, a> - <eta2, b> (App. A.2, the dual
     of Eq. (5) in the coordinates eta = (alpha, beta)/eps, sign flipped so that it
@@ -465,6 +498,28 @@ def divergence(X, Y, a, b, Z=None, eps=None, iters=100, theta: Theta | None = No
         out["W_xx"] = dual_estimate(a, a, sxx["logu"], sxx["logv"], eps)
         out["W_yy"] = dual_estimate(b, b, syy["logu"], syy["logv"], eps)
         out["res_xx"], out["res_yy"] = sxx["residual"], syy["residual"]
+        out["W_bar"] = out["W_xy"] - 0.5 * (out["W_xx"] + out["W_yy"])
+    return out
+
+
+def divergence_tol(X, Y, a, b, Z, eps, max_iters, tol, check_every=1,
+                   debiased: bool = True) -> dict:
+    """``divergence`` with Alg. 1's stopping rule on each term of Eq. (2): every
+    term runs ``sinkhorn_log_tol`` on its own (its own iteration count)."""
+    theta = make_theta(X, Y, Z, eps)
+    Lx = log_features(X, theta.U, eps, theta.q)
+    Ly = log_features(Y, theta.U, eps, theta.q)
+    out = {"theta": theta}
+    terms = [("xy", Lx, Ly, a, b)]
+    if debiased:
+        terms += [("xx", Lx, Lx, a, a), ("yy", Ly, Ly, b, b)]
+    for name, L1, L2, w1, w2 in terms:
+        st = sinkhorn_log_tol(L1, L2, w1, w2, max_iters, tol, check_every)
+        out[name] = st
+        out["W_" + name] = dual_estimate(w1, w2, st["logu"], st["logv"], eps)
+        out["res_" + name] = st["residual"]
+        out["iters_" + name] = st["iters"]
+    if debiased:
         out["W_bar"] = out["W_xy"] - 0.5 * (out["W_xx"] + out["W_yy"])
     return out
 

@@ -502,6 +502,30 @@ def lsf_debiased(theta: Theta, x: Cloud, y: Cloud, iters: int, mode: str, s_xy: 
                              _stream(stream)), "lsf_debiased")
 
 
+def lsf_solve_tol(theta: Theta, x: Cloud, y: Cloud, max_iters: int, tol: float, check_every: int,
+                  mode: str, out: Scalings, result, workspace, stream=None):
+    """Alg. 1 until the residual is at most tol (checked every check_every
+    iterations); synchronises the stream at every check."""
+    th, cx, cy, so = theta.as_c(), x.as_c(), y.as_c(), out.as_c()
+    check(lib().lsf_solve_tol(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy), int(max_iters),
+                              float(tol), int(check_every), MODES[mode], ctypes.byref(so),
+                              _p(result), _p(workspace), workspace.numel(), _stream(stream)),
+          "lsf_solve_tol")
+
+
+def lsf_debiased_tol(theta: Theta, x: Cloud, y: Cloud, max_iters: int, tol: float, check_every: int,
+                     mode: str, s_xy: Scalings, s_xx: Scalings, s_yy: Scalings, result, wbar,
+                     workspace, stream=None):
+    """Eq. (2) with each term stopped by Alg. 1's rule; synchronises at every check."""
+    th, cx, cy = theta.as_c(), x.as_c(), y.as_c()
+    a, b, c = s_xy.as_c(), s_xx.as_c(), s_yy.as_c()
+    check(lib().lsf_debiased_tol(ctypes.byref(th), ctypes.byref(cx), ctypes.byref(cy),
+                                 int(max_iters), float(tol), int(check_every), MODES[mode],
+                                 ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _p(result),
+                                 _p(wbar), _p(workspace), workspace.numel(), _stream(stream)),
+          "lsf_debiased_tol")
+
+
 def lsf_divergence(theta: Theta, xs, ys, ss, results, coef=None, combined=None, workspace=None,
                    stream=None, mode: str = "stored"):
     k = len(xs)
@@ -732,16 +756,33 @@ class SinkhornProblem:
     def result_view(self, k: int) -> torch.Tensor:
         return self.results[k * RESULT_BYTES:(k + 1) * RESULT_BYTES]
 
-    def run(self, iters: int, debiased: bool = True) -> None:
+    def run(self, iters: int, debiased: bool = True, tol: float | None = None,
+            check_every: int = 10) -> None:
         """Launch the solve (and Eq. (6)/(2) reductions) on the stream.
 
         No host synchronisation, except in ``auto`` mode, where the library reads
         the spread and the status back to pick the domain (``used_mode``).
+        With ``tol``, Alg. 1's stopping rule: each solve ends at the first check
+        (every ``check_every`` iterations, ``iters`` at most) where its residual
+        is at most ``tol``; each check reads the residual on the host, and the
+        iterations run are in each result record (``values()["iters_*"]``).
         """
         self.debiased = bool(debiased)
         self.iters = iters
         self._used = None
-        self._launch(iters)
+        if tol is None:
+            self._launch(iters)
+            return
+        if self.debiased:
+            lsf_debiased_tol(self.theta, self.x, self.y, iters, tol, check_every, self.mode,
+                             self.s_xy, self.s_xx, self.s_yy, self.results, self.wbar,
+                             self.workspace, self.stream)
+        else:
+            r0 = self.result_view(0)
+            lsf_solve_tol(self.theta, self.x, self.y, iters, tol, check_every, self.mode, self.s_xy,
+                          r0, self.workspace, self.stream)
+            lsf_divergence(self.theta, [self.x], [self.y], [self.s_xy], [r0], [1.0], self.wbar,
+                           self.workspace, self.stream, mode=self.used_mode)
 
     @property
     def used_mode(self) -> str:
@@ -796,11 +837,13 @@ class SinkhornProblem:
         """Host copy of the results of the last run (synchronises)."""
         recs = read_results(self.results)
         out = {"W_xy": recs[0]["W"], "res_xy": recs[0]["residual"], "status": recs[0]["status"],
-               "iters": recs[0]["iters"], "records": recs, "mode": MODE_NAMES[recs[0]["mode"]]}
+               "iters": recs[0]["iters"], "iters_xy": recs[0]["iters"], "records": recs,
+               "mode": MODE_NAMES[recs[0]["mode"]]}
         out["W"] = float(self.wbar.item())
         if self.debiased:
             out.update(W_xx=recs[1]["W"], W_yy=recs[2]["W"], res_xx=recs[1]["residual"],
-                       res_yy=recs[2]["residual"], W_bar=out["W"])
+                       res_yy=recs[2]["residual"], W_bar=out["W"], iters_xx=recs[1]["iters"],
+                       iters_yy=recs[2]["iters"])
         return out
 
     def log_potentials(self, which: str = "xy"):

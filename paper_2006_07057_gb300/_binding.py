@@ -168,6 +168,11 @@ _SIGNATURES = {
     "lsf_debiased": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_int,
                              _P(LsfScalings), _P(LsfScalings), _P(LsfScalings), c_void_p,
                              c_void_p, c_void_p, c_size_t, c_void_p]),
+    "lsf_solve_tol": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double, c_int,
+                              c_int, _P(LsfScalings), c_void_p, c_void_p, c_size_t, c_void_p]),
+    "lsf_debiased_tol": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), c_int, c_double, c_int,
+                                 c_int, _P(LsfScalings), _P(LsfScalings), _P(LsfScalings),
+                                 c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsf_gradient": (c_int, [_P(LsfTheta), _P(LsfCloud), _P(LsfCloud), _P(LsfScalings),
                              _P(LsfScalings), _P(LsfScalings), c_void_p, c_int, c_int,
                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -357,6 +357,97 @@ int launch_divergence(const lsf_theta* th, int nterms, const lsf_cloud* const* x
   return check_launch("divergence_kernel");
 }
 
+// `count` iterations of Alg. 1 on one pair: u <- a/(K v) then v <- b/(K^T u).
+int single_iterations(int mode, const lsf_theta* th, const lsf_cloud* x, const lsf_cloud* y,
+                      const lsf_scalings* out, int count, const Workspace& ws, int* status,
+                      cudaStream_t st) {
+  for (int it = 0; it < count; ++it) {
+    PassRhs ru{};
+    ru.t_in = out->t_v; ru.w = x->w; ru.out = out->u; ru.t_out = out->t_u;
+    LSF_TRY(run_pass(mode, th, x, kPassUpdate, 1, &ru, ws, status, st));
+    PassRhs rv{};
+    rv.t_in = out->t_u; rv.w = y->w; rv.out = out->v; rv.t_out = out->t_v;
+    LSF_TRY(run_pass(mode, th, y, kPassUpdate, 1, &rv, ws, status, st));
+  }
+  return LSF_OK;
+}
+
+// The residual ||u o (K v) - a||_1 of one pair after its last v-half.
+int single_residual(int mode, const lsf_theta* th, const lsf_cloud* x, const lsf_scalings* out,
+                    lsf_result* result, const Workspace& ws, int* status, cudaStream_t st) {
+  PassRhs rd{};
+  rd.t_in = out->t_v; rd.w = x->w; rd.old = out->u; rd.res_out = &result->residual;
+  return run_pass(mode, th, x, kPassDot, 1, &rd, ws, status, st);
+}
+
+// Passes over one feature matrix with the right-hand sides of the active terms
+// (none: no pass).
+int run_active(int mode, const lsf_theta* th, const lsf_cloud* cl, int pmode, const PassRhs* r0,
+               bool a0, const PassRhs* r1, bool a1, const Workspace& ws, int* status, cudaStream_t st) {
+  PassRhs r[2];
+  int k = 0;
+  if (a0) r[k++] = *r0;
+  if (a1) r[k++] = *r1;
+  if (k == 0) return LSF_OK;
+  return run_pass(mode, th, cl, pmode, k, r, ws, status, st);
+}
+
+// `count` lock-step iterations of the debiased solves (Eq. (2)) whose flags act[]
+// (xy, xx, yy) are set: xi pass {XY u-half, XX u-half}, zeta pass {XY v-half,
+// YY u-half}, xi pass {XX v-half}, zeta pass {YY v-half}; a pass carries only the
+// active terms' right-hand sides.
+int debiased_iterations(int mode, const lsf_theta* th, const lsf_cloud* x, const lsf_cloud* y,
+                        const lsf_scalings* s_xy, const lsf_scalings* s_xx, const lsf_scalings* s_yy,
+                        const bool act[3], int count, const Workspace& ws, int* status,
+                        cudaStream_t st) {
+  for (int it = 0; it < count; ++it) {
+    PassRhs p1a{}, p1b{};
+    p1a.t_in = s_xy->t_v; p1a.w = x->w; p1a.out = s_xy->u; p1a.t_out = s_xy->t_u;
+    p1b.t_in = s_xx->t_v; p1b.w = x->w; p1b.out = s_xx->u; p1b.t_out = s_xx->t_u;
+    LSF_TRY(run_active(mode, th, x, kPassUpdate, &p1a, act[0], &p1b, act[1], ws, status, st));
+    PassRhs p2a{}, p2b{};
+    p2a.t_in = s_xy->t_u; p2a.w = y->w; p2a.out = s_xy->v; p2a.t_out = s_xy->t_v;
+    p2b.t_in = s_yy->t_v; p2b.w = y->w; p2b.out = s_yy->u; p2b.t_out = s_yy->t_u;
+    LSF_TRY(run_active(mode, th, y, kPassUpdate, &p2a, act[0], &p2b, act[2], ws, status, st));
+    PassRhs p3{};
+    p3.t_in = s_xx->t_u; p3.w = x->w; p3.out = s_xx->v; p3.t_out = s_xx->t_v;
+    LSF_TRY(run_active(mode, th, x, kPassUpdate, &p3, act[1], nullptr, false, ws, status, st));
+    PassRhs p4{};
+    p4.t_in = s_yy->t_u; p4.w = y->w; p4.out = s_yy->v; p4.t_out = s_yy->t_v;
+    LSF_TRY(run_active(mode, th, y, kPassUpdate, &p4, act[2], nullptr, false, ws, status, st));
+  }
+  return LSF_OK;
+}
+
+// The residuals of the active debiased terms after their last v-half.
+int debiased_residuals(int mode, const lsf_theta* th, const lsf_cloud* x, const lsf_cloud* y,
+                       const lsf_scalings* s_xy, const lsf_scalings* s_xx, const lsf_scalings* s_yy,
+                       lsf_result* rxy, lsf_result* rxx, lsf_result* ryy, const bool act[3],
+                       const Workspace& ws, int* status, cudaStream_t st) {
+  PassRhs d1a{}, d1b{};
+  d1a.t_in = s_xy->t_v; d1a.w = x->w; d1a.old = s_xy->u; d1a.res_out = &rxy->residual;
+  d1b.t_in = s_xx->t_v; d1b.w = x->w; d1b.old = s_xx->u; d1b.res_out = &rxx->residual;
+  LSF_TRY(run_active(mode, th, x, kPassDot, &d1a, act[0], &d1b, act[1], ws, status, st));
+  PassRhs d2{};
+  d2.t_in = s_yy->t_v; d2.w = y->w; d2.old = s_yy->u; d2.res_out = &ryy->residual;
+  return run_active(mode, th, y, kPassDot, &d2, act[2], nullptr, false, ws, status, st);
+}
+
+// Host copies of `count` device result records (synchronises the stream).
+int read_results(const lsf_result* dev, lsf_result* host, int count, cudaStream_t st) {
+  if (cudaMemcpyAsync(host, dev, sizeof(lsf_result) * count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LSF_ERR_CUDA, "reading the result records failed");
+  return LSF_OK;
+}
+
+int check_stop(int max_iters, double tol, int check_every) {
+  if (max_iters < 1) return fail(LSF_ERR_ARG, "max_iters must be >= 1");
+  if (!(tol >= 0.0)) return fail(LSF_ERR_ARG, "tol must be >= 0");
+  if (check_every < 1) return fail(LSF_ERR_ARG, "check_every must be >= 1");
+  return LSF_OK;
+}
+
 }  // namespace lsf
 
 using namespace lsf;
@@ -394,22 +485,53 @@ int lsf_solve(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, in
     r.t_out = out->t_v;
     LSF_TRY(run_pass(mode, theta, y, kPassAxpy, 1, &r, ws, status, st));
   }
-  for (int it = 0; it < iters; ++it) {
-    PassRhs ru{};
-    ru.t_in = out->t_v; ru.w = x->w; ru.out = out->u; ru.t_out = out->t_u;
-    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 1, &ru, ws, status, st));
-    PassRhs rv{};
-    rv.t_in = out->t_u; rv.w = y->w; rv.out = out->v; rv.t_out = out->t_v;
-    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 1, &rv, ws, status, st));
-  }
-  {
-    PassRhs rd{};
-    rd.t_in = out->t_v; rd.w = x->w; rd.old = out->u; rd.res_out = &result->residual;
-    LSF_TRY(run_pass(mode, theta, x, kPassDot, 1, &rd, ws, status, st));
-  }
+  LSF_TRY(single_iterations(mode, theta, x, y, out, iters, ws, status, st));
+  LSF_TRY(single_residual(mode, theta, x, out, result, ws, status, st));
   {
     LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
     set_iters_kernel<<<1, 32, 0, st>>>(result, nullptr, nullptr, iters, mode);
+  }
+  return check_launch("set_iters_kernel");
+}
+
+int lsf_solve_tol(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int max_iters,
+                  double tol, int check_every, int mode, const lsf_scalings* out, lsf_result* result,
+                  void* workspace, size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_solve_tol");
+  LSF_TRY(check_theta(theta));
+  LSF_TRY(check_stop(max_iters, tol, check_every));
+  if (mode == LSF_MODE_AUTO)
+    return solve_auto(theta, x, y, result, workspace, ws_bytes, as_stream(stream), [&](int m) {
+      return lsf_solve_tol(theta, x, y, max_iters, tol, check_every, m, out, result, workspace,
+                           ws_bytes, stream);
+    });
+  LSF_TRY(check_cloud(x, mode, "x"));
+  LSF_TRY(check_cloud(y, mode, "y"));
+  LSF_TRY(check_scalings(out, "out"));
+  cudaStream_t st = as_stream(stream);
+  Workspace ws{};
+  LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 1, &ws, st));
+  int* status = &result->status;
+  LSF_TRY(init_side(y, ws.keys + 0, out->v, &result->log_scale, nullptr, mode, st));
+  {
+    PassRhs r{};
+    r.old = out->v;
+    r.t_out = out->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassAxpy, 1, &r, ws, status, st));
+  }
+  int done = 0;
+  while (done < max_iters) {
+    const int chunk = std::min(check_every, max_iters - done);
+    LSF_TRY(single_iterations(mode, theta, x, y, out, chunk, ws, status, st));
+    done += chunk;
+    LSF_TRY(single_residual(mode, theta, x, out, result, ws, status, st));
+    lsf_result h{};
+    LSF_TRY(read_results(result, &h, 1, st));
+    if ((h.status & LSF_ERR_NONFINITE) || h.residual <= tol) break;
+  }
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    set_iters_kernel<<<1, 32, 0, st>>>(result, nullptr, nullptr, done, mode);
   }
   return check_launch("set_iters_kernel");
 }
@@ -497,35 +619,9 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
     q.old = s_xx->v; q.t_out = s_xx->t_v;
     LSF_TRY(run_pass(mode, theta, x, kPassAxpy, 1, &q, ws, status, st));
   }
-  for (int it = 0; it < iters; ++it) {
-    // xi pass: {XY u-half, XX u-half}
-    PassRhs p1[2] = {};
-    p1[0].t_in = s_xy->t_v; p1[0].w = x->w; p1[0].out = s_xy->u; p1[0].t_out = s_xy->t_u;
-    p1[1].t_in = s_xx->t_v; p1[1].w = x->w; p1[1].out = s_xx->u; p1[1].t_out = s_xx->t_u;
-    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 2, p1, ws, status, st));
-    // zeta pass: {XY v-half, YY u-half}
-    PassRhs p2[2] = {};
-    p2[0].t_in = s_xy->t_u; p2[0].w = y->w; p2[0].out = s_xy->v; p2[0].t_out = s_xy->t_v;
-    p2[1].t_in = s_yy->t_v; p2[1].w = y->w; p2[1].out = s_yy->u; p2[1].t_out = s_yy->t_u;
-    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 2, p2, ws, status, st));
-    // xi pass: {XX v-half}
-    PassRhs p3{};
-    p3.t_in = s_xx->t_u; p3.w = x->w; p3.out = s_xx->v; p3.t_out = s_xx->t_v;
-    LSF_TRY(run_pass(mode, theta, x, kPassUpdate, 1, &p3, ws, status, st));
-    // zeta pass: {YY v-half}
-    PassRhs p4{};
-    p4.t_in = s_yy->t_u; p4.w = y->w; p4.out = s_yy->v; p4.t_out = s_yy->t_v;
-    LSF_TRY(run_pass(mode, theta, y, kPassUpdate, 1, &p4, ws, status, st));
-  }
-  {
-    PassRhs d1[2] = {};
-    d1[0].t_in = s_xy->t_v; d1[0].w = x->w; d1[0].old = s_xy->u; d1[0].res_out = &rxy->residual;
-    d1[1].t_in = s_xx->t_v; d1[1].w = x->w; d1[1].old = s_xx->u; d1[1].res_out = &rxx->residual;
-    LSF_TRY(run_pass(mode, theta, x, kPassDot, 2, d1, ws, status, st));
-    PassRhs d2{};
-    d2.t_in = s_yy->t_v; d2.w = y->w; d2.old = s_yy->u; d2.res_out = &ryy->residual;
-    LSF_TRY(run_pass(mode, theta, y, kPassDot, 1, &d2, ws, status, st));
-  }
+  const bool all[3] = {true, true, true};
+  LSF_TRY(debiased_iterations(mode, theta, x, y, s_xy, s_xx, s_yy, all, iters, ws, status, st));
+  LSF_TRY(debiased_residuals(mode, theta, x, y, s_xy, s_xx, s_yy, rxy, rxx, ryy, all, ws, status, st));
   {
     const lsf_cloud* xs[3] = {x, x, y};
     const lsf_cloud* ys[3] = {y, x, y};
@@ -540,6 +636,86 @@ int lsf_debiased(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y,
     set_iters_kernel<<<1, 32, 0, st>>>(rxy, rxx, ryy, iters, mode);
   }
   // Status bits of all passes were collected in the first record; mirror them.
+  if (cudaMemcpyAsync(&rxx->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&ryy->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess)
+    return fail(LSF_ERR_CUDA, "debiased: status copy failed");
+  return check_launch("set_iters_kernel");
+}
+
+int lsf_debiased_tol(const lsf_theta* theta, const lsf_cloud* x, const lsf_cloud* y, int max_iters,
+                     double tol, int check_every, int mode, const lsf_scalings* s_xy,
+                     const lsf_scalings* s_xx, const lsf_scalings* s_yy, lsf_result* result,
+                     double* wbar, void* workspace, size_t ws_bytes, void* stream) {
+  lsf::TraceRange trace_range("lsf_debiased_tol");
+  LSF_TRY(check_theta(theta));
+  LSF_TRY(check_stop(max_iters, tol, check_every));
+  if (mode == LSF_MODE_AUTO)
+    return solve_auto(theta, x, y, result, workspace, ws_bytes, as_stream(stream), [&](int m) {
+      return lsf_debiased_tol(theta, x, y, max_iters, tol, check_every, m, s_xy, s_xx, s_yy, result,
+                              wbar, workspace, ws_bytes, stream);
+    });
+  LSF_TRY(check_cloud(x, mode, "x"));
+  LSF_TRY(check_cloud(y, mode, "y"));
+  LSF_TRY(check_scalings(s_xy, "xy"));
+  LSF_TRY(check_scalings(s_xx, "xx"));
+  LSF_TRY(check_scalings(s_yy, "yy"));
+  cudaStream_t st = as_stream(stream);
+  Workspace ws{};
+  LSF_TRY(start_solve(workspace, ws_bytes, theta->ldr, result, 3, &ws, st));
+  lsf_result* rxy = result + 0;
+  lsf_result* rxx = result + 1;
+  lsf_result* ryy = result + 2;
+  int* status = &rxy->status;
+  LSF_TRY(init_side(y, ws.keys + 0, s_xy->v, &rxy->log_scale, &ryy->log_scale, mode, st));
+  if (cudaMemcpyAsync(s_yy->v, s_xy->v, sizeof(float) * y->n, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return fail(LSF_ERR_CUDA, "debiased: copy of the start vector failed");
+  LSF_TRY(init_side(x, ws.keys + 1, s_xx->v, &rxx->log_scale, nullptr, mode, st));
+  {
+    PassRhs r[2] = {};
+    r[0].old = s_xy->v; r[0].t_out = s_xy->t_v;
+    r[1].old = s_yy->v; r[1].t_out = s_yy->t_v;
+    LSF_TRY(run_pass(mode, theta, y, kPassAxpy, 2, r, ws, status, st));
+    PassRhs q{};
+    q.old = s_xx->v; q.t_out = s_xx->t_v;
+    LSF_TRY(run_pass(mode, theta, x, kPassAxpy, 1, &q, ws, status, st));
+  }
+  // each term of Eq. (2) stops on its own test; the others keep their lock-step
+  // passes
+  bool act[3] = {true, true, true};
+  int done[3] = {0, 0, 0};
+  int it = 0;
+  while (it < max_iters && (act[0] || act[1] || act[2])) {
+    const int chunk = std::min(check_every, max_iters - it);
+    LSF_TRY(debiased_iterations(mode, theta, x, y, s_xy, s_xx, s_yy, act, chunk, ws, status, st));
+    it += chunk;
+    LSF_TRY(debiased_residuals(mode, theta, x, y, s_xy, s_xx, s_yy, rxy, rxx, ryy, act, ws, status, st));
+    lsf_result h[3];
+    LSF_TRY(read_results(result, h, 3, st));
+    const bool void_run = (h[0].status & LSF_ERR_NONFINITE) != 0;
+    for (int t = 0; t < 3; ++t)
+      if (act[t]) {
+        done[t] = it;
+        if (void_run || h[t].residual <= tol) act[t] = false;
+      }
+  }
+  {
+    const lsf_cloud* xs[3] = {x, x, y};
+    const lsf_cloud* ys[3] = {y, x, y};
+    const lsf_scalings* ss[3] = {s_xy, s_xx, s_yy};
+    lsf_result* rs[3] = {rxy, rxx, ryy};
+    const double coef[3] = {1.0, -0.5, -0.5};
+    LSF_TRY(launch_divergence(theta, 3, xs, ys, ss, rs, coef, wbar, ws, st,
+                              mode == LSF_MODE_LOG ? 1 : 0));
+  }
+  {
+    LaunchScope ls(st, LSF_KERNEL_OTHER, 0.0);
+    set_iters_kernel<<<1, 32, 0, st>>>(rxy, nullptr, nullptr, done[0], mode);
+    set_iters_kernel<<<1, 32, 0, st>>>(rxx, nullptr, nullptr, done[1], mode);
+    set_iters_kernel<<<1, 32, 0, st>>>(ryy, nullptr, nullptr, done[2], mode);
+  }
   if (cudaMemcpyAsync(&rxx->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(&ryy->status, &rxy->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=

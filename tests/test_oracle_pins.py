@@ -189,6 +189,40 @@ def test_factored_log_matches_dense_textbook():
         assert abs(sl["residual"] - sd["residual"]) < 1e-13
 
 
+def test_stopping_rule_stops_at_the_first_passing_check_of_the_dense_textbook():
+    # the textbook solver on the explicit K gives the residual after every
+    # iteration count; the stopped solve must end at the first multiple of k
+    # whose residual is within tol, with that iteration's scalings
+    X, Y, Z, a, b, th, Lx, Ly = _tiny_factors(seed=3, n=9, m=6, r=4)
+    K = np.exp(Lx) @ np.exp(Ly).T
+    res = {t: o.sinkhorn_dense(K, a, b, t)["residual"] for t in range(1, 61)}
+    for k in (1, 3, 7):
+        for tol in (1e-2, 1e-4, 1e-7):
+            st = o.sinkhorn_log_tol(Lx, Ly, a, b, 60, tol, k)
+            checks = [t for t in range(k, 61, k)] + ([] if 60 % k == 0 else [60])
+            want = next((t for t in checks if res[t] <= tol), 60)
+            assert st["iters"] == want, (k, tol, st["iters"], want)
+            sd = o.sinkhorn_dense(K, a, b, want)
+            np.testing.assert_allclose(st["logu"], sd["logu"], rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(st["logv"], sd["logv"], rtol=1e-12, atol=1e-12)
+            assert abs(st["residual"] - res[want]) < 1e-13
+
+
+def test_stopping_rule_on_a_rank_one_kernel_and_at_zero_tolerance():
+    # one feature: K = xi zeta^T has rank one, so after one iteration
+    # u o (K v) = a (sum b) = a exactly, and any positive tol stops at the first
+    # check
+    X, Y, Z, a, b, th, Lx, Ly = _tiny_factors(seed=5, n=8, m=6, r=1)
+    st = o.sinkhorn_log_tol(Lx, Ly, a, b, 50, 1e-12, 1)
+    assert st["iters"] == 1 and st["residual"] < 1e-14
+    st = o.sinkhorn_log_tol(Lx, Ly, a, b, 50, 1e-12, 4)
+    assert st["iters"] == 4
+    # tol = 0 on a full-rank kernel is never met: the cap is reached
+    X, Y, Z, a, b, th, Lx, Ly = _tiny_factors(seed=5, n=8, m=6, r=5)
+    st = o.sinkhorn_log_tol(Lx, Ly, a, b, 13, 0.0, 5)
+    assert st["iters"] == 13 and st["residual"] > 0.0
+
+
 def test_scaled_matches_log():
     p = synth.tiny_problem(n=300, m=250, r=40, iters=30)
     th = o.make_theta(p.X, p.Y, p.Z, p.eps)
