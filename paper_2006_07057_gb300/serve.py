@@ -75,6 +75,18 @@ class Request:
                              self.eps, self.iters, True, mode)
 
 
+HYBRID_MAX_D = 4
+
+
+def first_mode(req: "Request") -> str:
+    """The domain and pass a request starts in. The hybrid pass (half the feature
+    columns rebuilt in registers, half streamed) beats the stored pass when its
+    rebuilt entries are cheap (d + 3 FP32 operations each); for larger d the
+    stored pass is faster. A non-finite scaling in either sends the request to the
+    log domain."""
+    return "hybrid" if req.X.shape[1] <= HYBRID_MAX_D else "stored"
+
+
 def request_bytes(n: int, m: int, r: int, d: int, mode: str = "stored") -> int:
     """Device bytes a request holds while admitted: its lsf_pipeline_run arena
     (inputs, theta, features, scalings, results, workspace)."""
@@ -185,7 +197,7 @@ class Server:
         """Finish the slot's request, or relaunch it in the log domain (returns None)."""
         req = slot.req
         rec = slot.record()
-        if (rec["status"] & LSF_ERR_NONFINITE) and slot.mode == "stored":
+        if (rec["status"] & LSF_ERR_NONFINITE) and slot.mode != "log":
             self.relaunched += 1
             self._start(slot, req, "log")
             return None
@@ -237,7 +249,7 @@ class Server:
                 waiting.popleft()
                 free.range = rng
                 req.start_s = now()
-                self._start(free, req, "stored")
+                self._start(free, req, first_mode(req))
                 self.peak_bytes = max(self.peak_bytes, float(self.pool.in_use))
                 self.peak_inflight = max(self.peak_inflight, sum(s.req is not None for s in self.slots))
             if not waiting and pending and all(s.req is None for s in self.slots):
@@ -400,7 +412,8 @@ class BatchingServer:
 
 def serve_sequential(requests: list[Request], realtime: bool = True, device=None) -> list[Request]:
     """The plain competitor: one request at a time, in arrival order, one stream, the
-    same library call and the same routing (log domain after a non-finite run)."""
+    same library call and the same routing as ``Server`` (``first_mode``, then the
+    log domain after a non-finite run)."""
     device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
     reqs = sorted(requests, key=lambda r: r.arrival_s)
     for r in reqs:
@@ -418,7 +431,7 @@ def serve_sequential(requests: list[Request], realtime: bool = True, device=None
         if wait > 0:
             time.sleep(wait)
         req.start_s = time.perf_counter() - t0
-        for mode in ("stored", "log"):
+        for mode in (first_mode(req), "log"):
             _launch(req, mode, arena, out, stream)
             stream.synchronize()
             rec = LsfPipelineOut.from_address(out.data_ptr())

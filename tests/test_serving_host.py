@@ -63,3 +63,12 @@ def test_free_list_first_fit_against_a_brute_force_model():
         for (o1, l1), (o2, _) in zip(fl.free_list, fl.free_list[1:]):
             assert o1 + l1 < o2            # coalesced: no two free ranges touch
         assert all(o % 256 == 0 and ln % 256 == 0 for o, ln in fl.free_list)
+
+
+def test_first_mode_takes_the_hybrid_pass_for_low_dimensions():
+    def req(d):
+        z = np.zeros((4, d), np.float32)
+        return serve.Request(0, z, z, np.ones(4, np.float32) / 4, np.ones(4, np.float32) / 4,
+                             np.zeros((8, d), np.float32), 1.0, 1)
+    assert [serve.first_mode(req(d)) for d in (1, 2, 3, 4, 5, 16)] == \
+        ["hybrid"] * 4 + ["stored"] * 2
