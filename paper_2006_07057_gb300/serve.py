@@ -76,15 +76,20 @@ class Request:
 
 
 HYBRID_MAX_D = 4
+SMALL_SOLVER_ENTRIES = 1 << 24   # the library's default size rule for its one-launch solver
 
 
 def first_mode(req: "Request") -> str:
     """The domain and pass a request starts in. The hybrid pass (half the feature
     columns rebuilt in registers, half streamed) beats the stored pass when its
     rebuilt entries are cheap (d + 3 FP32 operations each); for larger d the
-    stored pass is faster. A non-finite scaling in either sends the request to the
-    log domain."""
-    return "hybrid" if req.X.shape[1] <= HYBRID_MAX_D else "stored"
+    stored pass is faster. Requests whose three terms all fit the stored mode's
+    one-launch solver ((n + m) ldr <= 2^24 entries for each) stay stored: their
+    time is launches, not entries. A non-finite scaling in either sends the
+    request to the log domain."""
+    n, m, d = req.X.shape[0], req.Y.shape[0], req.X.shape[1]
+    small = 2 * max(n, m) * ldr_for(req.Z.shape[0]) <= SMALL_SOLVER_ENTRIES
+    return "hybrid" if d <= HYBRID_MAX_D and not small else "stored"
 
 
 def request_bytes(n: int, m: int, r: int, d: int, mode: str = "stored") -> int:

@@ -65,10 +65,14 @@ def test_free_list_first_fit_against_a_brute_force_model():
         assert all(o % 256 == 0 and ln % 256 == 0 for o, ln in fl.free_list)
 
 
-def test_first_mode_takes_the_hybrid_pass_for_low_dimensions():
-    def req(d):
-        z = np.zeros((4, d), np.float32)
-        return serve.Request(0, z, z, np.ones(4, np.float32) / 4, np.ones(4, np.float32) / 4,
-                             np.zeros((8, d), np.float32), 1.0, 1)
-    assert [serve.first_mode(req(d)) for d in (1, 2, 3, 4, 5, 16)] == \
+def test_first_mode_takes_the_hybrid_pass_for_large_low_dimensional_requests():
+    def req(n, d, r):
+        z = np.zeros((n, d), np.float32)
+        w = np.ones(n, np.float32) / n
+        return serve.Request(0, z, z, w, w, np.zeros((r, d), np.float32), 1.0, 1)
+    big = 1 << 15   # 2 n ldr = 2^25 entries at r = 512: past the one-launch solver
+    assert [serve.first_mode(req(big, d, 512)) for d in (1, 2, 3, 4, 5, 16)] == \
         ["hybrid"] * 4 + ["stored"] * 2
+    # within the one-launch solver's size rule ((n + m) ldr <= 2^24 per term)
+    assert serve.first_mode(req(1 << 14, 3, 512)) == "stored"
+    assert serve.first_mode(req(1 << 14, 3, 513)) == "hybrid"
