@@ -31,7 +31,8 @@
 namespace lsf {
 namespace {
 
-template <int C, int NRHS, int MODE>
+// EXACT: ldr = 128 C (no padded columns), so no column needs a bounds test.
+template <int C, int NRHS, int MODE, bool EXACT = false>
 __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs a) {
   constexpr int RW = 8 / C;
   constexpr int SH = RowFold<RW>::kShift;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 #pragma unroll
           for (int j = 0; j < C; ++j) {
             const int col = 4 * lane + 128 * j;
-            f[q][j] = (rr + q < rows && col < ldr)
+            f[q][j] = ((RW == 1 || rr + q < rows) && (EXACT || col < ldr))
                           ? *reinterpret_cast<const float4*>(tF + static_cast<size_t>(rr + q) * ldr + col)
                           : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
           }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           const int col = 4 * lane + 128 * j;
-          if (col < ldr) {
+          if (EXACT || col < ldr) {
             float* rg = red + (static_cast<size_t>(warp) * NRHS + k) * 2 * ldr;
             *reinterpret_cast<float4*>(rg + col) =
                 make_float4(lm[k][j][0].x, lm[k][j][0].y, lm[k][j][1].x, lm[k][j][1].y);
@@ -245,7 +246,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
 template <int C, int NRHS>
 int launch_log_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {
   void (*kern)(PassArgs) = nullptr;
-  if (mode == kPassUpdate) kern = logpass_kernel<C, NRHS, kPassUpdate>;
+  // (at C = 8 the unpredicated loads raise the register need past the file: spills)
+  if (mode == kPassUpdate && C <= 4 && a.ldr == 128 * C) kern = logpass_kernel<C, NRHS, kPassUpdate, C <= 4>;
+  else if (mode == kPassUpdate) kern = logpass_kernel<C, NRHS, kPassUpdate>;
   else if (mode == kPassAxpy) kern = logpass_kernel<C, NRHS, kPassAxpy>;
   else if (mode == kPassDot) kern = logpass_kernel<C, NRHS, kPassDot>;
   else if constexpr (NRHS == 1) {
