@@ -259,7 +259,7 @@ int lsf_workspace_bytes(int ldr, size_t* bytes);
 
 /*
  * Alg. 1 (Sec. 2) on the factored kernel K_theta = xi^T zeta (Sec. 3.1),
- * spec order: from v = 1, `iters` times u <- a/(K v), v <- b/(K^T u).
+ * in this order: from v = 1, `iters` times u <- a/(K v), v <- b/(K^T u).
  * Each half is one fused pass over a feature matrix that forms s = F t,
  * divides the weights by s and accumulates the transposed product in the same
  * read. After the loop one more read of F gives the residual
