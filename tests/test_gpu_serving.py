@@ -106,3 +106,34 @@ def test_batching_server_routes_range_failures_to_the_log_domain(serve):
         assert abs(r.W_bar - a.W_bar) <= 1e-4 * scale, (r.rid, r.W_bar, a.W_bar)
     if any(a.result["mode"] == "log" for a in alone):
         assert srv.relaunched > 0 and any(r.result["mode"] == "log" for r in mixed)
+
+
+def test_server_runs_large_low_dimensional_requests_on_the_hybrid_pass(serve):
+    # requests past the one-launch solver's size with d <= 4 start on the hybrid
+    # pass (serve.first_mode); the sequential arm routes the same way, and both
+    # must match the oracle
+    from oracle import oracle as o
+    out = []
+    for i, rq in enumerate(synth.serving_stream(seed=11, count=40, rate_per_s=4000.0, iters=20,
+                                                n_lo=1 << 15, n_hi=1 << 15)):
+        p = rq.problem
+        if p.X.shape[1] <= 3 and p.Z.shape[0] == 512 and p.eps >= 0.2:
+            out.append(serve.Request(len(out), p.X, p.Y, p.a, p.b, p.Z, p.eps, 20, rq.arrival_s))
+        if len(out) == 2:
+            break
+    assert len(out) == 2
+    assert all(serve.first_mode(r) == "hybrid" for r in out)
+    alone = serve.serve_sequential([serve.Request(r.rid, r.X, r.Y, r.a, r.b, r.Z, r.eps, r.iters)
+                                    for r in out], realtime=False)
+    srv = serve.Server(budget_bytes=20e9, slots=4)
+    mixed = srv.serve(out, realtime=False)
+    by_id = {r.rid: r for r in alone}
+    for r in mixed:
+        a = by_id[r.rid]
+        assert r.status == 0 and a.status == 0
+        assert r.result["mode"] == "hybrid" and a.result["mode"] == "hybrid"
+        # (the scaling-domain oracle: eps >= 0.2 at d = 2 is well inside FP64 range)
+        ref = o.divergence(r.X, r.Y, r.a, r.b, r.Z, r.eps, r.iters, debiased=True, mode="scaled")
+        scale = abs(ref["W_xy"]) + 0.5 * abs(ref["W_xx"]) + 0.5 * abs(ref["W_yy"])
+        assert abs(r.W_bar - ref["W_bar"]) <= 1e-4 * scale, (r.rid, r.W_bar, ref["W_bar"])
+        assert abs(r.W_bar - a.W_bar) <= 1e-4 * scale

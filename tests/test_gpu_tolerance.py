@@ -143,3 +143,29 @@ def test_tolerance_arguments_are_checked(lsf):
     with pytest.raises(lsf.LsfError) as e:
         prob.run(0, debiased=True, tol=1e-3)
     assert e.value.status == lsf.LSF_ERR_ARG
+
+
+def test_auto_mode_with_a_tolerance_picks_the_domain_and_stops(lsf):
+    # LSF_MODE_AUTO with the stopping rule: the library builds the features,
+    # picks the domain (the log domain after a range failure) and stops by the
+    # residual; checked against the oracle after the iterations it ran
+    for seed, d, eps, shift in ((51, 3, 0.3, 0.0), (17, 16, 0.05, 1.0)):
+        p = synth.small_problem(seed, 400, 300, d, 128, eps, 0, weights="dirichlet", shift=shift)
+        prob = problem(lsf, p, "auto")
+        tol, k, cap = 1e-3, 5, 80
+        prob.run(cap, debiased=False, tol=tol, check_every=k)
+        g = prob.values()
+        assert g["status"] == 0
+        assert prob.used_mode in ("stored", "log")
+        T = g["iters"]
+        Lx, Ly = oracle_factors(p)
+        cache = {}
+
+        def res_at(t):
+            if t not in cache:
+                cache[t] = o.sinkhorn_log(Lx, Ly, p.a, p.b, t)["residual"]
+            return cache[t]
+
+        check_stop(T, k, cap, tol, res_at)
+        ref = o.divergence(p.X, p.Y, p.a, p.b, p.Z, p.eps, T, debiased=False)
+        assert abs(g["W_xy"] - ref["W_xy"]) <= W_RTOL * abs(ref["W_xy"]), (seed, g["W_xy"], ref["W_xy"])
