@@ -970,16 +970,21 @@ def main():
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         e0.record(stream)
-        for _ in range(args.steps):
+        marks[0].record(stream)
+        for i in range(args.steps):
             if mode in ("recompute", "hybrid"):
                 l2_flush.zero_()
             prob = step_resident()
+            marks[i + 1].record(stream)
         e1.record(stream)
         barrier()
         launches = lsf.lsf_launch_count()
         clocks = sampler.stop()
         ms = slowest(e0.elapsed_time(e1) / args.steps)
+        per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
+        ms_median = per_step[len(per_step) // 2]
         cls = {"stored": lsf.LSF_KERNEL_PASS, "recompute": lsf.LSF_KERNEL_PASS_RECOMPUTE,
                "log": lsf.LSF_KERNEL_PASS_LOG, "hybrid": lsf.LSF_KERNEL_PASS_HYBRID}[mode]
         k_ms, k_n, k_bytes = lsf.lsf_profile_read(cls)
@@ -1049,7 +1054,7 @@ def main():
                         "bytes_per_launch": k_bytes / launches_n, "share_of_step": share}
         return {"mode": mode, "ms": ms, "value": whole_job_value(updates, world, ms), "launches": launches,
                 "clocks": clocks, "roofline": roof, "vals": vals,
-                "features_ms_per_step": feat_ms / args.steps}
+                "features_ms_per_step": feat_ms / args.steps, "ms_median": ms_median}
 
     modes = (["stored", "recompute", "hybrid"] if args.mode == "all" else
              ["stored", "recompute"] if args.mode == "both" else [args.mode])
@@ -1102,7 +1107,9 @@ def main():
             "data": "synthetic", "config": workload_config(args, best["mode"]), "e2e": e2e,
             "gpu_launches": int(best["launches"]), "roofline": best["roofline"],
             "cpu_baseline": cpu, "clocks": best["clocks"],
+            "ms_per_step_median": best["ms_median"],
             "variants": {r["mode"]: {"value": r["value"], "ms_per_step": r["ms"],
+                                     "ms_per_step_median": r["ms_median"],
                                      "gpu_launches": int(r["launches"]), "roofline": r["roofline"],
                                      "W_bar": r["vals"]["W_bar"], "clocks": r["clocks"],
                                      "features_ms_per_step": r["features_ms_per_step"]}
