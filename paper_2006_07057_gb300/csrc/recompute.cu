@@ -43,9 +43,13 @@ constexpr int kRcWarps = 8;                      // compute warps
 constexpr int kRcThreads = (kRcWarps + 1) * 32;  // + the service warp
 constexpr int kRcRB = 8;  // rows per group per batch
 
-template <int GW, int D, int NRHS>
+// FIXED: the update pass without previous scalings at ldr = 1024 (every pass of
+// the solvers' loops on the large workload), compiled with the mode and the
+// row stride fixed.
+template <int GW, int D, int NRHS, bool FIXED = false>
 __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
-    recompute_kernel(const RecomputeArgs a, const int mode) {
+    recompute_kernel(const RecomputeArgs a, const int mode_in) {
+  const int mode = FIXED ? static_cast<int>(kPassUpdate) : mode_in;
   constexpr int NG = kRcWarps / GW;         // row groups per CTA
   constexpr int RPB = NG * kRcRB;           // rows per batch
   constexpr int TPG = GW * 32;              // threads per group
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
   const bool service = warp == kRcWarps;
   const int g = service ? 0 : warp / GW;    // my group
   const int tg = tid - g * TPG;             // my thread index inside the group
-  const int ldr = a.ldr, d = a.d;
+  const int ldr = FIXED ? 1024 : a.ldr, d = a.d;
   const int col0 = 4 * tg;                  // my four columns
 
   if (tid == 0) {
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(kRcThreads, D <= 4 ? 2 : 1)
     // ---- service warp: row records in, scalings out ----
     bool has_old[NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    for (int k = 0; k < NRHS; ++k) has_old[k] = !FIXED && a.rhs[k].old != nullptr;
     // Each lane serves one right-hand side (items in steps of 32 with kRcRB = 8)
     // and sums the residual terms |old s - w| of its rows: each term in one
     // rounding (a fused multiply-add), the sum compensated in FP32, widened once
@@ -360,6 +364,11 @@ int launch_gdn(int mode, const RecomputeArgs& a, cudaStream_t st) {
   constexpr int NG = kRcWarps / GW;
   const size_t smem = sizeof(float) * static_cast<size_t>(NG) * NRHS * a.ldr;
   auto kern = recompute_kernel<GW, D, NRHS>;
+  if constexpr (GW == 8 && D <= 4) {
+    bool old = false;
+    for (int k = 0; k < NRHS; ++k) old = old || a.rhs[k].old != nullptr;
+    if (mode == kPassUpdate && !old && a.ldr == 1024) kern = recompute_kernel<GW, D, NRHS, true>;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return fail(LSF_ERR_CUDA, "recompute: smem attribute: %s", cudaGetErrorString(e));
