@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
 
   int flag = 0;
   float acc[NRHS][C][4];
+  // residual terms |old s - w| of the rows this lane owns: each in one rounding
+  // (a fused multiply-add), summed with compensation in FP32 and widened once at
+  // the end (no FP64 arithmetic per row)
+  CompSum racc[NRHS];
   double res[NRHS];
 #pragma unroll
   for (int k = 0; k < NRHS; ++k) {
@@ -206,8 +210,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
               const float* vold = vw + TR;
               const float wi = vw[mrow];
               if (has_old[k] && owner)
-                res[k] += fabs(static_cast<double>(vold[mrow]) * static_cast<double>(dot) -
-                               static_cast<double>(wi));
+                racc[k].add(fabsf(fmaf(vold[mrow], dot, -wi)));
               if (MODE == kPassUpdate) {
                 sc = wi * __frcp_rn(dot);
                 if (owner) {
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) pass_kernel(const PassArgs a)
     }
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) {
-      double r = res[k];
+      double r = static_cast<double>(racc[k].s) + static_cast<double>(racc[k].c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
       res[k] = r;
