@@ -32,7 +32,8 @@ namespace lsf {
 namespace {
 
 // EXACT: ldr = 128 C (no padded columns), so no column needs a bounds test.
-template <int C, int NRHS, int MODE, bool EXACT = false>
+// NOOLD: no right-hand side carries previous scalings (no residual terms).
+template <int C, int NRHS, int MODE, bool EXACT = false, bool NOOLD = false>
 __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs a) {
   constexpr int RW = 8 / C;
   constexpr int SH = RowFold<RW>::kShift;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) logpass_kernel(const PassArgs
   } else {
     bool has_old[NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) has_old[k] = a.rhs[k].old != nullptr;
+    for (int k = 0; k < NRHS; ++k) has_old[k] = !NOOLD && a.rhs[k].old != nullptr;
     const int myq = (lane >> SH) & (RW - 1);
     const bool owner = (lane & ((1 << SH) - 1)) == 0;
 
@@ -247,7 +248,14 @@ template <int C, int NRHS>
 int launch_log_c_nrhs(int mode, const PassArgs& a, unsigned grid, size_t smem, cudaStream_t st) {
   void (*kern)(PassArgs) = nullptr;
   // (at C = 8 the unpredicated loads raise the register need past the file: spills)
-  if (mode == kPassUpdate && C <= 4 && a.ldr == 128 * C) kern = logpass_kernel<C, NRHS, kPassUpdate, C <= 4>;
+  bool noold = true;
+  for (int k = 0; k < NRHS; ++k) noold = noold && a.rhs[k].old == nullptr;
+  const bool exact = C <= 4 && a.ldr == 128 * C;
+  // (NOOLD pays at C <= 4; at C = 8 it measured about 1 % slower)
+  if (mode == kPassUpdate && noold && C <= 4)
+    kern = exact ? logpass_kernel<C, NRHS, kPassUpdate, C <= 4, C <= 4>
+                 : logpass_kernel<C, NRHS, kPassUpdate, false, C <= 4>;
+  else if (mode == kPassUpdate && exact) kern = logpass_kernel<C, NRHS, kPassUpdate, C <= 4>;
   else if (mode == kPassUpdate) kern = logpass_kernel<C, NRHS, kPassUpdate>;
   else if (mode == kPassAxpy) kern = logpass_kernel<C, NRHS, kPassAxpy>;
   else if (mode == kPassDot) kern = logpass_kernel<C, NRHS, kPassDot>;
