@@ -627,17 +627,26 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
           err |= LSF_ERR_TIMEOUT;
           break;
         }
+        // (the mode is tested once, outside the unrolled loops, so that an update
+        // launch issues none of the residual's FP64 instructions)
+        if (a.mode == kMultiUpdate) {
 #pragma unroll
-        for (int p = 0; p < KP; ++p) {
-          u[p] = 0.f;
-          if (mine(p) && p < a.k && valid) {
-            // hi-plane part + lo-plane part (the same sum on either side)
-            const float sp = (d[p] + d[KP + p]) + xb[p * kTileRows + rloc];
-            if (a.mode == kMultiUpdate) {
+          for (int p = 0; p < KP; ++p) {
+            u[p] = 0.f;
+            if (mine(p) && p < a.k && valid) {
+              // hi-plane part + lo-plane part (the same sum on either side)
+              const float sp = (d[p] + d[KP + p]) + xb[p * kTileRows + rloc];
               const float v = w[p] * __frcp_rn(sp);
               if (!(v > 0.f && v < INFINITY)) bad |= 1u << p;
               u[p] = v;
-            } else {
+            }
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < KP; ++p) {
+            u[p] = 0.f;
+            if (mine(p) && p < a.k && valid) {
+              const float sp = (d[p] + d[KP + p]) + xb[p * kTileRows + rloc];
               resid[p] += fabs(static_cast<double>(o[p]) * static_cast<double>(sp) - static_cast<double>(w[p]));
             }
           }
