@@ -92,3 +92,23 @@ def test_tracing_level_switch():
             lsf.lsf_set_tracing(bad)
         assert e.value.status == B.LSF_ERR_ARG
     assert lsf.lsf_set_tracing(1) == 0
+
+
+def test_tolerance_solves_validate_before_launching():
+    # the stopping-rule arguments are checked on the host, before any device work
+    L = lsf.lib()
+    th = B.LsfTheta(None, None, 8, 8, 2, 0.5)
+    cl = B.LsfCloud(None, None, None, None, 0)
+    sc = B.LsfScalings(None, None, None, None)
+    for max_iters, tol, k in ((0, 1e-3, 5), (10, -1.0, 5), (10, float("nan"), 5), (10, 1e-3, 0)):
+        rc = L.lsf_solve_tol(ctypes.byref(th), ctypes.byref(cl), ctypes.byref(cl), max_iters, tol, k,
+                             0, ctypes.byref(sc), None, None, 0, None)
+        assert rc == B.LSF_ERR_ARG, (max_iters, tol, k)
+        rc = L.lsf_debiased_tol(ctypes.byref(th), ctypes.byref(cl), ctypes.byref(cl), max_iters, tol, k,
+                                0, ctypes.byref(sc), ctypes.byref(sc), ctypes.byref(sc), None, None,
+                                None, 0, None)
+        assert rc == B.LSF_ERR_ARG, (max_iters, tol, k)
+    # valid stopping arguments: the empty cloud is the next thing refused
+    rc = L.lsf_solve_tol(ctypes.byref(th), ctypes.byref(cl), ctypes.byref(cl), 10, 1e-3, 5, 0,
+                         ctypes.byref(sc), None, None, 0, None)
+    assert rc == B.LSF_ERR_ARG and b"n >= 1" in L.lsf_last_error()
